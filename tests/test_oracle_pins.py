@@ -1,0 +1,417 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: every expected value comes from
+an independent construction (explicit Jacobian of Eq. (3.1), numpy einsum of a
+definition, closed forms, exact decompositions, finite differences, dense
+solves).  Sizes keep the whole file to seconds.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from tests import cpref
+from paper_1910_12331_gb300 import datagen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+SHAPES = [((5, 7, 9), 3), ((6, 5, 4, 7), 4), ((8, 6), 3), ((3, 4, 2, 3, 2), 2)]
+
+
+def _rand_factors(dims, R, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((s, R)) for s in dims]
+
+
+def _rand_tensor(dims, seed):
+    return np.random.default_rng(seed + 1000).standard_normal(dims)
+
+
+# ----------------------------------------------------------------- Gram, Gamma
+
+@pytest.mark.parametrize("dims,R", SHAPES)
+def test_gram_gamma(orc, dims, R):
+    A = _rand_factors(dims, R, 1)
+    S = orc.gram(A)
+    for n, a in enumerate(A):
+        np.testing.assert_allclose(S[n], a.T @ a, rtol=1e-13, atol=1e-13)
+    G = orc.gamma(S)
+    N = len(dims)
+    for n in range(N):
+        for p in range(N):
+            ref = np.ones((R, R))
+            for m in range(N):
+                if m not in (n, p):
+                    ref = ref * (A[m].T @ A[m])
+            np.testing.assert_allclose(G[n, p], ref, rtol=1e-13)
+            np.testing.assert_array_equal(G[n, p], G[p, n])      # symmetric in (n, p)
+            np.testing.assert_allclose(G[n, p], G[n, p].T, rtol=1e-13)  # each block symmetric
+
+
+def test_gamma_order2_all_ones(orc):
+    A = _rand_factors((5, 6), 3, 2)
+    G = orc.gamma(orc.gram(A))
+    np.testing.assert_array_equal(G[0, 1], np.ones((3, 3)))
+    np.testing.assert_allclose(G[0, 0], A[1].T @ A[1], rtol=1e-14)
+
+
+# ---------------------------------------------------------------------- MTTKRP
+
+def _einsum_mttkrp(X, A, n):
+    """M^(n) = X_(n) P^(n) written as one einsum over the definition."""
+    N = X.ndim
+    letters = "abcdefgh"[:N]
+    ins = [letters] + [f"{letters[m]}z" for m in range(N) if m != n]
+    spec = ",".join(ins) + f"->{letters[n]}z"
+    return np.einsum(spec, X, *[A[m] for m in range(N) if m != n], optimize=True)
+
+
+@pytest.mark.parametrize("dims,R", SHAPES)
+@pytest.mark.parametrize("method", ["def", "dt"])
+def test_mttkrp_definition(orc, dims, R, method):
+    A = _rand_factors(dims, R, 3)
+    X = _rand_tensor(dims, 3)
+    M = orc.mttkrp(X, A, method)
+    for n in range(len(dims)):
+        ref = _einsum_mttkrp(X, A, n)
+        np.testing.assert_allclose(M[n], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dims,R", SHAPES[:2])
+def test_mttkrp_row(orc, dims, R):
+    A = _rand_factors(dims, R, 4)
+    X = _rand_tensor(dims, 4)
+    M = orc.mttkrp(X, A)
+    for n in range(len(dims)):
+        for i in (0, dims[n] - 1):
+            np.testing.assert_allclose(orc.mttkrp_row(X, A, n, i), M[n][i], rtol=1e-13, atol=1e-13)
+
+
+def test_mttkrp_rank1_closed_form(orc):
+    """All-ones factors: M^(n)_{i r} = sum of the mode-n slice i of X."""
+    dims = (4, 6, 5)
+    X = _rand_tensor(dims, 5)
+    A = [np.ones((s, 2)) for s in dims]
+    M = orc.mttkrp(X, A, "dt")
+    for n in range(3):
+        axes = tuple(m for m in range(3) if m != n)
+        sums = X.sum(axis=axes)
+        np.testing.assert_allclose(M[n], np.stack([sums, sums], 1), rtol=1e-13)
+
+
+@pytest.mark.parametrize("dims,R", [((7, 8, 9), 4), ((5, 4, 6, 3), 3)])
+def test_mttkrp_exact_decomposition(orc, dims, R):
+    """For X = [[A]] the normal equations hold exactly: M^(n) = A^(n) Gamma^(n),
+    and <X, X> = <M^(n), A^(n)> for every mode n."""
+    A = _rand_factors(dims, R, 6)
+    X = cpref.reconstruct(A)
+    M = orc.mttkrp(X, A, "dt")
+    for n in range(len(dims)):
+        Gam = np.ones((R, R))
+        for m in range(len(dims)):
+            if m != n:
+                Gam *= A[m].T @ A[m]
+        np.testing.assert_allclose(M[n], A[n] @ Gam, rtol=1e-12, atol=1e-12 * np.abs(M[n]).max())
+        assert abs(np.sum(M[n] * A[n]) - np.sum(X * X)) <= 1e-12 * np.sum(X * X)
+
+
+# ---------------------------------------------------------------- matmul tensor
+
+def test_strassen_golden(orc):
+    C, Af, Bf = cpref.load_strassen(os.path.join(GOLDEN, "strassen_2x2.txt"))
+    T = datagen.matmul_tensor(2)
+    # the fixture itself: it is an exact rank-7 decomposition of the tensor
+    np.testing.assert_array_equal(cpref.reconstruct([C, Af, Bf]), T)
+    # the tensor multiplies matrices (c_ij = sum_l a_il b_lj)
+    rng = np.random.default_rng(0)
+    a, b = rng.standard_normal((2, 2)), rng.standard_normal((2, 2))
+    c = np.einsum("xyz,y,z->x", T, a.reshape(-1), b.reshape(-1)).reshape(2, 2)
+    np.testing.assert_allclose(c, a @ b, rtol=1e-14)
+    A = [C, Af, Bf]
+    assert orc.residual(T, A) == 0.0
+    Gam = orc.gamma(orc.gram(A))
+    M = orc.mttkrp(T, A, "dt")
+    G, gn = orc.gradient(A, Gam, M)
+    assert np.all(gn == 0.0)  # entries are small integers: exact arithmetic
+    # classical algorithm, rank 8: product (i,l,j) -> c_ij += a_il b_lj
+    Cc, Ac, Bc = np.zeros((4, 8)), np.zeros((4, 8)), np.zeros((4, 8))
+    r = 0
+    for i in range(2):
+        for j in range(2):
+            for l in range(2):
+                Cc[2 * i + j, r] = Ac[2 * i + l, r] = Bc[2 * l + j, r] = 1.0
+                r += 1
+    assert orc.residual(T, [Cc, Ac, Bc]) == 0.0
+    # a perturbed Strassen factor has a non-zero residual and gradient
+    A2 = [C.copy(), Af.copy(), Bf.copy()]
+    A2[1][0, 0] += 1.0
+    assert orc.residual(T, A2) > 0.1
+
+
+# -------------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("dims,R", [((20, 20, 20), 5), ((4, 3, 5, 2), 3)])
+def test_gradient_is_jacobian_transpose_residual(orc, dims, R):
+    """G = J_r^T r (Section 3: gradient of phi) with J_r the explicit Jacobian of
+    Eq. (3.1) and r = X - [[A]]; checked at a random (non-stationary) point."""
+    A = _rand_factors(dims, R, 7)
+    X = _rand_tensor(dims, 7)
+    Gam = orc.gamma(orc.gram(A))
+    M = orc.mttkrp(X, A, "dt")
+    G, gn = orc.gradient(A, Gam, M)
+    J = cpref.jacobian(A)
+    r = (X - cpref.reconstruct(A)).reshape(-1)
+    ref = J.T @ r
+    got = cpref.pack(G)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(gn, [np.linalg.norm(g) for g in cpref.unpack(ref, dims, R)], rtol=1e-12)
+
+
+def test_gradient_finite_differences(orc):
+    dims, R = (6, 5, 7), 3
+    A = _rand_factors(dims, R, 8)
+    X = _rand_tensor(dims, 8)
+    Gam = orc.gamma(orc.gram(A))
+    G, _ = orc.gradient(A, Gam, orc.mttkrp(X, A, "def"))
+    rng = np.random.default_rng(9)
+    h = 1e-5
+    for _ in range(3):
+        D = [rng.standard_normal(a.shape) for a in A]
+        fp = cpref.objective(X, [a + h * d for a, d in zip(A, D)])
+        fm = cpref.objective(X, [a - h * d for a, d in zip(A, D)])
+        fd = (fp - fm) / (2 * h)
+        an = sum(float(np.sum(g * d)) for g, d in zip(G, D))
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
+
+
+# ------------------------------------------------------------ preconditioner
+
+def test_precond_inverse(orc):
+    A = _rand_factors((9, 8, 7), 5, 10)
+    Gam = orc.gamma(orc.gram(A))
+    for lam in (0.0, 1e-3, 10.0):
+        P, st = orc.precond_inv(Gam[0, 0], lam)
+        assert st == orc.OK
+        np.testing.assert_allclose((Gam[0, 0] + lam * np.eye(5)) @ P, np.eye(5), atol=1e-12)
+        np.testing.assert_allclose(P, P.T, rtol=1e-12, atol=1e-14)
+
+
+def test_precond_not_spd(orc):
+    G = np.ones((3, 3))  # rank one: singular
+    _, st = orc.precond_inv(G, 0.0)
+    assert st == orc.ERR_NOT_SPD
+    _, st = orc.precond_inv(-np.eye(2), 0.5)
+    assert st == orc.ERR_NOT_SPD
+
+
+# ----------------------------------------------------------------------- matvec
+
+@pytest.mark.parametrize("dims,R", [((20, 20, 20), 5), ((4, 3, 5, 2), 3), ((5, 6), 2)])
+@pytest.mark.parametrize("lam", [0.0, 0.37])
+def test_matvec_explicit_jacobian(orc, dims, R, lam):
+    """Q = (J^T J + lam I) w with J formed explicitly (Eq. (3.1)); checks the
+    Hessian blocks of Eq. (3.2) and the contractions of Eq. (3.4)."""
+    A = _rand_factors(dims, R, 11)
+    W = _rand_factors(dims, R, 12)
+    Gam = orc.gamma(orc.gram(A))
+    Q = orc.matvec(A, Gam, W, lam)
+    J = cpref.jacobian(A)
+    w = cpref.pack(W)
+    ref = J.T @ (J @ w) + lam * w
+    np.testing.assert_allclose(cpref.pack(Q), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_matvec_listing_einsums(orc):
+    """Listing 1's einsum strings evaluated by numpy on the same inputs."""
+    dims, R = (6, 7, 5), 4
+    A = _rand_factors(dims, R, 13)
+    W = _rand_factors(dims, R, 14)
+    Gam = orc.gamma(orc.gram(A))
+    Q = orc.matvec(A, Gam, W, 0.0)
+    for n in range(3):
+        U = np.zeros((dims[n], R))
+        for p in range(3):
+            if n == p:
+                U += np.einsum("rz,kz->kr", Gam[n, p], W[p])
+            else:
+                U += np.einsum("kz,lr,rz,lz->kr", A[n], A[p], Gam[n, p], W[p])
+        np.testing.assert_allclose(Q[n], U, rtol=1e-12, atol=1e-12 * np.abs(U).max())
+
+
+def test_matvec_symmetric_psd_nullspace(orc):
+    dims, R = (7, 6, 5), 3
+    A = _rand_factors(dims, R, 15)
+    Gam = orc.gamma(orc.gram(A))
+    U = _rand_factors(dims, R, 16)
+    V = _rand_factors(dims, R, 17)
+    HU = orc.matvec(A, Gam, U, 0.0)
+    HV = orc.matvec(A, Gam, V, 0.0)
+    uhv = sum(float(np.sum(u * h)) for u, h in zip(U, HV))
+    vhu = sum(float(np.sum(v * h)) for v, h in zip(V, HU))
+    assert abs(uhv - vhu) <= 1e-12 * abs(uhv)
+    assert sum(float(np.sum(v * h)) for v, h in zip(V, HV)) > 0
+    # scaling indeterminacy (Section 3.2): d/dt [[a1 (1+t), a2/(1+t), a3]] = 0
+    D = [np.zeros_like(a) for a in A]
+    D[0][:, 1] = A[0][:, 1]
+    D[1][:, 1] = -A[1][:, 1]
+    HD = orc.matvec(A, Gam, D, 0.0)
+    scale = max(np.abs(h).max() for h in HU)
+    assert max(np.abs(h).max() for h in HD) <= 1e-12 * scale
+
+
+# -------------------------------------------------------------------------- PCG
+
+@pytest.mark.parametrize("dims,R,lam", [((5, 4, 6), 3, 1e-2), ((4, 3, 3, 2), 2, 0.5)])
+def test_pcg_solves_normal_equations(orc, dims, R, lam):
+    """CP-CG (Algorithm 2) driven to a tiny tolerance equals the dense solve of
+    (J^T J + lam I) v = -g, within the N s R iteration bound of Section 3.4."""
+    A = _rand_factors(dims, R, 18)
+    X = _rand_tensor(dims, 18)
+    Gam = orc.gamma(orc.gram(A))
+    G, _ = orc.gradient(A, Gam, orc.mttkrp(X, A))
+    V, iters, rn, st = orc.pcg(A, Gam, G, lam, 1e-13, 10000)
+    assert st == orc.OK
+    J = cpref.jacobian(A)
+    H = J.T @ J + lam * np.eye(J.shape[1])
+    ref = np.linalg.solve(H, -cpref.pack(G))
+    np.testing.assert_allclose(cpref.pack(V), ref, rtol=1e-8, atol=1e-9 * np.abs(ref).max())
+    # finite termination: N s R iterations already reach the solution up to rounding
+    n_unknowns = sum(dims) * R
+    Vn, it_n, _, _ = orc.pcg(A, Gam, G, lam, 0.0, n_unknowns)
+    assert it_n == n_unknowns
+    np.testing.assert_allclose(cpref.pack(Vn), ref, rtol=1e-7, atol=1e-8 * np.abs(ref).max())
+
+
+def test_pcg_fixed_iterations_and_warning(orc):
+    dims, R = (6, 5, 4), 3
+    A = _rand_factors(dims, R, 19)
+    X = _rand_tensor(dims, 19)
+    Gam = orc.gamma(orc.gram(A))
+    G, _ = orc.gradient(A, Gam, orc.mttkrp(X, A))
+    V, iters, _, st = orc.pcg(A, Gam, G, 1e-3, 0.0, 4)
+    assert iters == 4 and st == orc.WARN_CG_MAXIT
+    # one CG step from V=0 is the preconditioned steepest-descent step
+    V1, it1, _, _ = orc.pcg(A, Gam, G, 1e-3, 0.0, 1)
+    Z = [g @ orc.precond_inv(Gam[n, n], 1e-3)[0] for n, g in enumerate(G)]
+    Rr = [-g for g in G]
+    Zr = [-z for z in Z]
+    HZ = orc.matvec(A, Gam, Zr, 1e-3)
+    alpha = sum(np.sum(r * z) for r, z in zip(Rr, Zr)) / sum(np.sum(z * h) for z, h in zip(Zr, HZ))
+    for v, z in zip(V1, Zr):
+        np.testing.assert_allclose(v, alpha * z, rtol=1e-12, atol=1e-15)
+
+
+def test_pcg_printed_beta_differs(orc):
+    """The ratio printed for beta in Algorithm 2 differs from standard PCG; the
+    oracle keeps both (beta_kind) and the library follows standard PCG."""
+    dims, R = (6, 5, 4), 3
+    A = _rand_factors(dims, R, 20)
+    X = _rand_tensor(dims, 20)
+    Gam = orc.gamma(orc.gram(A))
+    G, _ = orc.gradient(A, Gam, orc.mttkrp(X, A))
+    Vs, _, _, _ = orc.pcg(A, Gam, G, 1e-2, 0.0, 3, 0)
+    Vp, _, _, _ = orc.pcg(A, Gam, G, 1e-2, 0.0, 3, 1)
+    assert max(np.abs(a - b).max() for a, b in zip(Vs, Vp)) > 1e-6
+
+
+# ------------------------------------------------------------------ lambda rule
+
+def test_lambda_schedule_golden(orc):
+    for lam0, lo, hi, mu, seq in cpref.load_lambda_golden(os.path.join(GOLDEN, "lambda_schedule.txt")):
+        lam, d = lam0, 0
+        got = []
+        for _ in seq:
+            got.append(lam)
+            lam, d = orc.lambda_next(lam, d, lo, hi, mu)
+        np.testing.assert_allclose(got, seq, rtol=1e-15)
+
+
+# ---------------------------------------------------------------------- GN step
+
+def test_gn_exact_recovery(orc):
+    """Algorithm 1 recovers exact rank-5 decompositions of 20^3 Gaussian tensors
+    to relative residual <= 1e-10 (Section 5.3's exact-CP setting)."""
+    converged = 0
+    for seed in range(4):
+        p = datagen.workload("exact20", seed=seed)
+        X, A = p["X"], p["init"]
+        hi, lo = orc.default_lambda(A)
+        lam, d = hi, 0
+        r = 1.0
+        for _ in range(100):
+            A, lam, d, s, st = orc.gn_step(X, A, lam, d, lo, hi, 2.0, 1e-3, 250)
+            assert st in (orc.OK, orc.WARN_CG_MAXIT)
+            r = orc.residual(X, A)
+            if r <= 1e-10:
+                break
+        converged += r <= 1e-10
+    assert converged == 4
+
+
+def test_gn_step_stats(orc):
+    p = datagen.workload("exact20", seed=1)
+    X, A = p["X"], p["init"]
+    Gam = orc.gamma(orc.gram(A))
+    M = orc.mttkrp(X, A)
+    _, gn = orc.gradient(A, Gam, M)
+    A1, lam, d, s, st = orc.gn_step(X, A, 1.0, 0, 1e-3, 1.0, 2.0, 0.0, 5)
+    assert s["cg_iters"] == 5 and st == orc.WARN_CG_MAXIT
+    assert abs(s["grad_norm_sum"] - gn.sum()) <= 1e-12 * gn.sum()
+    assert s["lam_used"] == 1.0 and lam == 0.5 and d == 0
+    V, _, _, _ = orc.pcg(A, Gam, orc.gradient(A, Gam, M)[0], 1.0, 0.0, 5)
+    for a1, a, v in zip(A1, A, V):
+        np.testing.assert_allclose(a1, a + v, rtol=1e-13, atol=1e-14)
+
+
+# --------------------------------------------------------------------- residual
+
+def test_residual(orc):
+    dims, R = (9, 8, 7), 4
+    A = _rand_factors(dims, R, 21)
+    X0 = cpref.reconstruct(A)
+    assert orc.residual(X0, A) <= 1e-15
+    E = np.random.default_rng(22).standard_normal(dims)
+    eta = 1e-3
+    X = X0 + eta * np.linalg.norm(X0) * E / np.linalg.norm(E)
+    r = orc.residual(X, A)
+    ref = np.linalg.norm(X - X0) / np.linalg.norm(X)
+    assert abs(r - ref) <= 1e-12 * ref
+    assert abs(r - eta) <= 2e-3 * eta
+    B = _rand_factors(dims, R, 23)
+    ref = np.linalg.norm(X - cpref.reconstruct(B)) / np.linalg.norm(X)
+    assert abs(orc.residual(X, B) - ref) <= 1e-13 * ref
+
+
+# -------------------------------------------------------------------------- ALS
+
+def test_als_monotone_and_normal_equations(orc):
+    """ALS decreases the objective monotonically (Section 1) and, right after
+    mode n is updated, its gradient block vanishes (the normal equations)."""
+    dims, R = (8, 7, 6), 3
+    X = _rand_tensor(dims, 24)
+    A = _rand_factors(dims, R, 25)
+    f_prev = cpref.objective(X, A)
+    for _ in range(8):
+        A, st = orc.als_sweep(X, A)
+        assert st == orc.OK
+        f = cpref.objective(X, A)
+        assert f <= f_prev * (1 + 1e-14)
+        f_prev = f
+        # the last mode was updated last: its gradient block is zero
+        Gam = orc.gamma(orc.gram(A))
+        G, gn = orc.gradient(A, Gam, orc.mttkrp(X, A))
+        Mn = np.linalg.norm(orc.mttkrp(X, A)[2])
+        assert gn[2] <= 1e-12 * Mn
+
+
+def test_als_regularised(orc):
+    """With lam > 0 the mode update solves A (Gamma + lam I) = M."""
+    dims, R = (6, 5, 7), 3
+    X = _rand_tensor(dims, 26)
+    A = _rand_factors(dims, R, 27)
+    lam = 0.3
+    A1, _ = orc.als_sweep(X, A, lam)
+    # mode 0 was updated with the original factors of modes 1, 2
+    Gam0 = (A[1].T @ A[1]) * (A[2].T @ A[2])
+    M0 = _einsum_mttkrp(X, A, 0)
+    np.testing.assert_allclose(A1[0] @ (Gam0 + lam * np.eye(R)), M0, rtol=1e-11, atol=1e-12)
