@@ -1,0 +1,212 @@
+/*
+ * cpgn.h -- C ABI of the GB300 (sm_103a) Gauss-Newton CP decomposition library.
+ *
+ * Method: Singh, Ma, Yang, Solomonik, "Comparison of Accuracy and Scalability
+ * of Gauss-Newton and Alternating Least Squares for CP Decomposition" (2019).
+ * Section, equation and algorithm numbers below refer to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - X is a dense order-N tensor s_1 x ... x s_N, C-contiguous (mode N is the
+ *    fastest index), element type cp_desc.x_dtype, in DEVICE memory.
+ *  - Factor-like arguments (A, M, W, Q, G) are passed as a HOST array of N
+ *    DEVICE pointers; pointer n addresses a row-major s_n x R matrix of
+ *    doubles (R contiguous).
+ *  - The caller owns every buffer it passes.  The library never frees or
+ *    retains caller memory beyond the call.  The handle owns its device
+ *    workspace (grown on demand with cudaMalloc, freed by cp_destroy) and a
+ *    cache of split-precision copies of X keyed by (pointer, size, version).
+ *  - Outputs must not alias inputs (CP_ERR_ARG).
+ *  - All device work is enqueued on the handle's stream (cp_set_stream;
+ *    default: the legacy default stream).  Calls that return host scalars or
+ *    statistics synchronise that stream before returning, and say so.
+ *  - Argument errors are returned before any work is enqueued.  Errors found
+ *    on the device (non-SPD pivot, non-finite value, CG breakdown, barrier
+ *    timeout) are returned by the synchronising call that observes them.
+ *  - Supported: 2 <= N <= CP_MAX_ORDER, 1 <= R <= CP_MAX_RANK, every s_n >= 1.
+ */
+#ifndef CPGN_H
+#define CPGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CP_MAX_ORDER 8
+#define CP_MAX_RANK 1024
+
+typedef enum {
+    CP_OK = 0,
+    CP_ERR_ARG = 1,          /* invalid argument (shape, pointer, aliasing, dtype) */
+    CP_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    CP_ERR_NOMEM = 3,        /* workspace allocation failed */
+    CP_ERR_UNSUPPORTED = 4,  /* valid but not supported by this build/path */
+    CP_ERR_NOT_SPD = 5,      /* Gamma^(n,n) + lambda I has a non-positive Cholesky pivot */
+    CP_ERR_NONFINITE = 6,    /* a NaN/Inf appeared in a gradient or CG scalar */
+    CP_ERR_BREAKDOWN = 7,    /* CG curvature <W, (J^T J + lambda I) W> <= 0 */
+    CP_ERR_TIMEOUT = 8,      /* a device-side grid barrier exceeded its spin limit */
+    CP_WARN_CG_MAXIT = 9     /* CG stopped at its iteration cap (result still applied) */
+} cp_status;
+
+typedef enum { CP_F32 = 0, CP_F64 = 1 } cp_dtype;
+
+/* Arithmetic of the MTTKRP (and of the CG vectors in cp_gn_step):
+ *  CP_PREC_FP64    FP64 everywhere (the plain path);
+ *  CP_PREC_BF16X3  MTTKRP on tcgen05 tensor cores with each operand split into
+ *                  bf16 high/low parts (hi*hi + hi*lo + lo*hi, FP32
+ *                  accumulation); CG vectors and matvec in FP32; Gram, Gamma,
+ *                  gradient, preconditioner, dot products, norms, alpha/beta
+ *                  and the residual stay FP64. */
+typedef enum { CP_PREC_FP64 = 0, CP_PREC_BF16X3 = 1 } cp_precision;
+
+typedef struct cp_handle_s* cp_handle;
+
+typedef struct {
+    int order;                     /* N */
+    int rank;                      /* R */
+    int64_t dims[CP_MAX_ORDER];    /* s_1 .. s_N */
+    cp_dtype x_dtype;              /* element type of X */
+    uint64_t x_version;            /* bump when the contents of X change (split cache key) */
+} cp_desc;
+
+/* Parameters of one Gauss-Newton step (Algorithm 1) and its CG solve
+ * (Algorithm 2).  lam / lam_dir are in/out: cp_gn_step uses lam for this
+ * step and then advances it by the varying rule of Section 3.2. */
+typedef struct {
+    double eps_cg;        /* CG stop: sum_n ||R^(n)||_F <= eps_cg sum_n ||G^(n)||_F (paper: 1e-3) */
+    int cg_max_iter;      /* CG iteration cap (>= 0) */
+    double lam;           /* lambda of this step (in), of the next step (out) */
+    double lam_lo;        /* lower threshold of the varying rule */
+    double lam_hi;        /* upper threshold of the varying rule */
+    double mu;            /* factor mu > 1 of the varying rule */
+    int lam_dir;          /* 0: decreasing, 1: increasing (in/out) */
+    int lam_fixed;        /* 1: keep lam constant (constant regularisation) */
+    cp_precision prec;    /* MTTKRP arithmetic */
+    int cg_fp32;          /* 1: CG vectors and the matvec in FP32 (dot products, norms, alpha,
+                             beta stay FP64); 0: FP64 */
+    int want_residual;    /* 1: also return the direct FP64 relative residual after the update */
+    double stop_stationarity; /* > 0: if sum||G||/sum||M|| <= this at the entry point, apply no
+                                 update and report stats.stopped = 1 (Algorithm 1's loop test) */
+    int64_t spin_limit;   /* grid-barrier spin limit in polls; 0 selects the default (~seconds) */
+} cp_gn_params;
+
+typedef struct {
+    int status;              /* cp_status of the step */
+    int cg_iters;            /* CG iterations performed */
+    int stopped;             /* 1: the stationarity test held at entry; no update was applied */
+    double grad_norm_sum;    /* sum_n ||G^(n)||_F at the entry point (FP64) */
+    double m_norm_sum;       /* sum_n ||M^(n)||_F at the entry point */
+    double update_norm_sum;  /* sum_n ||V^(n)||_F of the applied update */
+    double factor_norm_sum;  /* sum_n ||A^(n)||_F after the update */
+    double lam_used;         /* lambda used by this step */
+    double cg_rnorm;         /* final sum_n ||R^(n)||_F of CG */
+    double rel_residual;     /* ||X - [[A]]||_F / ||X||_F after the update, or -1 */
+} cp_gn_stats;
+
+/* Human-readable name of a status code (static storage). */
+const char* cp_status_string(cp_status s);
+
+/* Create a handle bound to CUDA device `device`.  Allocates nothing on the
+ * device yet.  Errors: CP_ERR_ARG (null out-pointer, bad device), CP_ERR_CUDA. */
+cp_status cp_create(cp_handle* out, int device);
+
+/* Free the handle and all of its workspace.  Synchronises its stream. */
+cp_status cp_destroy(cp_handle h);
+
+/* Enqueue all later work of `h` on `stream` (a cudaStream_t; NULL = default). */
+cp_status cp_set_stream(cp_handle h, void* stream);
+
+/* Bytes of handle-owned device workspace a call pattern on `desc` needs at
+ * precision `prec` (excluding the split-X cache, which is reported by
+ * *split_bytes when non-null). */
+cp_status cp_workspace_size(cp_handle h, const cp_desc* desc, cp_precision prec, size_t* bytes,
+                            size_t* split_bytes);
+
+/* All-mode MTTKRP, M^(n) = X_(n) P^(n) for n = 1..N, with P^(n) the Khatri-Rao
+ * product of all factors but A^(n) (Section 2.2, Eq. (2.1); the
+ * "main computational bottleneck").  Evaluated as a dimension tree in one
+ * pass over X: for every index m of the middle modes 2..N-1, the two
+ * first-level contractions Y_m = X(:,m,:) A^(N) and Z_m = X(:,m,:)^T A^(1)
+ * are formed and folded into every M^(n).
+ * A: host array of N device pointers (s_n x R doubles, read).
+ * M: host array of N device pointers (s_n x R doubles, overwritten).
+ * Asynchronous.  Errors: CP_ERR_ARG, CP_ERR_NOMEM, CP_ERR_CUDA. */
+cp_status cp_mttkrp_all(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
+                        double* const* M, cp_precision prec);
+
+/* Gradient of f (Eq. (2.3)) through Algorithm 1's gradient line:
+ * G^(n) = A^(n) Gamma^(n,n) - M^(n), with M from cp_mttkrp_all at `prec`.
+ * Also returns, in host memory, gnorm[n] = ||G^(n)||_F and mnorm[n] =
+ * ||M^(n)||_F (either may be NULL).  Synchronises. */
+cp_status cp_gradient(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
+                      double* const* G, cp_precision prec, double* gnorm, double* mnorm);
+
+/* Implicit Gauss-Newton matvec of Algorithm 2 (Eq. (3.4)):
+ * Q^(n) = lambda W^(n) + W^(n) Gamma^(n,n) + sum_{p != n} A^(n) (Gamma^(n,p) * Y^(p))^T,
+ * Y^(p) = A^(p)^T W^(p), i.e. Q = (J^T J + lambda I) W with J the Jacobian of
+ * Eq. (3.1).  FP64.  Gamma is formed from A inside the call.
+ * Asynchronous.  Errors: CP_ERR_ARG, CP_ERR_NOMEM, CP_ERR_CUDA. */
+cp_status cp_gn_matvec(cp_handle h, const cp_desc* desc, const double* const* A, const double* const* W,
+                       double lambda, double* const* Q);
+
+/* One CP-GN iteration (Algorithm 1 loop body): MTTKRP, Gram/Gamma, gradient,
+ * preconditioner (Gamma^(n,n) + lambda I)^{-1} (Cholesky then explicit
+ * inverse, Section 3.3), CP-CG (Algorithm 2, standard PCG beta) as one
+ * persistent device kernel, then A^(n) += V^(n) in place, then lambda
+ * advances (unless lam_fixed).  A is in/out.  Synchronises; fills *stats
+ * (host, may be NULL).  Returns the step's status: CP_OK, CP_WARN_CG_MAXIT
+ * (update applied), or an error (A unchanged for CP_ERR_NOT_SPD,
+ * CP_ERR_NONFINITE; unspecified for CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT). */
+cp_status cp_gn_step(cp_handle h, const cp_desc* desc, const void* X, double* const* A,
+                     cp_gn_params* params, cp_gn_stats* stats);
+
+/* Options of cp_gn_solve (a host loop over cp_gn_step). */
+typedef struct {
+    int max_iters;           /* GN iteration cap */
+    double target_residual;  /* stop when the direct relative residual <= this (<= 0: unused) */
+    double target_stationarity; /* stop when sum||G||/sum||M|| (FP64 gradient) <= this (<= 0: unused) */
+    double refine_below;     /* BF16X3 only: switch the MTTKRP to FP64 once the low-precision
+                                stationarity falls below this (<= 0: never) */
+    int residual_every;      /* evaluate the residual every k iterations (0: only when targeted) */
+} cp_solve_opts;
+
+typedef struct {
+    int status;
+    int iters;               /* GN iterations performed */
+    int iters_refined;       /* of which with an FP64 MTTKRP */
+    int cg_iters_total;
+    int converged;           /* 1 if a target was met */
+    double stationarity;     /* last sum||G||/sum||M|| */
+    double rel_residual;     /* last residual evaluated, or -1 */
+    double lam;              /* lambda after the last step */
+} cp_solve_result;
+
+/* Run Algorithm 1 from the factors in A (in/out) until a target of `opts` is
+ * met or max_iters steps have run.  params is in/out as in cp_gn_step.
+ * Synchronises. */
+cp_status cp_gn_solve(cp_handle h, const cp_desc* desc, const void* X, double* const* A,
+                      cp_gn_params* params, const cp_solve_opts* opts, cp_solve_result* result);
+
+/* One CP-ALS sweep (Section 2.2): for n = 1..N in order,
+ * A^(n) <- M^(n) (Gamma^(n) + lambda I)^{-1} with M^(n) = X_(n) P^(n) formed
+ * from the factors already updated in this sweep; the inverse is built from
+ * the Cholesky factor.  lambda = 0 is plain ALS.  A is in/out.  If
+ * rel_residual is non-null, the direct FP64 residual after the sweep is
+ * written there (synchronises); otherwise asynchronous. */
+cp_status cp_als_sweep(cp_handle h, const cp_desc* desc, const void* X, double* const* A, double lambda,
+                       cp_precision prec, double* rel_residual);
+
+/* Relative residual r = ||X - [[A]]||_F / ||X||_F (Section 5), with the
+ * reconstruction formed element by element in FP64 and both squared sums
+ * accumulated in FP64.  Writes the host scalar; synchronises. */
+cp_status cp_residual(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
+                      double* rel_residual);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPGN_H */

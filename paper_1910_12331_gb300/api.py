@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libcpgn.so (include/cpgn.h), same call names.
+
+Argument marshalling only: torch tensors are passed as raw device pointers
+plus shapes; every step runs in the library's CUDA kernels.  The library is
+loaded on first use; if it is missing the call raises (there is no CPU
+fallback).  All device work is enqueued on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+MAX_ORDER = 8
+
+CP_OK, CP_ERR_ARG, CP_ERR_CUDA, CP_ERR_NOMEM, CP_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+CP_ERR_NOT_SPD, CP_ERR_NONFINITE, CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT, CP_WARN_CG_MAXIT = 5, 6, 7, 8, 9
+CP_F32, CP_F64 = 0, 1
+CP_PREC_FP64, CP_PREC_BF16X3 = 0, 1
+PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3}
+
+SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
+           "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
+           "cp_residual")
+
+
+class cp_desc(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("rank", ctypes.c_int), ("dims", ctypes.c_int64 * MAX_ORDER),
+                ("x_dtype", ctypes.c_int), ("x_version", ctypes.c_uint64)]
+
+
+class cp_gn_params(ctypes.Structure):
+    _fields_ = [("eps_cg", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("lam", ctypes.c_double),
+                ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double), ("mu", ctypes.c_double),
+                ("lam_dir", ctypes.c_int), ("lam_fixed", ctypes.c_int), ("prec", ctypes.c_int),
+                ("cg_fp32", ctypes.c_int), ("want_residual", ctypes.c_int),
+                ("stop_stationarity", ctypes.c_double), ("spin_limit", ctypes.c_int64)]
+
+
+class cp_gn_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cg_iters", ctypes.c_int), ("stopped", ctypes.c_int),
+                ("grad_norm_sum", ctypes.c_double), ("m_norm_sum", ctypes.c_double),
+                ("update_norm_sum", ctypes.c_double), ("factor_norm_sum", ctypes.c_double),
+                ("lam_used", ctypes.c_double), ("cg_rnorm", ctypes.c_double), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cp_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("target_residual", ctypes.c_double),
+                ("target_stationarity", ctypes.c_double), ("refine_below", ctypes.c_double),
+                ("residual_every", ctypes.c_int)]
+
+
+class cp_solve_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("iters_refined", ctypes.c_int),
+                ("cg_iters_total", ctypes.c_int), ("converged", ctypes.c_int), ("stationarity", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("lam", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CPError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libcpgn.so.  Raises if it is missing (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError(f"libcpgn.so not built ({_build.LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        pd = ctypes.POINTER(cp_desc)
+        L.cp_status_string.argtypes = [i]
+        L.cp_status_string.restype = ctypes.c_char_p
+        L.cp_create.argtypes = [ctypes.POINTER(vp), i]
+        L.cp_destroy.argtypes = [vp]
+        L.cp_set_stream.argtypes = [vp, vp]
+        L.cp_workspace_size.argtypes = [vp, pd, i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+        L.cp_mttkrp_all.argtypes = [vp, pd, vp, vp, vp, i]
+        L.cp_gradient.argtypes = [vp, pd, vp, vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.cp_gn_matvec.argtypes = [vp, pd, vp, vp, d, vp]
+        L.cp_gn_step.argtypes = [vp, pd, vp, vp, ctypes.POINTER(cp_gn_params), ctypes.POINTER(cp_gn_stats)]
+        L.cp_gn_solve.argtypes = [vp, pd, vp, vp, ctypes.POINTER(cp_gn_params), ctypes.POINTER(cp_solve_opts),
+                                  ctypes.POINTER(cp_solve_result)]
+        L.cp_als_sweep.argtypes = [vp, pd, vp, vp, d, i, ctypes.POINTER(d)]
+        L.cp_residual.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d)]
+        for name in SYMBOLS:
+            if name != "cp_status_string":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def status_string(s: int) -> str:
+    return load().cp_status_string(int(s)).decode()
+
+
+def _check(s, where, ok=(CP_OK,)):
+    if s not in ok:
+        raise CPError(s, where)
+    return s
+
+
+# --------------------------------------------------------------------- marshalling
+
+def make_desc(shape, rank, x_dtype, version=0) -> cp_desc:
+    d = cp_desc()
+    d.order = len(shape)
+    d.rank = int(rank)
+    for k, s in enumerate(shape):
+        d.dims[k] = int(s)
+    d.x_dtype = CP_F32 if x_dtype == torch.float32 else CP_F64
+    d.x_version = int(version)
+    return d
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for k, t in enumerate(tensors):
+        arr[k] = t.data_ptr()
+    return arr
+
+
+def _check_factor(t, rows, rank, name):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == (rows, rank)):
+        raise ValueError(f"{name}: expected contiguous CUDA float64 tensor of shape ({rows}, {rank})")
+
+
+def _check_x(X):
+    if not (X.is_cuda and X.dtype in (torch.float32, torch.float64) and X.is_contiguous()):
+        raise ValueError("X: expected a contiguous CUDA float32/float64 tensor")
+
+
+class Handle:
+    """Owns a cp_handle bound to a CUDA device; work goes to torch's current stream."""
+
+    def __init__(self, device=None):
+        L = load()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev.index if dev.index is not None else torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        _check(L.cp_create(ctypes.byref(h), self.device), "cp_create")
+        self.h = h
+        self._version = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().cp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        load().cp_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def desc(self, X, rank):
+        _check_x(X)
+        return make_desc(X.shape, rank, X.dtype, self._version.get(X.data_ptr(), 0))
+
+    def bump_version(self, X):
+        """Declare that the contents of X changed (invalidates the split cache)."""
+        self._version[X.data_ptr()] = self._version.get(X.data_ptr(), 0) + 1
+
+
+def _factors(X, A):
+    if len(A) != X.dim():
+        raise ValueError("need one factor per mode")
+    R = A[0].shape[1]
+    for n, a in enumerate(A):
+        _check_factor(a, X.shape[n], R, f"A[{n}]")
+    return R
+
+
+def cp_workspace_size(h: Handle, X, rank, prec="fp64"):
+    d = h.desc(X, rank)
+    b, sb = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().cp_workspace_size(h.h, ctypes.byref(d), PREC[prec], ctypes.byref(b), ctypes.byref(sb)),
+           "cp_workspace_size")
+    return b.value, sb.value
+
+
+def cp_mttkrp_all(h: Handle, X, A, M=None, prec="fp64"):
+    R = _factors(X, A)
+    if M is None:
+        M = [torch.empty_like(a) for a in A]
+    for n, m in enumerate(M):
+        _check_factor(m, X.shape[n], R, f"M[{n}]")
+    h._bind_stream()
+    d = h.desc(X, R)
+    _check(load().cp_mttkrp_all(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), _ptr_array(M), PREC[prec]),
+           "cp_mttkrp_all")
+    return M
+
+
+def cp_gradient(h: Handle, X, A, G=None, prec="fp64"):
+    R = _factors(X, A)
+    if G is None:
+        G = [torch.empty_like(a) for a in A]
+    h._bind_stream()
+    d = h.desc(X, R)
+    N = X.dim()
+    gn, mn = (ctypes.c_double * N)(), (ctypes.c_double * N)()
+    _check(load().cp_gradient(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), _ptr_array(G), PREC[prec],
+                              gn, mn), "cp_gradient")
+    return G, list(gn), list(mn)
+
+
+def cp_gn_matvec(h: Handle, A, W, lam, Q=None):
+    R = A[0].shape[1]
+    shape = [a.shape[0] for a in A]
+    for n in range(len(A)):
+        _check_factor(A[n], shape[n], R, f"A[{n}]")
+        _check_factor(W[n], shape[n], R, f"W[{n}]")
+    if Q is None:
+        Q = [torch.empty_like(a) for a in A]
+    h._bind_stream()
+    d = make_desc(shape, R, torch.float64)
+    _check(load().cp_gn_matvec(h.h, ctypes.byref(d), _ptr_array(A), _ptr_array(W), float(lam), _ptr_array(Q)),
+           "cp_gn_matvec")
+    return Q
+
+
+def gn_params(lam, lam_lo, lam_hi, mu=2.0, eps_cg=1e-3, cg_max_iter=250, prec="fp64", cg_fp32=None,
+              lam_dir=0, lam_fixed=False, want_residual=False, stop_stationarity=0.0, spin_limit=0):
+    p = cp_gn_params()
+    p.eps_cg, p.cg_max_iter = float(eps_cg), int(cg_max_iter)
+    p.lam, p.lam_lo, p.lam_hi, p.mu = float(lam), float(lam_lo), float(lam_hi), float(mu)
+    p.lam_dir, p.lam_fixed = int(lam_dir), int(bool(lam_fixed))
+    p.prec = PREC[prec]
+    p.cg_fp32 = int(prec != "fp64") if cg_fp32 is None else int(bool(cg_fp32))
+    p.want_residual = int(bool(want_residual))
+    p.stop_stationarity = float(stop_stationarity)
+    p.spin_limit = int(spin_limit)
+    return p
+
+
+def cp_gn_step(h: Handle, X, A, params: cp_gn_params, check=True):
+    """One GN iteration; A (list of float64 CUDA tensors) is updated in place.
+    Returns (status, stats dict); params.lam / lam_dir advance in place."""
+    R = _factors(X, A)
+    h._bind_stream()
+    d = h.desc(X, R)
+    st = cp_gn_stats()
+    s = load().cp_gn_step(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(params), ctypes.byref(st))
+    if check:
+        _check(s, "cp_gn_step", ok=(CP_OK, CP_WARN_CG_MAXIT))
+    return s, st.as_dict()
+
+
+def solve_opts(max_iters=200, target_residual=0.0, target_stationarity=0.0, refine_below=0.0, residual_every=0):
+    o = cp_solve_opts()
+    o.max_iters, o.target_residual, o.target_stationarity = int(max_iters), float(target_residual), \
+        float(target_stationarity)
+    o.refine_below, o.residual_every = float(refine_below), int(residual_every)
+    return o
+
+
+def cp_gn_solve(h: Handle, X, A, params: cp_gn_params, opts: cp_solve_opts, check=True):
+    R = _factors(X, A)
+    h._bind_stream()
+    d = h.desc(X, R)
+    res = cp_solve_result()
+    s = load().cp_gn_solve(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(params),
+                           ctypes.byref(opts), ctypes.byref(res))
+    if check:
+        _check(s, "cp_gn_solve")
+    return s, res.as_dict()
+
+
+def cp_als_sweep(h: Handle, X, A, lam=0.0, prec="fp64", want_residual=True):
+    R = _factors(X, A)
+    h._bind_stream()
+    d = h.desc(X, R)
+    r = ctypes.c_double(-1.0)
+    _check(load().cp_als_sweep(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), float(lam), PREC[prec],
+                               ctypes.byref(r) if want_residual else None), "cp_als_sweep")
+    return r.value
+
+
+def cp_residual(h: Handle, X, A):
+    R = _factors(X, A)
+    h._bind_stream()
+    d = h.desc(X, R)
+    r = ctypes.c_double()
+    _check(load().cp_residual(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(r)), "cp_residual")
+    return r.value

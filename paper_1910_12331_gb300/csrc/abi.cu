@@ -1,0 +1,550 @@
+// abi.cu -- the C ABI of include/cpgn.h: argument checks, handle-owned
+// workspace, and the orchestration of the kernels of one GN step
+// (Algorithm 1), one ALS sweep, the MTTKRP, the matvec and the residual.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cpgn.h"
+#include "kernels.hpp"
+#include "tc.hpp"
+
+using namespace cpgn;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr long long kDefaultSpin = 1LL << 24;  // polls (with 64 ns sleeps: about a second or more)
+
+}  // namespace
+
+struct cp_handle_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch;
+    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y;
+    DevStats* h_stats = nullptr;  // pinned
+    SplitCache split;             // bf16 planes of X (tensor-core path)
+};
+
+static cp_status grow(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return CP_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return CP_ERR_NOMEM;
+    }
+    b.bytes = bytes;
+    return CP_OK;
+}
+
+#define CP_TRY(x)                           \
+    do {                                    \
+        cp_status _s = (x);                 \
+        if (_s != CP_OK) return _s;         \
+    } while (0)
+
+#define CUDA_TRY(x)                                  \
+    do {                                             \
+        if ((x) != cudaSuccess) {                    \
+            cudaGetLastError();                      \
+            return CP_ERR_CUDA;                      \
+        }                                            \
+    } while (0)
+
+static cp_status check_desc(const cp_desc* d) {
+    if (!d) return CP_ERR_ARG;
+    if (d->order < 2 || d->order > CP_MAX_ORDER) return CP_ERR_ARG;
+    if (d->rank < 1 || d->rank > CP_MAX_RANK) return CP_ERR_ARG;
+    if (d->x_dtype != CP_F32 && d->x_dtype != CP_F64) return CP_ERR_ARG;
+    double total = 1.0;
+    for (int n = 0; n < d->order; ++n) {
+        if (d->dims[n] < 1 || d->dims[n] > (1LL << 31)) return CP_ERR_ARG;
+        total *= (double)d->dims[n];
+    }
+    if (total > 9.0e15) return CP_ERR_ARG;
+    int64_t mid = 1;
+    for (int n = 1; n + 1 < d->order; ++n) mid *= d->dims[n];
+    if (mid > 0x7fffffffLL) return CP_ERR_UNSUPPORTED;  // grid.x limit of the slice kernels
+    return CP_OK;
+}
+
+static cp_status check_ptrs(const void* const* P, int n) {
+    if (!P) return CP_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!P[i]) return CP_ERR_ARG;
+    return CP_OK;
+}
+
+// no output pointer may coincide with an input pointer
+static bool aliased(const void* const* out, int nout, const void* const* in, int nin, const void* X) {
+    for (int i = 0; i < nout; ++i) {
+        if (out[i] == X) return true;
+        for (int j = 0; j < nin; ++j)
+            if (out[i] == in[j]) return true;
+        for (int j = 0; j < i; ++j)
+            if (out[i] == out[j]) return true;
+    }
+    return false;
+}
+
+template <typename T>
+static Ptrs<T> ptrs_of(T* const* p, int N) {
+    Ptrs<T> r{};
+    for (int n = 0; n < N; ++n) r.p[n] = p[n];
+    return r;
+}
+
+template <typename T>
+static Ptrs<T> packed_ptrs(T* base, const Shape& s) {
+    Ptrs<T> r{};
+    for (int n = 0; n < s.N; ++n) r.p[n] = base + s.roff[n] * s.R;
+    return r;
+}
+
+static Ptrs<const double> as_const(Ptrs<double> p) {
+    Ptrs<const double> r{};
+    for (int n = 0; n < kMaxN; ++n) r.p[n] = p.p[n];
+    return r;
+}
+
+static cp_status ensure_common(cp_handle h, const Shape& s) {
+    const size_t RR = (size_t)s.R * s.R;
+    const size_t rows = (size_t)s.roff[s.N];
+    CP_TRY(grow(h->gram_part, (size_t)s.N * gram_chunks(s) * RR * sizeof(double)));
+    CP_TRY(grow(h->S, s.N * RR * sizeof(double)));
+    CP_TRY(grow(h->Gam, (size_t)s.N * s.N * RR * sizeof(double)));
+    CP_TRY(grow(h->GamF, (size_t)s.N * s.N * RR * sizeof(float)));
+    CP_TRY(grow(h->Pinv, s.N * RR * sizeof(double)));
+    CP_TRY(grow(h->PinvF, s.N * RR * sizeof(float)));
+    if (precond_smem_bytes(s.R) == 0) CP_TRY(grow(h->precond_scratch, 2 * s.N * RR * sizeof(double)));
+    CP_TRY(grow(h->Mp, rows * s.R * sizeof(double)));
+    CP_TRY(grow(h->Gp, rows * s.R * sizeof(double)));
+    CP_TRY(grow(h->stats, sizeof(DevStats)));
+    if (!h->h_stats) CUDA_TRY(cudaMallocHost((void**)&h->h_stats, sizeof(DevStats)));
+    return CP_OK;
+}
+
+static cp_status sync_stats(cp_handle h) {
+    CUDA_TRY(cudaMemcpyAsync(h->h_stats, h->stats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return CP_OK;
+}
+
+// M (caller or packed pointers) = all-mode MTTKRP of X at `prec`.
+static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
+                             Ptrs<double> M, cp_precision prec) {
+    for (int n = 0; n < s.N; ++n)
+        CUDA_TRY(cudaMemsetAsync(M.p[n], 0, (size_t)s.dims[n] * s.R * sizeof(double), h->stream));
+    if (prec == CP_PREC_FP64) {
+        launch_mttkrp_f64(s, d->x_dtype, X, A, M, (1u << s.N) - 1u, h->stream);
+    } else if (prec == CP_PREC_BF16X3) {
+        CP_TRY(tc_mttkrp_all(h->split, d, s, X, A, M, h->stream));
+    } else {
+        return CP_ERR_ARG;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return CP_OK;
+}
+
+// S, Gamma (FP64) and the float copy of Gamma.
+static cp_status gram_gamma(cp_handle h, const Shape& s, Ptrs<const double> A) {
+    const int chunks = gram_chunks(s);
+    launch_gram_partial(s, A, (double*)h->gram_part.p, chunks, h->stream);
+    launch_gamma(s, (const double*)h->gram_part.p, chunks, (double*)h->S.p, (double*)h->Gam.p, (float*)h->GamF.p,
+                 h->stream);
+    CUDA_TRY(cudaGetLastError());
+    return CP_OK;
+}
+
+extern "C" {
+
+const char* cp_status_string(cp_status s) {
+    switch (s) {
+        case CP_OK: return "CP_OK";
+        case CP_ERR_ARG: return "CP_ERR_ARG";
+        case CP_ERR_CUDA: return "CP_ERR_CUDA";
+        case CP_ERR_NOMEM: return "CP_ERR_NOMEM";
+        case CP_ERR_UNSUPPORTED: return "CP_ERR_UNSUPPORTED";
+        case CP_ERR_NOT_SPD: return "CP_ERR_NOT_SPD";
+        case CP_ERR_NONFINITE: return "CP_ERR_NONFINITE";
+        case CP_ERR_BREAKDOWN: return "CP_ERR_BREAKDOWN";
+        case CP_ERR_TIMEOUT: return "CP_ERR_TIMEOUT";
+        case CP_WARN_CG_MAXIT: return "CP_WARN_CG_MAXIT";
+    }
+    return "CP_UNKNOWN_STATUS";
+}
+
+cp_status cp_create(cp_handle* out, int device) {
+    if (!out) return CP_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return CP_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return CP_ERR_ARG;
+    cp_handle h = new (std::nothrow) cp_handle_s();
+    if (!h) return CP_ERR_NOMEM;
+    h->device = device;
+    *out = h;
+    return CP_OK;
+}
+
+cp_status cp_destroy(cp_handle h) {
+    if (!h) return CP_ERR_ARG;
+    {
+        DeviceGuard g(h->device);
+        cudaStreamSynchronize(h->stream);
+        DevBuf* bufs[] = {&h->gram_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
+                          &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
+                          &h->stats, &h->Y};
+        for (DevBuf* b : bufs)
+            if (b->p) cudaFree(b->p);
+        if (h->h_stats) cudaFreeHost(h->h_stats);
+        split_cache_free(h->split);
+        cudaGetLastError();
+    }
+    delete h;
+    return CP_OK;
+}
+
+cp_status cp_set_stream(cp_handle h, void* stream) {
+    if (!h) return CP_ERR_ARG;
+    h->stream = (cudaStream_t)stream;
+    return CP_OK;
+}
+
+cp_status cp_workspace_size(cp_handle h, const cp_desc* d, cp_precision prec, size_t* bytes, size_t* split_bytes) {
+    if (!h || !bytes) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    const Shape s = make_shape(d);
+    const size_t RR = (size_t)s.R * s.R, rows = (size_t)s.roff[s.N];
+    size_t b = 0;
+    b += (size_t)s.N * gram_chunks(s) * RR * 8 + s.N * RR * 8 + (size_t)s.N * s.N * RR * 12 + s.N * RR * 12;
+    b += rows * s.R * 8 * 2;                    // M, G
+    b += rows * s.R * 8 * 7;                    // packed A and CG vectors (FP64 worst case)
+    b += (size_t)4096 * RR * 8 + s.N * RR * 8;  // partial A^T W per block, T
+    *bytes = b;
+    if (split_bytes) *split_bytes = prec == CP_PREC_BF16X3 ? split_cache_bytes(d) : 0;
+    return CP_OK;
+}
+
+cp_status cp_mttkrp_all(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* const* M,
+                        cp_precision prec) {
+    if (!h || !X) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    CP_TRY(check_ptrs((const void* const*)M, d->order));
+    if (aliased((const void* const*)M, d->order, (const void* const*)A, d->order, X)) return CP_ERR_ARG;
+    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    return mttkrp_into(h, d, s, X, ptrs_of(A, s.N), ptrs_of(M, s.N), prec);
+}
+
+cp_status cp_gradient(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* const* G,
+                      cp_precision prec, double* gnorm, double* mnorm) {
+    if (!h || !X) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    CP_TRY(check_ptrs((const void* const*)G, d->order));
+    if (aliased((const void* const*)G, d->order, (const void* const*)A, d->order, X)) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    CP_TRY(ensure_common(h, s));
+    const Ptrs<const double> Ap = ptrs_of(A, s.N);
+    CUDA_TRY(cudaMemsetAsync(h->stats.p, 0, sizeof(DevStats), h->stream));
+    CP_TRY(mttkrp_into(h, d, s, X, Ap, packed_ptrs((double*)h->Mp.p, s), prec));
+    CP_TRY(gram_gamma(h, s, Ap));
+    launch_gradient(s, Ap, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
+                    (DevStats*)h->stats.p, h->stream);
+    launch_unpack(s, (const double*)h->Gp.p, ptrs_of(G, s.N), h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CP_TRY(sync_stats(h));
+    for (int n = 0; n < s.N; ++n) {
+        if (gnorm) gnorm[n] = sqrt(h->h_stats->gnorm2[n]);
+        if (mnorm) mnorm[n] = sqrt(h->h_stats->mnorm2[n]);
+    }
+    return h->h_stats->status ? (cp_status)h->h_stats->status : CP_OK;
+}
+
+cp_status cp_gn_matvec(cp_handle h, const cp_desc* d, const double* const* A, const double* const* W, double lambda,
+                       double* const* Q) {
+    if (!h) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    CP_TRY(check_ptrs((const void* const*)W, d->order));
+    CP_TRY(check_ptrs((const void* const*)Q, d->order));
+    if (aliased((const void* const*)Q, d->order, (const void* const*)A, d->order, nullptr)) return CP_ERR_ARG;
+    if (aliased((const void* const*)Q, d->order, (const void* const*)W, d->order, nullptr)) return CP_ERR_ARG;
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    CP_TRY(ensure_common(h, s));
+    CP_TRY(grow(h->Y, (size_t)s.N * s.R * s.R * sizeof(double)));
+    const Ptrs<const double> Ap = ptrs_of(A, s.N);
+    CP_TRY(gram_gamma(h, s, Ap));
+    launch_matvec_f64(s, Ap, (const double*)h->Gam.p, ptrs_of(W, s.N), lambda, ptrs_of(Q, s.N), (double*)h->Y.p,
+                      h->stream);
+    CUDA_TRY(cudaGetLastError());
+    return CP_OK;
+}
+
+}  // extern "C"
+
+static void lambda_advance(cp_gn_params* p) {
+    if (p->lam_fixed) return;
+    if (p->lam_dir == 0) {
+        const double t = p->lam / p->mu;
+        if (t < p->lam_lo) {
+            p->lam_dir = 1;
+            p->lam = p->lam * p->mu;
+        } else {
+            p->lam = t;
+        }
+    } else {
+        const double t = p->lam * p->mu;
+        if (t > p->lam_hi) {
+            p->lam_dir = 0;
+            p->lam = p->lam / p->mu;
+        } else {
+            p->lam = t;
+        }
+    }
+}
+
+template <typename T>
+static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller, const cp_gn_params* p) {
+    const size_t RR = (size_t)s.R * s.R, len = (size_t)s.roff[s.N] * s.R;
+    CP_TRY(grow(h->Ap, len * sizeof(T)));
+    CP_TRY(grow(h->vec, 5 * len * sizeof(T)));
+    CP_TRY(grow(h->Ypart, (size_t)4096 * RR * sizeof(T)));
+    CP_TRY(grow(h->Tm, s.N * RR * sizeof(T)));
+    CP_TRY(grow(h->pcg_part, 3 * 4096 * sizeof(double)));
+    CP_TRY(grow(h->bar, sizeof(GridBarrier)));
+    launch_pack<T>(s, Acaller, (T*)h->Ap.p, h->stream);
+    PcgArgs<T> a{};
+    a.s = s;
+    a.Ap = (const T*)h->Ap.p;
+    if (sizeof(T) == 4) {
+        a.GamT = (const T*)h->GamF.p;
+        a.PinvT = (const T*)h->PinvF.p;
+    } else {
+        a.GamT = (const T*)h->Gam.p;
+        a.PinvT = (const T*)h->Pinv.p;
+    }
+    a.G = (const double*)h->Gp.p;
+    T* v = (T*)h->vec.p;
+    a.V = v;
+    a.Rv = v + len;
+    a.Z = v + 2 * len;
+    a.W = v + 3 * len;
+    a.Q = v + 4 * len;
+    a.Ypart = (T*)h->Ypart.p;
+    a.Tm = (T*)h->Tm.p;
+    a.part = (double*)h->pcg_part.p;
+    a.bar = (GridBarrier*)h->bar.p;
+    a.stats = (DevStats*)h->stats.p;
+    a.lam = p->lam;
+    a.eps_cg = p->eps_cg;
+    a.stop_ratio = p->stop_stationarity;
+    a.maxit = p->cg_max_iter;
+    a.spin_limit = p->spin_limit > 0 ? p->spin_limit : kDefaultSpin;
+    CUDA_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(GridBarrier), h->stream));
+    CP_TRY(launch_pcg<T>(a, 0, h->stream));
+    return CP_OK;
+}
+
+static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, double* const* A, cp_gn_params* p,
+                              cp_gn_stats* st) {
+    const Shape s = make_shape(d);
+    CP_TRY(ensure_common(h, s));
+    const Ptrs<const double> Ac = ptrs_of((const double* const*)A, s.N);
+    DevStats* ds = (DevStats*)h->stats.p;
+    CUDA_TRY(cudaMemsetAsync(ds, 0, sizeof(DevStats), h->stream));
+    // Algorithm 1: MTTKRP, Gamma^(n,p), G^(n) = A^(n) Gamma^(n,n) - M^(n)
+    CP_TRY(mttkrp_into(h, d, s, X, Ac, packed_ptrs((double*)h->Mp.p, s), p->prec));
+    CP_TRY(gram_gamma(h, s, Ac));
+    launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p, ds, h->stream);
+    // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
+    launch_precond(s, (const double*)h->Gam.p, p->lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
+                   (double*)h->precond_scratch.p, ds, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    if (p->cg_fp32)
+        CP_TRY(gn_pcg<float>(h, s, Ac, p));
+    else
+        CP_TRY(gn_pcg<double>(h, s, Ac, p));
+    // A^(n) += V^(n)
+    Ptrs<double> Am = ptrs_of(A, s.N);
+    if (p->cg_fp32)
+        launch_update<float>(s, Am, (const float*)h->vec.p, ds, h->stream);
+    else
+        launch_update<double>(s, Am, (const double*)h->vec.p, ds, h->stream);
+    if (p->want_residual) launch_residual_f64(s, d->x_dtype, X, as_const(Am), ds, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CP_TRY(sync_stats(h));
+    const DevStats& hs = *h->h_stats;
+    cp_status status = (cp_status)hs.status;
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->status = status;
+        st->cg_iters = hs.cg_iters;
+        st->stopped = hs.stopped;
+        for (int n = 0; n < s.N; ++n) {
+            st->grad_norm_sum += sqrt(hs.gnorm2[n]);
+            st->m_norm_sum += sqrt(hs.mnorm2[n]);
+            st->update_norm_sum += sqrt(hs.vnorm2[n]);
+            st->factor_norm_sum += sqrt(hs.anorm2[n]);
+        }
+        st->lam_used = p->lam;
+        st->cg_rnorm = hs.cg_rnorm;
+        st->rel_residual = p->want_residual ? sqrt(hs.res_num) / sqrt(hs.res_den) : -1.0;
+    }
+    if ((status == CP_OK || status == CP_WARN_CG_MAXIT) && !hs.stopped) lambda_advance(p);
+    return status;
+}
+
+static cp_status check_params(const cp_gn_params* p) {
+    if (!p) return CP_ERR_ARG;
+    if (!(p->eps_cg >= 0.0) || p->cg_max_iter < 0) return CP_ERR_ARG;
+    if (!(p->lam >= 0.0) || !isfinite(p->lam)) return CP_ERR_ARG;
+    if (!p->lam_fixed && !(p->mu > 1.0 && p->lam_lo > 0.0 && p->lam_hi >= p->lam_lo)) return CP_ERR_ARG;
+    if (p->prec != CP_PREC_FP64 && p->prec != CP_PREC_BF16X3) return CP_ERR_ARG;
+    return CP_OK;
+}
+
+extern "C" {
+
+cp_status cp_gn_step(cp_handle h, const cp_desc* d, const void* X, double* const* A, cp_gn_params* p,
+                     cp_gn_stats* st) {
+    if (!h || !X) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    CP_TRY(check_params(p));
+    if (aliased((const void* const*)A, d->order, nullptr, 0, X)) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    return gn_step_impl(h, d, X, A, p, st);
+}
+
+cp_status cp_gn_solve(cp_handle h, const cp_desc* d, const void* X, double* const* A, cp_gn_params* p,
+                      const cp_solve_opts* o, cp_solve_result* res) {
+    if (!h || !X || !o || !res) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    CP_TRY(check_params(p));
+    if (o->max_iters < 0) return CP_ERR_ARG;
+    if (aliased((const void* const*)A, d->order, nullptr, 0, X)) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    memset(res, 0, sizeof(*res));
+    res->rel_residual = -1.0;
+    const cp_precision base_prec = p->prec;
+    bool refining = base_prec == CP_PREC_FP64;
+    cp_status status = CP_OK;
+    for (int it = 0; it < o->max_iters; ++it) {
+        cp_gn_params q = *p;
+        q.prec = refining ? CP_PREC_FP64 : base_prec;
+        // Algorithm 1's loop test on sum||G||: only trusted with an FP64-accurate gradient
+        q.stop_stationarity = refining ? o->target_stationarity : 0.0;
+        const bool resid_now = o->target_residual > 0.0 || (o->residual_every > 0 && (it + 1) % o->residual_every == 0);
+        q.want_residual = resid_now ? 1 : 0;
+        cp_gn_stats st;
+        status = gn_step_impl(h, d, X, A, &q, &st);
+        p->lam = q.lam;
+        p->lam_dir = q.lam_dir;
+        res->cg_iters_total += st.cg_iters;
+        res->stationarity = st.m_norm_sum > 0 ? st.grad_norm_sum / st.m_norm_sum : 0.0;
+        if (status != CP_OK && status != CP_WARN_CG_MAXIT) break;
+        if (st.stopped) {  // no update was applied: the entry point met the target
+            res->converged = 1;
+            break;
+        }
+        ++res->iters;
+        if (q.prec == CP_PREC_FP64 && base_prec != CP_PREC_FP64) ++res->iters_refined;
+        if (resid_now) res->rel_residual = st.rel_residual;
+        if (o->target_residual > 0.0 && st.rel_residual <= o->target_residual) {
+            res->converged = 1;
+            break;
+        }
+        if (!refining && o->refine_below > 0.0 && res->stationarity <= o->refine_below) refining = true;
+    }
+    res->lam = p->lam;
+    res->status = status;
+    return status == CP_WARN_CG_MAXIT ? CP_OK : status;
+}
+
+cp_status cp_als_sweep(cp_handle h, const cp_desc* d, const void* X, double* const* A, double lambda,
+                       cp_precision prec, double* rel_residual) {
+    if (!h || !X) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return CP_ERR_ARG;
+    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3) return CP_ERR_ARG;
+    if (aliased((const void* const*)A, d->order, nullptr, 0, X)) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    CP_TRY(ensure_common(h, s));
+    DevStats* ds = (DevStats*)h->stats.p;
+    CUDA_TRY(cudaMemsetAsync(ds, 0, sizeof(DevStats), h->stream));
+    const Ptrs<const double> Ac = ptrs_of((const double* const*)A, s.N);
+    Ptrs<double> Mp = packed_ptrs((double*)h->Mp.p, s);
+    for (int n = 0; n < s.N; ++n) {
+        CP_TRY(gram_gamma(h, s, Ac));
+        CUDA_TRY(cudaMemsetAsync(Mp.p[n], 0, (size_t)s.dims[n] * s.R * sizeof(double), h->stream));
+        if (prec == CP_PREC_FP64)
+            launch_mttkrp_f64(s, d->x_dtype, X, Ac, Mp, 1u << n, h->stream);
+        else
+            CP_TRY(tc_mttkrp_mode(h->split, d, s, X, Ac, Mp, n, h->stream));
+        launch_precond(s, (const double*)h->Gam.p, lambda, (double*)h->Pinv.p, nullptr,
+                       (double*)h->precond_scratch.p, ds, h->stream);
+        launch_als_solve(s, n, Mp.p[n], (const double*)h->Pinv.p + (size_t)n * s.R * s.R, A[n], h->stream);
+        CUDA_TRY(cudaGetLastError());
+    }
+    if (rel_residual) {
+        launch_residual_f64(s, d->x_dtype, X, Ac, ds, h->stream);
+        CP_TRY(sync_stats(h));
+        *rel_residual = sqrt(h->h_stats->res_num) / sqrt(h->h_stats->res_den);
+        if (h->h_stats->status) return (cp_status)h->h_stats->status;
+    }
+    return CP_OK;
+}
+
+cp_status cp_residual(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* rel_residual) {
+    if (!h || !X || !rel_residual) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    CP_TRY(grow(h->stats, sizeof(DevStats)));
+    if (!h->h_stats) CUDA_TRY(cudaMallocHost((void**)&h->h_stats, sizeof(DevStats)));
+    CUDA_TRY(cudaMemsetAsync(h->stats.p, 0, sizeof(DevStats), h->stream));
+    launch_residual_f64(s, d->x_dtype, X, ptrs_of(A, s.N), (DevStats*)h->stats.p, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CP_TRY(sync_stats(h));
+    *rel_residual = sqrt(h->h_stats->res_num) / sqrt(h->h_stats->res_den);
+    return CP_OK;
+}
+
+}  // extern "C"

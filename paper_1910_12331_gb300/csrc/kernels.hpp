@@ -1,0 +1,81 @@
+// kernels.hpp -- host-side launchers of the CP-GN kernels (one definition per .cu file).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace cpgn {
+
+Shape make_shape(const cp_desc* d);
+
+// ---- small dense kernels (k_dense.cu) ----------------------------------------
+// Gram partial sums over row chunks: part[n][chunk][R][R]; returns chunk count per mode in *chunks.
+int gram_chunks(const Shape& s);
+void launch_gram_partial(const Shape& s, Ptrs<const double> A, double* part, int chunks, cudaStream_t st);
+// S[n] = sum of partials; Gam[n][p] = prod_{m != n,p} S[m]; GamF = float copy (may be null).
+void launch_gamma(const Shape& s, const double* part, int chunks, double* S, double* Gam, float* GamF,
+                  cudaStream_t st);
+// G^(n) = A^(n) Gam[n][n] - M^(n) (packed G, packed M); norms into stats.
+void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
+                     DevStats* stats, cudaStream_t st);
+// Pinv[n] = (Gam[n][n] + lam I)^{-1} (FP64 Cholesky + inverse); PinvF float copy (may be null).
+// scratch: N*2*R*R doubles, used only when precond_smem_bytes(R) == 0.
+void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv, float* PinvF, double* scratch,
+                    DevStats* stats, cudaStream_t st);
+size_t precond_smem_bytes(int R);
+// Packed copy of the factors in T.
+template <typename T>
+void launch_pack(const Shape& s, Ptrs<const double> A, T* Ap, cudaStream_t st);
+// A^(n) += V^(n) (V packed in T); ||V^(n)||^2 and ||A^(n)||^2 into stats.
+template <typename T>
+void launch_update(const Shape& s, Ptrs<double> A, const T* V, DevStats* stats, cudaStream_t st);
+// ALS mode update: A^(n) = M^(n) Pinv^(n) (M packed rows of mode n).
+void launch_als_solve(const Shape& s, int n, const double* Mn, const double* Pinv_n, double* An, cudaStream_t st);
+// Copy packed rows of mode n to a caller pointer set (FP64).
+void launch_unpack(const Shape& s, const double* packed, Ptrs<double> out, cudaStream_t st);
+
+// ---- FP64 SIMT MTTKRP (k_mttkrp_f64.cu) -----------------------------------------
+// Accumulates (atomically) into M; M must be zeroed first.  mode_mask selects
+// which modes are produced (bit n = mode n).
+void launch_mttkrp_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, Ptrs<double> M,
+                       unsigned mode_mask, cudaStream_t st);
+
+// ---- implicit matvec and persistent PCG (k_pcg.cu) --------------------------------
+template <typename T>
+struct PcgArgs {
+    Shape s;
+    const T* Ap;        // packed factors
+    const T* GamT;      // N*N*R*R Gamma in T
+    const T* PinvT;     // N*R*R preconditioner in T
+    const double* G;    // packed FP64 gradient
+    T* V; T* Rv; T* Z; T* W; T* Q;   // packed CG vectors
+    T* Ypart;           // [nblocks][R*R] per-block partial A^T W
+    T* Tm;              // N*R*R: T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p)
+    double* part;       // [4][nblocks] per-block partial scalars
+    GridBarrier* bar;
+    DevStats* stats;
+    double lam;
+    double eps_cg;
+    double stop_ratio;  // > 0: no CG iteration when sum||G|| <= stop_ratio sum||M||
+    int maxit;
+    long long spin_limit;
+    int nblocks;
+    // Row ownership: blocks never straddle modes.  Mode n owns blocks
+    // [mode_blk0[n], mode_blk0[n+1]); its block j owns rows
+    // [j * rpb[n], min(s_n, (j+1) * rpb[n])) of A^(n).
+    int mode_blk0[kMaxN + 1];
+    int rpb[kMaxN];
+};
+template <typename T>
+cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st);
+// Plain (non-persistent) FP64 matvec used by cp_gn_matvec: Q = (J^T J + lam I) W.
+void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
+                       Ptrs<double> Q, double* Y, cudaStream_t st);
+
+// ---- residual (k_residual.cu) ------------------------------------------------------
+void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,
+                         cudaStream_t st);
+
+}  // namespace cpgn

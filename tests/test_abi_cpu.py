@@ -1,0 +1,87 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every call the
+header declares; host-side logic that needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(cp_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1910_12331_gb300 import build
+
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_calls():
+    names = _declared()
+    for n in ("cp_mttkrp_all", "cp_gn_matvec", "cp_gn_step", "cp_als_sweep", "cp_residual"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_1910_12331_gb300 import api
+
+    assert set(api.SYMBOLS) <= set(_declared())
+
+
+def test_status_strings(lib):
+    lib.cp_status_string.restype = ctypes.c_char_p
+    assert lib.cp_status_string(0) == b"CP_OK"
+    assert lib.cp_status_string(8) == b"CP_ERR_TIMEOUT"
+    assert lib.cp_status_string(123) == b"CP_UNKNOWN_STATUS"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    # argument checks run before any CUDA call
+    lib.cp_mttkrp_all.restype = ctypes.c_int
+    assert lib.cp_mttkrp_all(None, None, None, None, None, 0) == 1
+    lib.cp_residual.restype = ctypes.c_int
+    assert lib.cp_residual(None, None, None, None, None) == 1
+    lib.cp_create.restype = ctypes.c_int
+    assert lib.cp_create(None, 0) == 1
+
+
+def test_struct_layouts_match_header():
+    """The ctypes mirrors of the header structs have the C sizes (checked with gcc)."""
+    import subprocess
+    import tempfile
+
+    from paper_1910_12331_gb300 import api
+
+    prog = r"""
+#include <stdio.h>
+#include "cpgn.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(cp_desc), sizeof(cp_gn_params), sizeof(cp_gn_stats),
+         sizeof(cp_solve_opts), sizeof(cp_solve_result));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "s.c"), os.path.join(d, "s")
+        open(src, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        sizes = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
+    mine = [ctypes.sizeof(c) for c in (api.cp_desc, api.cp_gn_params, api.cp_gn_stats, api.cp_solve_opts,
+                                       api.cp_solve_result)]
+    assert sizes == mine
