@@ -161,7 +161,8 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
     if (prec == CP_PREC_FP64) {
         launch_mttkrp_f64(s, d->x_dtype, X, A, M, (1u << s.N) - 1u, h->stream);
     } else if (prec == CP_PREC_BF16X3) {
-        CP_TRY(tc_mttkrp_all(h->split, d, s, X, A, M, h->stream));
+        CP_TRY(grow(h->stats, sizeof(DevStats)));
+        CP_TRY(tc_mttkrp_all(h->split, d, s, X, A, M, &((DevStats*)h->stats.p)->status, h->stream));
     } else {
         return CP_ERR_ARG;
     }
@@ -516,7 +517,7 @@ cp_status cp_als_sweep(cp_handle h, const cp_desc* d, const void* X, double* con
         if (prec == CP_PREC_FP64)
             launch_mttkrp_f64(s, d->x_dtype, X, Ac, Mp, 1u << n, h->stream);
         else
-            CP_TRY(tc_mttkrp_mode(h->split, d, s, X, Ac, Mp, n, h->stream));
+            CP_TRY(tc_mttkrp_mode(h->split, d, s, X, Ac, Mp, n, &ds->status, h->stream));
         launch_precond(s, (const double*)h->Gam.p, lambda, (double*)h->Pinv.p, nullptr,
                        (double*)h->precond_scratch.p, ds, h->stream);
         launch_als_solve(s, n, Mp.p[n], (const double*)h->Pinv.p + (size_t)n * s.R * s.R, A[n], h->stream);

@@ -16,6 +16,8 @@
 // reductions (dot products, norms) are FP64 and are summed by every block in
 // the same fixed order, so every block takes the same alpha, beta and stop
 // decision.  Vectors are FP64 (plain path) or FP32 (mixed path).
+#include <stdlib.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -26,6 +28,10 @@ namespace cpgn {
 namespace {
 constexpr int kThreads = 256;
 
+// a * b + c with one rounding, in the precision of T (no promotion to double)
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 struct Smem {
     T* G;   // Gamma^(n,n), R x R (or a global pointer)
@@ -35,6 +41,22 @@ struct Smem {
     T* V; T* Rv; T* Z; T* W; T* Q;
     double* red;
 };
+
+// sum_{c in [c0, c1)} v[c], computed by warp 0 with lane-strided loads and a
+// shuffle tree (a fixed order, identical in every block) and broadcast to the
+// whole block through shared memory.
+__device__ __forceinline__ double block_gather_sum(const double* v, int c0, int c1, double* bcast) {
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        for (int c = c0 + (int)threadIdx.x; c < c1; c += 32) acc += __ldcg(&v[c]);
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) *bcast = acc;
+    }
+    __syncthreads();
+    const double r = *bcast;
+    __syncthreads();
+    return r;
+}
 
 template <typename T>
 __device__ __forceinline__ double dsum_rows(const T* x, const T* y, int len, double* red) {
@@ -50,7 +72,8 @@ __device__ __forceinline__ void rows_times(const T* in, const T* M, T* out, int 
         const int k = e / R, r = e % R;
         const T* a = in + k * R;
         T acc = 0;
-        for (int z = 0; z < R; ++z) acc = fma(a[z], M[z * R + r], acc);
+#pragma unroll 4
+        for (int z = 0; z < R; ++z) acc = fmadd(a[z], M[z * R + r], acc);
         out[e] = acc;
     }
 }
@@ -61,7 +84,8 @@ __device__ __forceinline__ void y_partial(const T* A, const T* W, T* Yp, int row
     for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
         const int r = q / R, z = q % R;
         T acc = 0;
-        for (int k = 0; k < rows; ++k) acc = fma(A[k * R + r], W[k * R + z], acc);
+#pragma unroll 4
+        for (int k = 0; k < rows; ++k) acc = fmadd(A[k * R + r], W[k * R + z], acc);
         Yp[q] = acc;
     }
 }
@@ -142,15 +166,11 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
     int it = 0;
     double rsum = 0.0, rz = 0.0;
     bool ok = grid_sync(a.bar, status, nb, lim);
+    double* const bcast = sm.red + 40;
     auto reduce_r = [&](double& rz_out, double& rsum_out) {
-        double t = 0.0, tot = 0.0;
-        for (int c = 0; c < (int)nb; ++c) t += ldcg(&part_rz[c]);
-        for (int m = 0; m < N; ++m) {
-            double q = 0.0;
-            for (int c = a.mode_blk0[m]; c < a.mode_blk0[m + 1]; ++c) q += ldcg(&part_rn[c]);
-            tot += sqrt(q);
-        }
-        rz_out = t;
+        rz_out = block_gather_sum(part_rz, 0, (int)nb, bcast);
+        double tot = 0.0;
+        for (int m = 0; m < N; ++m) tot += sqrt(block_gather_sum(part_rn, a.mode_blk0[m], a.mode_blk0[m + 1], bcast));
         rsum_out = tot;
     };
     if (ok) reduce_r(rz, rsum);
@@ -162,19 +182,37 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         if (!(rsum > tol)) break;
         if (!isfinite(rsum) || !isfinite(rz)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
-        // ---- T phase: T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed
-        for (int64_t e = (int64_t)b * blockDim.x + threadIdx.x; e < (int64_t)N * RR;
-             e += (int64_t)nb * blockDim.x) {
-            const int nn = (int)(e / RR), q = (int)(e % RR);
-            const int r = q / R, z = q % R;
-            T acc = 0;
-            for (int p = 0; p < N; ++p) {
-                if (p == nn) continue;
-                T y = 0;
-                for (int c = a.mode_blk0[p]; c < a.mode_blk0[p + 1]; ++c) y += ldcg(&a.Ypart[(int64_t)c * RR + q]);
-                acc = fma(a.GamT[((int64_t)nn * N + p) * RR + q], y, acc);
+        // ---- T phase: T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed.
+        // One warp per entry q: the lanes split the per-block partials of every
+        // Y^(p)_q, a shuffle reduction completes them, lane n forms T^(n)_q.
+        {
+            const int lane = threadIdx.x & 31;
+            const int64_t gw = ((int64_t)b * blockDim.x + threadIdx.x) >> 5;
+            const int64_t nw = ((int64_t)nb * blockDim.x) >> 5;
+            for (int64_t q = gw; q < RR; q += nw) {
+                T y[kMaxN];
+#pragma unroll
+                for (int p = 0; p < kMaxN; ++p) {
+                    if (p >= N) break;
+                    T acc = 0;
+                    for (int c = a.mode_blk0[p] + lane; c < a.mode_blk0[p + 1]; c += 32)
+                        acc += ldcg(&a.Ypart[(int64_t)c * RR + q]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    y[p] = acc;
+                }
+                if (lane < N) {
+                    const int nn = lane;
+                    T t = 0;
+#pragma unroll
+                    for (int p = 0; p < kMaxN; ++p) {
+                        if (p >= N) break;
+                        if (p != nn) t = fmadd(a.GamT[((int64_t)nn * N + p) * RR + q], y[p], t);
+                    }
+                    const int r = (int)(q / R), z = (int)(q % R);
+                    a.Tm[(int64_t)nn * RR + z * R + r] = t;
+                }
             }
-            a.Tm[(int64_t)nn * RR + z * R + r] = acc;
         }
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         // ---- Q phase: Q = lam W + W Gamma^(n,n) + A T^(n)^T
@@ -187,9 +225,17 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
             const T* w = sm.W + k * R;
             const T* ar = sm.A + k * R;
             T acc = lam * w[r];
-            for (int z = 0; z < R; ++z) {
-                acc = fma(w[z], sm.G[z * R + r], acc);
-                acc = fma(ar[z], stage_mats ? sm.Tt[z * R + r] : ldcg(&sm.Tt[z * R + r]), acc);
+            if (stage_mats) {
+#pragma unroll 4
+                for (int z = 0; z < R; ++z) {
+                    acc = fmadd(w[z], sm.G[z * R + r], acc);
+                    acc = fmadd(ar[z], sm.Tt[z * R + r], acc);
+                }
+            } else {
+                for (int z = 0; z < R; ++z) {
+                    acc = fmadd(w[z], sm.G[z * R + r], acc);
+                    acc = fmadd(ar[z], ldcg(&sm.Tt[z * R + r]), acc);
+                }
             }
             sm.Q[e] = acc;
         }
@@ -197,15 +243,14 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         const double wq_p = dsum_rows(sm.W, sm.Q, len, sm.red);
         if (threadIdx.x == 0) part_wq[b] = wq_p;
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
-        double wq = 0.0;
-        for (int c = 0; c < (int)nb; ++c) wq += ldcg(&part_wq[c]);
+        const double wq = block_gather_sum(part_wq, 0, (int)nb, bcast);
         if (!isfinite(wq)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (!(wq > 0.0)) { set_status(status, CP_ERR_BREAKDOWN); break; }
         const double alpha = rz / wq;
         const T al = (T)alpha;
         for (int e = threadIdx.x; e < len; e += blockDim.x) {
-            sm.V[e] = fma(al, sm.W[e], sm.V[e]);
-            sm.Rv[e] = fma(-al, sm.Q[e], sm.Rv[e]);
+            sm.V[e] = fmadd(al, sm.W[e], sm.V[e]);
+            sm.Rv[e] = fmadd(-al, sm.Q[e], sm.Rv[e]);
         }
         __syncthreads();
         rows_times(sm.Rv, sm.P, sm.Z, rows, R);
@@ -222,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         const double beta = rz_new / rz;
         rz = rz_new;
         const T be = (T)beta;
-        for (int e = threadIdx.x; e < len; e += blockDim.x) sm.W[e] = fma(be, sm.W[e], sm.Z[e]);
+        for (int e = threadIdx.x; e < len; e += blockDim.x) sm.W[e] = fmadd(be, sm.W[e], sm.Z[e]);
         __syncthreads();
         y_partial(sm.A, sm.W, a.Ypart + (int64_t)b * RR, rows, R);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
@@ -247,7 +292,13 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t rows_total = s.roff[s.N];
-    int target = std::max(s.N, std::min<int>(max_blocks > 0 ? max_blocks : sms, (int)std::min<int64_t>(rows_total, 4096)));
+    // FP64 vectors: the work is DFMA-bound, spread it over every SM.  FP32
+    // vectors: the iteration is latency-bound, so use fewer, fatter blocks
+    // (about 32 rows each) to shorten the barriers and reductions.
+    int want = max_blocks > 0 ? max_blocks
+                              : (sizeof(T) == 8 ? sms : (int)std::min<int64_t>(sms, (rows_total + 31) / 32));
+    if (const char* env = getenv(sizeof(T) == 8 ? "CPGN_PCG_BLOCKS_F64" : "CPGN_PCG_BLOCKS_F32")) want = atoi(env);
+    int target = std::max(s.N, std::min<int>(want, (int)std::min<int64_t>(rows_total, 4096)));
     // choose the blocks per mode so that the smem of the largest block fits
     const size_t budget = 200 * 1024;
     for (int attempt = 0; attempt < 64; ++attempt) {

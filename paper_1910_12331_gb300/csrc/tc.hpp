@@ -25,10 +25,11 @@ struct SplitCache {
 size_t split_cache_bytes(const cp_desc* d);
 void split_cache_free(SplitCache& c);
 // All-mode MTTKRP on tensor cores (bf16x3): M zeroed by the caller.
+// status: device word that receives CP_ERR_TIMEOUT if a bounded wait expires.
 cp_status tc_mttkrp_all(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
-                        Ptrs<double> M, cudaStream_t st);
+                        Ptrs<double> M, int* status, cudaStream_t st);
 // Single mode n (ALS) on tensor cores: M.p[n] zeroed by the caller.
 cp_status tc_mttkrp_mode(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
-                         Ptrs<double> M, int n, cudaStream_t st);
+                         Ptrs<double> M, int n, int* status, cudaStream_t st);
 
 }  // namespace cpgn
