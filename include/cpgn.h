@@ -104,6 +104,10 @@ typedef struct {
     double lam_used;         /* lambda used by this step */
     double cg_rnorm;         /* final sum_n ||R^(n)||_F of CG */
     double rel_residual;     /* ||X - [[A]]||_F / ||X||_F after the update, or -1 */
+    double mttkrp_ms;        /* device time of the MTTKRP phase (CUDA events) */
+    double pcg_ms;           /* device time of the CG kernel */
+    double step_ms;          /* device time of the whole step */
+    int kernel_launches;     /* kernels this step launched */
 } cp_gn_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -182,6 +186,10 @@ typedef struct {
     double stationarity;     /* last sum||G||/sum||M|| */
     double rel_residual;     /* last residual evaluated, or -1 */
     double lam;              /* lambda after the last step */
+    double mttkrp_ms;        /* summed device time of the MTTKRP phases */
+    double pcg_ms;           /* summed device time of the CG kernels */
+    double device_ms;        /* summed device time of all steps */
+    long long kernel_launches; /* kernels launched by the solve */
 } cp_solve_result;
 
 /* Run Algorithm 1 from the factors in A (in/out) until a target of `opts` is

@@ -45,7 +45,9 @@ class cp_gn_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("cg_iters", ctypes.c_int), ("stopped", ctypes.c_int),
                 ("grad_norm_sum", ctypes.c_double), ("m_norm_sum", ctypes.c_double),
                 ("update_norm_sum", ctypes.c_double), ("factor_norm_sum", ctypes.c_double),
-                ("lam_used", ctypes.c_double), ("cg_rnorm", ctypes.c_double), ("rel_residual", ctypes.c_double)]
+                ("lam_used", ctypes.c_double), ("cg_rnorm", ctypes.c_double), ("rel_residual", ctypes.c_double),
+                ("mttkrp_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -60,7 +62,8 @@ class cp_solve_opts(ctypes.Structure):
 class cp_solve_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("iters_refined", ctypes.c_int),
                 ("cg_iters_total", ctypes.c_int), ("converged", ctypes.c_int), ("stationarity", ctypes.c_double),
-                ("rel_residual", ctypes.c_double), ("lam", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("lam", ctypes.c_double), ("mttkrp_ms", ctypes.c_double),
+                ("pcg_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

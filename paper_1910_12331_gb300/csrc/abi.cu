@@ -44,7 +44,18 @@ struct cp_handle_s {
     DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y;
     DevStats* h_stats = nullptr;  // pinned
     SplitCache split;             // bf16 planes of X (tensor-core path)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
+    int launches = 0;             // kernels launched by the current call
 };
+
+static cp_status ensure_events(cp_handle h) {
+    for (auto& e : h->ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return CP_ERR_CUDA;
+        }
+    return CP_OK;
+}
 
 static cp_status grow(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -160,7 +171,9 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         CUDA_TRY(cudaMemsetAsync(M.p[n], 0, (size_t)s.dims[n] * s.R * sizeof(double), h->stream));
     if (prec == CP_PREC_FP64) {
         launch_mttkrp_f64(s, d->x_dtype, X, A, M, (1u << s.N) - 1u, h->stream);
+        h->launches += 2;
     } else if (prec == CP_PREC_BF16X3) {
+        h->launches += tc_launch_count(h->split, d, s);
         CP_TRY(grow(h->stats, sizeof(DevStats)));
         CP_TRY(tc_mttkrp_all(h->split, d, s, X, A, M, &((DevStats*)h->stats.p)->status, h->stream));
     } else {
@@ -225,6 +238,8 @@ cp_status cp_destroy(cp_handle h) {
         for (DevBuf* b : bufs)
             if (b->p) cudaFree(b->p);
         if (h->h_stats) cudaFreeHost(h->h_stats);
+        for (auto& e : h->ev)
+            if (e) cudaEventDestroy(e);
         split_cache_free(h->split);
         cudaGetLastError();
     }
@@ -347,6 +362,7 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     CP_TRY(grow(h->pcg_part, 3 * 4096 * sizeof(double)));
     CP_TRY(grow(h->bar, sizeof(GridBarrier)));
     launch_pack<T>(s, Acaller, (T*)h->Ap.p, h->stream);
+    CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
     PcgArgs<T> a{};
     a.s = s;
     a.Ap = (const T*)h->Ap.p;
@@ -383,29 +399,41 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
                               cp_gn_stats* st) {
     const Shape s = make_shape(d);
     CP_TRY(ensure_common(h, s));
+    CP_TRY(ensure_events(h));
+    h->launches = 0;
     const Ptrs<const double> Ac = ptrs_of((const double* const*)A, s.N);
     DevStats* ds = (DevStats*)h->stats.p;
+    CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
     CUDA_TRY(cudaMemsetAsync(ds, 0, sizeof(DevStats), h->stream));
     // Algorithm 1: MTTKRP, Gamma^(n,p), G^(n) = A^(n) Gamma^(n,n) - M^(n)
     CP_TRY(mttkrp_into(h, d, s, X, Ac, packed_ptrs((double*)h->Mp.p, s), p->prec));
+    CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
     CP_TRY(gram_gamma(h, s, Ac));
+    h->launches += 2;
     launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p, ds, h->stream);
     // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
     launch_precond(s, (const double*)h->Gam.p, p->lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
                    (double*)h->precond_scratch.p, ds, h->stream);
+    h->launches += 2;
     CUDA_TRY(cudaGetLastError());
     if (p->cg_fp32)
         CP_TRY(gn_pcg<float>(h, s, Ac, p));
     else
         CP_TRY(gn_pcg<double>(h, s, Ac, p));
+    h->launches += 2;  // pack + persistent CG
     // A^(n) += V^(n)
     Ptrs<double> Am = ptrs_of(A, s.N);
     if (p->cg_fp32)
         launch_update<float>(s, Am, (const float*)h->vec.p, ds, h->stream);
     else
         launch_update<double>(s, Am, (const double*)h->vec.p, ds, h->stream);
-    if (p->want_residual) launch_residual_f64(s, d->x_dtype, X, as_const(Am), ds, h->stream);
+    h->launches += 1;
+    if (p->want_residual) {
+        launch_residual_f64(s, d->x_dtype, X, as_const(Am), ds, h->stream);
+        h->launches += 1;
+    }
     CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
     CP_TRY(sync_stats(h));
     const DevStats& hs = *h->h_stats;
     cp_status status = (cp_status)hs.status;
@@ -423,6 +451,15 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
         st->lam_used = p->lam;
         st->cg_rnorm = hs.cg_rnorm;
         st->rel_residual = p->want_residual ? sqrt(hs.res_num) / sqrt(hs.res_den) : -1.0;
+        float t01 = 0.f, t23 = 0.f, t03 = 0.f;
+        cudaEventElapsedTime(&t01, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&t23, h->ev[2], h->ev[3]);
+        cudaEventElapsedTime(&t03, h->ev[0], h->ev[3]);
+        cudaGetLastError();
+        st->mttkrp_ms = t01;
+        st->pcg_ms = t23;  // CG kernel plus the factor update
+        st->step_ms = t03;
+        st->kernel_launches = h->launches;
     }
     if ((status == CP_OK || status == CP_WARN_CG_MAXIT) && !hs.stopped) lambda_advance(p);
     return status;
@@ -476,6 +513,10 @@ cp_status cp_gn_solve(cp_handle h, const cp_desc* d, const void* X, double* cons
         p->lam = q.lam;
         p->lam_dir = q.lam_dir;
         res->cg_iters_total += st.cg_iters;
+        res->mttkrp_ms += st.mttkrp_ms;
+        res->pcg_ms += st.pcg_ms;
+        res->device_ms += st.step_ms;
+        res->kernel_launches += st.kernel_launches;
         res->stationarity = st.m_norm_sum > 0 ? st.grad_norm_sum / st.m_norm_sum : 0.0;
         if (status != CP_OK && status != CP_WARN_CG_MAXIT) break;
         if (st.stopped) {  // no update was applied: the entry point met the target

@@ -72,7 +72,21 @@ struct Params {
     float* P_Z;         // [nunits][512][64]
     float* P_c;         // [nib * nkg][mid][64]
     int* status;
+    long long* trace;   // event timestamps of block 0 (trace builds only), else null
 };
+
+// Optional event trace of block 0 (compiled in with -DCPGN_TC_TRACE): slot
+// ev * 1024 + idx receives clock64() at event ev, occurrence idx.
+#ifdef CPGN_TC_TRACE
+#define TC_TRACE(ev, idx)                                                                  \
+    do {                                                                                   \
+        if (p.trace && blockIdx.x == 0 && (idx) < 1024) p.trace[(ev) * 1024 + (idx)] = clock64(); \
+    } while (0)
+#else
+#define TC_TRACE(ev, idx) \
+    do {                  \
+    } while (0)
+#endif
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -271,6 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1;
                         if (!(ok = mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1, &abort_s, p.status))) break;
+                        TC_TRACE(0, it);
                         const uint32_t fb = smem_u32(&bar_full[s]);
                         mbar_expect_tx(fb, kStageBytes);
                         const uint32_t st = s_stage0 + s * kStageBytes;
@@ -312,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = c0; c < c1; ++c, ++it) {
                         const int s = it % kStages;
                         if (!(ok = mbar_wait(smem_u32(&bar_full[s]), (it / kStages) & 1, &abort_s, p.status))) break;
+                        TC_TRACE(1, it);
                         tc_fence_after();
                         const uint32_t st = s_stage0 + s * kStageBytes;
                         // GEMM-Y: D_Y(128 i x 64 r) += X(i, k) * B_Y(k, r), k in this chunk
@@ -331,6 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // GEMM-Z needs this slice's B_Z = A^(1) * w_m
                         if (c == c0) {
                             if (!(ok = mbar_wait(smem_u32(&bar_bz_full), (uint32_t)(t & 1), &abort_s, p.status))) break;
+                            TC_TRACE(2, (int)t);
                             tc_fence_after();
                         }
                         // GEMM-Z: D_Z[c](128 k x 64 r) += X(i, k)^T * B_Z(i, r), i in this block
@@ -346,6 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             zfirst[c - c0] = false;
                         }
                         tc_commit(smem_u32(&bar_empty[s]));
+                        TC_TRACE(3, it);
                     }
                     if (!ok) break;
                     tc_commit(smem_u32(&bar_dy_full[buf]));
@@ -395,6 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int64_t tt = t0 + j, m = U.m0 + j;
                     const int wb = (int)(tt & 1);
                     if (!(ok = epi_wait(smem_u32(&bar_bz_empty), (uint32_t)((tt & 1) ^ 1)))) break;
+                    if (et == 0) TC_TRACE(4, (int)tt);
                     if (et < kRT) {
                         float w = 1.0f;
                         int64_t rem = m;
@@ -422,12 +441,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(smem_u32(&bar_bz_full));
+                    if (et == 0) TC_TRACE(5, (int)tt);
                 }
                 if (j > 0) {
                     // ---- epilogue of the previous slice: Y_m
                     const int64_t tp = t0 + j - 1, m = U.m0 + j - 1;
                     const int buf = (int)(tp & 1);
                     if (!(ok = epi_wait(smem_u32(&bar_dy_full[buf]), (uint32_t)((tp >> 1) & 1)))) break;
+                    if (et == 0) TC_TRACE(6, (int)tp);
                     tc_fence_after();
                     float y[kRT];
                     const uint32_t ta = t_dy0 + buf * kRT + ((uint32_t)(q * 32) << 16);
@@ -451,6 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         named_sync_epi();
                     }
+                    if (et == 0) TC_TRACE(7, (int)tp);
                 }
             }
             t = t0 + nsl;
@@ -603,6 +625,9 @@ static EncodeTiledFn encode_fn() {
 }
 
 static int64_t pad8(int64_t v) { return (v + 7) / 8 * 8; }
+#ifdef CPGN_TC_TRACE
+long long* tc_trace_ptr = nullptr;
+#endif
 
 }  // namespace tc
 
@@ -612,6 +637,13 @@ size_t split_cache_bytes(const cp_desc* d) {
     int64_t rows = 1;
     for (int n = 0; n + 1 < d->order; ++n) rows *= d->dims[n];
     return (size_t)(2 * rows * pad8(d->dims[d->order - 1]) * sizeof(__nv_bfloat16));
+}
+
+int tc_launch_count(const SplitCache& c, const cp_desc* d, const Shape& s) {
+    const bool hit = c.planes && c.key_ptr != nullptr && c.key_version == d->x_version && c.key_total == s.total &&
+                     c.key_dtype == (int)d->x_dtype;
+    const int tiles = (s.R + kRT - 1) / kRT;
+    return (hit ? 0 : 1) + tiles * (2 + (s.N - 2) + 2);
 }
 
 void split_cache_free(SplitCache& c) {
@@ -722,6 +754,16 @@ static cp_status tc_run(SplitCache& c, const cp_desc* d, const Shape& s, const v
     p.P_Z = (float*)(wb + off_pz);
     p.P_c = (float*)(wb + off_pc);
     p.status = status;
+    p.trace = nullptr;
+#ifdef CPGN_TC_TRACE
+    {
+        static long long* trace_buf = nullptr;
+        if (!trace_buf) cudaMalloc(&trace_buf, 8 * 1024 * sizeof(long long));
+        cudaMemsetAsync(trace_buf, 0, 8 * 1024 * sizeof(long long), st);
+        p.trace = trace_buf;
+        tc_trace_ptr = trace_buf;
+    }
+#endif
     // ---- tensor maps
     CUtensorMap tmX, tmBY;
     {
@@ -778,3 +820,11 @@ cp_status tc_mttkrp_mode(SplitCache& c, const cp_desc* d, const Shape& s, const 
 }
 
 }  // namespace cpgn
+
+#ifdef CPGN_TC_TRACE
+// trace builds only: device pointer of the last trace buffer (8 x 1024 int64)
+extern "C" int cpgn_tc_trace_copy(long long* host) {
+    if (!cpgn::tc::tc_trace_ptr) return 1;
+    return cudaMemcpy(host, cpgn::tc::tc_trace_ptr, 8 * 1024 * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess;
+}
+#endif

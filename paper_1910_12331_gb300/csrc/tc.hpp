@@ -23,6 +23,8 @@ struct SplitCache {
 };
 
 size_t split_cache_bytes(const cp_desc* d);
+// Kernels one tensor-core MTTKRP call launches (before it runs: counts the split if the cache misses).
+int tc_launch_count(const SplitCache& c, const cp_desc* d, const Shape& s);
 void split_cache_free(SplitCache& c);
 // All-mode MTTKRP on tensor cores (bf16x3): M zeroed by the caller.
 // status: device word that receives CP_ERR_TIMEOUT if a bounded wait expires.
