@@ -213,6 +213,34 @@ cp_status cp_als_sweep(cp_handle h, const cp_desc* desc, const void* X, double* 
 cp_status cp_residual(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
                       double* rel_residual);
 
+/* ---------------------------------------------------------------------------
+ * Matvec without device allocation.  The paper has no counterpart: this call
+ * serves callers that cannot call cudaMalloc -- code running under a fixed,
+ * pre-reserved device-memory budget, inside an allocator or memory-pool
+ * callback, or in a serving loop that must not allocate after start-up.
+ *
+ * Same result as cp_gn_matvec, Q = (J^T J + lambda I) W (FP64), but with no
+ * handle: the work is enqueued on `stream` (a cudaStream_t; NULL = default)
+ * of the CURRENT device, and its scratch (Gram matrices, Gamma set, A^T W)
+ * lives in one file-scope device array of CP_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.  The call allocates
+ * nothing and calls no allocating routine; the caller passes inputs and
+ * outputs (host arrays of N device pointers, s_n x R doubles each).
+ * The first call on a device looks up the array's device address (and may
+ * load the library's module); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race, so the
+ * caller must serialise them.  Each call rewrites all scratch it reads.
+ * Errors: CP_ERR_ARG (null/aliased pointers, bad shape, lambda < 0),
+ * CP_ERR_UNSUPPORTED (order > CP_NOALLOC_MAX_ORDER or rank >
+ * CP_NOALLOC_MAX_RANK: the problem does not fit the static scratch),
+ * CP_ERR_CUDA.  Asynchronous. */
+#define CP_NOALLOC_MAX_ORDER 4
+#define CP_NOALLOC_MAX_RANK 64
+#define CP_NOALLOC_SCRATCH_BYTES ((2 * CP_NOALLOC_MAX_ORDER + CP_NOALLOC_MAX_ORDER * CP_NOALLOC_MAX_ORDER) * \
+                                  CP_NOALLOC_MAX_RANK * CP_NOALLOC_MAX_RANK * 8)
+cp_status cp_gn_matvec_noalloc(const cp_desc* desc, const double* const* A, const double* const* W, double lambda,
+                               double* const* Q, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

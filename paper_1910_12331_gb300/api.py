@@ -25,7 +25,7 @@ PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3}
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
-           "cp_residual")
+           "cp_residual", "cp_gn_matvec_noalloc")
 
 
 class cp_desc(ctypes.Structure):
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = False):
                                   ctypes.POINTER(cp_solve_result)]
         L.cp_als_sweep.argtypes = [vp, pd, vp, vp, d, i, ctypes.POINTER(d)]
         L.cp_residual.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d)]
+        L.cp_gn_matvec_noalloc.argtypes = [pd, vp, vp, d, vp, vp]
         for name in SYMBOLS:
             if name != "cp_status_string":
                 getattr(L, name).restype = ctypes.c_int
@@ -315,3 +316,20 @@ def cp_residual(h: Handle, X, A):
     r = ctypes.c_double()
     _check(load().cp_residual(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(r)), "cp_residual")
     return r.value
+
+
+def cp_gn_matvec_noalloc(A, W, lam, Q):
+    """Q = (J^T J + lam I) W without any device allocation (static scratch in
+    the library; order <= 4, rank <= 64).  Q must be preallocated by the
+    caller; work goes to torch's current stream on the current device."""
+    R = A[0].shape[1]
+    shape = [a.shape[0] for a in A]
+    for n in range(len(A)):
+        _check_factor(A[n], shape[n], R, f"A[{n}]")
+        _check_factor(W[n], shape[n], R, f"W[{n}]")
+        _check_factor(Q[n], shape[n], R, f"Q[{n}]")
+    d = make_desc(shape, R, torch.float64)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(load().cp_gn_matvec_noalloc(ctypes.byref(d), _ptr_array(A), _ptr_array(W), float(lam), _ptr_array(Q),
+                                       st), "cp_gn_matvec_noalloc")
+    return Q
