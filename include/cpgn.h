@@ -60,7 +60,15 @@ typedef enum { CP_F32 = 0, CP_F64 = 1 } cp_dtype;
  *                  accumulation); CG vectors and matvec in FP32; Gram, Gamma,
  *                  gradient, preconditioner, dot products, norms, alpha/beta
  *                  and the residual stay FP64. */
-typedef enum { CP_PREC_FP64 = 0, CP_PREC_BF16X3 = 1 } cp_precision;
+/*  CP_PREC_RESIDUAL (gradient only: cp_gradient, cp_gn_step, cp_gn_solve)
+ *                  G^(n) = -E_(n) P^(n) with E = X - [[A]] the residual tensor,
+ *                  formed in double-float arithmetic (about 2^-44 relative),
+ *                  split into bf16 planes and contracted by the bf16x3
+ *                  tensor-core MTTKRP; M^(n) = A^(n) Gamma^(n,n) - G^(n).  This
+ *                  is the same gradient as Algorithm 1's A Gamma - M, but its
+ *                  error scales with |E| instead of |M|: the refinement used
+ *                  by the mixed path once the bf16x3 gradient stalls. */
+typedef enum { CP_PREC_FP64 = 0, CP_PREC_BF16X3 = 1, CP_PREC_RESIDUAL = 2 } cp_precision;
 
 typedef struct cp_handle_s* cp_handle;
 
@@ -104,6 +112,7 @@ typedef struct {
     double lam_used;         /* lambda used by this step */
     double cg_rnorm;         /* final sum_n ||R^(n)||_F of CG */
     double rel_residual;     /* ||X - [[A]]||_F / ||X||_F after the update, or -1 */
+    double entry_residual;   /* residual at the entry point (CP_PREC_RESIDUAL steps), or -1 */
     double mttkrp_ms;        /* device time of the MTTKRP phase (CUDA events) */
     double pcg_ms;           /* device time of the CG kernel */
     double step_ms;          /* device time of the whole step */
@@ -172,15 +181,16 @@ typedef struct {
     int max_iters;           /* GN iteration cap */
     double target_residual;  /* stop when the direct relative residual <= this (<= 0: unused) */
     double target_stationarity; /* stop when sum||G||/sum||M|| (FP64 gradient) <= this (<= 0: unused) */
-    double refine_below;     /* BF16X3 only: switch the MTTKRP to FP64 once the low-precision
-                                stationarity falls below this (<= 0: never) */
+    double refine_below;     /* BF16X3 only: switch the gradient to refine_prec once the
+                                low-precision stationarity falls below this (<= 0: never) */
+    cp_precision refine_prec; /* CP_PREC_RESIDUAL (default when 0 is given for BF16X3) or CP_PREC_FP64 */
     int residual_every;      /* evaluate the residual every k iterations (0: only when targeted) */
 } cp_solve_opts;
 
 typedef struct {
     int status;
     int iters;               /* GN iterations performed */
-    int iters_refined;       /* of which with an FP64 MTTKRP */
+    int iters_refined;       /* of which with the refined gradient */
     int cg_iters_total;
     int converged;           /* 1 if a target was met */
     double stationarity;     /* last sum||G||/sum||M|| */

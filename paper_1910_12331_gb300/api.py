@@ -20,8 +20,8 @@ MAX_ORDER = 8
 CP_OK, CP_ERR_ARG, CP_ERR_CUDA, CP_ERR_NOMEM, CP_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 CP_ERR_NOT_SPD, CP_ERR_NONFINITE, CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT, CP_WARN_CG_MAXIT = 5, 6, 7, 8, 9
 CP_F32, CP_F64 = 0, 1
-CP_PREC_FP64, CP_PREC_BF16X3 = 0, 1
-PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3}
+CP_PREC_FP64, CP_PREC_BF16X3, CP_PREC_RESIDUAL = 0, 1, 2
+PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3, "residual": CP_PREC_RESIDUAL}
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
@@ -46,7 +46,7 @@ class cp_gn_stats(ctypes.Structure):
                 ("grad_norm_sum", ctypes.c_double), ("m_norm_sum", ctypes.c_double),
                 ("update_norm_sum", ctypes.c_double), ("factor_norm_sum", ctypes.c_double),
                 ("lam_used", ctypes.c_double), ("cg_rnorm", ctypes.c_double), ("rel_residual", ctypes.c_double),
-                ("mttkrp_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
+                ("entry_residual", ctypes.c_double), ("mttkrp_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int)]
 
     def as_dict(self):
@@ -56,7 +56,7 @@ class cp_gn_stats(ctypes.Structure):
 class cp_solve_opts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("target_residual", ctypes.c_double),
                 ("target_stationarity", ctypes.c_double), ("refine_below", ctypes.c_double),
-                ("residual_every", ctypes.c_int)]
+                ("refine_prec", ctypes.c_int), ("residual_every", ctypes.c_int)]
 
 
 class cp_solve_result(ctypes.Structure):
@@ -259,7 +259,7 @@ def gn_params(lam, lam_lo, lam_hi, mu=2.0, eps_cg=1e-3, cg_max_iter=250, prec="f
     p.lam, p.lam_lo, p.lam_hi, p.mu = float(lam), float(lam_lo), float(lam_hi), float(mu)
     p.lam_dir, p.lam_fixed = int(lam_dir), int(bool(lam_fixed))
     p.prec = PREC[prec]
-    p.cg_fp32 = int(prec != "fp64") if cg_fp32 is None else int(bool(cg_fp32))
+    p.cg_fp32 = int(prec == "bf16x3") if cg_fp32 is None else int(bool(cg_fp32))
     p.want_residual = int(bool(want_residual))
     p.stop_stationarity = float(stop_stationarity)
     p.spin_limit = int(spin_limit)
@@ -279,11 +279,13 @@ def cp_gn_step(h: Handle, X, A, params: cp_gn_params, check=True):
     return s, st.as_dict()
 
 
-def solve_opts(max_iters=200, target_residual=0.0, target_stationarity=0.0, refine_below=0.0, residual_every=0):
+def solve_opts(max_iters=200, target_residual=0.0, target_stationarity=0.0, refine_below=0.0, residual_every=0,
+               refine_prec="residual"):
     o = cp_solve_opts()
     o.max_iters, o.target_residual, o.target_stationarity = int(max_iters), float(target_residual), \
         float(target_stationarity)
     o.refine_below, o.residual_every = float(refine_below), int(residual_every)
+    o.refine_prec = PREC[refine_prec]
     return o
 
 

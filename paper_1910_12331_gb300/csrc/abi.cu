@@ -41,7 +41,7 @@ struct cp_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch;
-    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y;
+    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes;
     DevStats* h_stats = nullptr;  // pinned
     SplitCache split;             // bf16 planes of X (tensor-core path)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
@@ -176,6 +176,14 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         h->launches += tc_launch_count(h->split, d, s);
         CP_TRY(grow(h->stats, sizeof(DevStats)));
         CP_TRY(tc_mttkrp_all(h->split, d, s, X, A, M, &((DevStats*)h->stats.p)->status, h->stream));
+    } else if (prec == CP_PREC_RESIDUAL) {
+        // MTTKRP of the residual tensor E = X - [[A]] (double-float), as bf16 planes
+        CP_TRY(grow(h->stats, sizeof(DevStats)));
+        CP_TRY(grow(h->resid_planes, (size_t)2 * s.dims[0] * s.mid * tc_row_pitch(s.dims[s.N - 1]) * 2));
+        DevStats* ds = (DevStats*)h->stats.p;
+        launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, tc_row_pitch(s.dims[s.N - 1]), ds, h->stream);
+        CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
+        h->launches += 1 + (s.R + 63) / 64 * (2 + (s.N - 2) + 2);
     } else {
         return CP_ERR_ARG;
     }
@@ -234,7 +242,7 @@ cp_status cp_destroy(cp_handle h) {
         cudaStreamSynchronize(h->stream);
         DevBuf* bufs[] = {&h->gram_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
                           &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
-                          &h->stats, &h->Y};
+                          &h->stats, &h->Y, &h->resid_planes};
         for (DevBuf* b : bufs)
             if (b->p) cudaFree(b->p);
         if (h->h_stats) cudaFreeHost(h->h_stats);
@@ -275,7 +283,7 @@ cp_status cp_mttkrp_all(cp_handle h, const cp_desc* d, const void* X, const doub
     CP_TRY(check_ptrs((const void* const*)A, d->order));
     CP_TRY(check_ptrs((const void* const*)M, d->order));
     if (aliased((const void* const*)M, d->order, (const void* const*)A, d->order, X)) return CP_ERR_ARG;
-    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3) return CP_ERR_ARG;
+    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3) return CP_ERR_ARG;  // RESIDUAL is gradient-only
     DeviceGuard g(h->device);
     const Shape s = make_shape(d);
     return mttkrp_into(h, d, s, X, ptrs_of(A, s.N), ptrs_of(M, s.N), prec);
@@ -284,6 +292,7 @@ cp_status cp_mttkrp_all(cp_handle h, const cp_desc* d, const void* X, const doub
 cp_status cp_gradient(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* const* G,
                       cp_precision prec, double* gnorm, double* mnorm) {
     if (!h || !X) return CP_ERR_ARG;
+    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3 && prec != CP_PREC_RESIDUAL) return CP_ERR_ARG;
     CP_TRY(check_desc(d));
     CP_TRY(check_ptrs((const void* const*)A, d->order));
     CP_TRY(check_ptrs((const void* const*)G, d->order));
@@ -296,7 +305,7 @@ cp_status cp_gradient(cp_handle h, const cp_desc* d, const void* X, const double
     CP_TRY(mttkrp_into(h, d, s, X, Ap, packed_ptrs((double*)h->Mp.p, s), prec));
     CP_TRY(gram_gamma(h, s, Ap));
     launch_gradient(s, Ap, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
-                    (DevStats*)h->stats.p, h->stream);
+                    (DevStats*)h->stats.p, h->stream, prec == CP_PREC_RESIDUAL);
     launch_unpack(s, (const double*)h->Gp.p, ptrs_of(G, s.N), h->stream);
     CUDA_TRY(cudaGetLastError());
     CP_TRY(sync_stats(h));
@@ -410,7 +419,8 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
     CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
     CP_TRY(gram_gamma(h, s, Ac));
     h->launches += 2;
-    launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p, ds, h->stream);
+    launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p, ds, h->stream,
+                    p->prec == CP_PREC_RESIDUAL);
     // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
     launch_precond(s, (const double*)h->Gam.p, p->lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
                    (double*)h->precond_scratch.p, ds, h->stream);
@@ -451,6 +461,7 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
         st->lam_used = p->lam;
         st->cg_rnorm = hs.cg_rnorm;
         st->rel_residual = p->want_residual ? sqrt(hs.res_num) / sqrt(hs.res_den) : -1.0;
+        st->entry_residual = p->prec == CP_PREC_RESIDUAL ? sqrt(hs.eres_num) / sqrt(hs.eres_den) : -1.0;
         float t01 = 0.f, t23 = 0.f, t03 = 0.f;
         cudaEventElapsedTime(&t01, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&t23, h->ev[2], h->ev[3]);
@@ -470,7 +481,7 @@ static cp_status check_params(const cp_gn_params* p) {
     if (!(p->eps_cg >= 0.0) || p->cg_max_iter < 0) return CP_ERR_ARG;
     if (!(p->lam >= 0.0) || !isfinite(p->lam)) return CP_ERR_ARG;
     if (!p->lam_fixed && !(p->mu > 1.0 && p->lam_lo > 0.0 && p->lam_hi >= p->lam_lo)) return CP_ERR_ARG;
-    if (p->prec != CP_PREC_FP64 && p->prec != CP_PREC_BF16X3) return CP_ERR_ARG;
+    if (p->prec != CP_PREC_FP64 && p->prec != CP_PREC_BF16X3 && p->prec != CP_PREC_RESIDUAL) return CP_ERR_ARG;
     return CP_OK;
 }
 
@@ -499,11 +510,12 @@ cp_status cp_gn_solve(cp_handle h, const cp_desc* d, const void* X, double* cons
     memset(res, 0, sizeof(*res));
     res->rel_residual = -1.0;
     const cp_precision base_prec = p->prec;
-    bool refining = base_prec == CP_PREC_FP64;
+    const cp_precision refine_prec = o->refine_prec == CP_PREC_FP64 ? CP_PREC_FP64 : CP_PREC_RESIDUAL;
+    bool refining = base_prec != CP_PREC_BF16X3;
     cp_status status = CP_OK;
     for (int it = 0; it < o->max_iters; ++it) {
         cp_gn_params q = *p;
-        q.prec = refining ? CP_PREC_FP64 : base_prec;
+        q.prec = refining ? (base_prec == CP_PREC_BF16X3 ? refine_prec : base_prec) : base_prec;
         // Algorithm 1's loop test on sum||G||: only trusted with an FP64-accurate gradient
         q.stop_stationarity = refining ? o->target_stationarity : 0.0;
         const bool resid_now = o->target_residual > 0.0 || (o->residual_every > 0 && (it + 1) % o->residual_every == 0);
@@ -524,7 +536,7 @@ cp_status cp_gn_solve(cp_handle h, const cp_desc* d, const void* X, double* cons
             break;
         }
         ++res->iters;
-        if (q.prec == CP_PREC_FP64 && base_prec != CP_PREC_FP64) ++res->iters_refined;
+        if (q.prec != base_prec) ++res->iters_refined;
         if (resid_now) res->rel_residual = st.rel_residual;
         if (o->target_residual > 0.0 && st.rel_residual <= o->target_residual) {
             res->converged = 1;

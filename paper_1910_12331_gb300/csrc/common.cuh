@@ -34,8 +34,10 @@ struct DevStats {
     double mnorm2[kMaxN];   // ||M^(n)||_F^2
     double vnorm2[kMaxN];   // ||V^(n)||_F^2
     double anorm2[kMaxN];   // ||A^(n)||_F^2 after the update
-    double res_num;         // sum (x - x~)^2
+    double res_num;         // sum (x - x~)^2 (after the update)
     double res_den;         // sum x^2
+    double eres_num;        // sum (x - x~)^2 at the entry point (residual gradient)
+    double eres_den;
     double cg_rnorm;        // final sum_n ||R^(n)||_F
     int cg_iters;
     int status;             // cp_status raised on the device

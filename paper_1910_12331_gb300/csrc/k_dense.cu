@@ -100,7 +100,7 @@ void launch_gamma(const Shape& s, const double* part, int chunks, double* S, dou
 // -------------------------------------------------------------- gradient
 // One thread per (row, column) of the packed gradient.
 __global__ void gradient_kernel(Shape s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
-                                DevStats* stats) {
+                                DevStats* stats, bool resid) {
     __shared__ double red[32];
     const int R = s.R;
     const int n = blockIdx.y;
@@ -115,10 +115,12 @@ __global__ void gradient_kernel(Shape s, Ptrs<const double> A, const double* Gam
         double acc = 0.0;
         for (int z = 0; z < R; ++z) acc += a[z] * Gnn[(int64_t)r * R + z];  // Gamma symmetric
         const double mv = M[s.roff[n] * R + e];
-        const double g = acc - mv;
+        // resid: mv = (E_(n) P^(n))_{ir}, G = -mv, M = A Gamma - G
+        const double g = resid ? -mv : acc - mv;
+        const double mfull = resid ? acc + mv : mv;
         G[s.roff[n] * R + e] = g;
         g2 = g * g;
-        m2 = mv * mv;
+        m2 = mfull * mfull;
     }
     g2 = block_sum(g2, red);
     m2 = block_sum(m2, red);
@@ -130,11 +132,11 @@ __global__ void gradient_kernel(Shape s, Ptrs<const double> A, const double* Gam
 }
 
 void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
-                     DevStats* stats, cudaStream_t st) {
+                     DevStats* stats, cudaStream_t st, bool resid) {
     int64_t mx = 0;
     for (int n = 0; n < s.N; ++n) mx = std::max<int64_t>(mx, s.dims[n] * s.R);
     dim3 grid((unsigned)((mx + 255) / 256), s.N);
-    gradient_kernel<<<grid, 256, 0, st>>>(s, A, Gam, M, G, stats);
+    gradient_kernel<<<grid, 256, 0, st>>>(s, A, Gam, M, G, stats, resid);
 }
 
 // -------------------------------------------------------- preconditioner

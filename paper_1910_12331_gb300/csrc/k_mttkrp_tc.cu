@@ -681,8 +681,42 @@ static TcGeom tc_geom(const Shape& s, int sms) {
     return g;
 }
 
-static cp_status tc_run(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
-                        Ptrs<double> M, unsigned mode_mask, int* status, cudaStream_t st) {
+int64_t tc_row_pitch(int64_t sN) { return pad8(sN); }
+
+// bf16 planes of X, cached by pointer / size / version.
+static cp_status tc_split_x(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, int sms,
+                            cudaStream_t st) {
+    const int N = s.N;
+    const int64_t sN = s.dims[N - 1], sNp = pad8(sN), rows = s.dims[0] * s.mid;
+    const size_t pbytes = (size_t)2 * rows * sNp * sizeof(__nv_bfloat16);
+    const bool hit = c.planes && c.key_ptr == X && c.key_version == d->x_version && c.key_total == s.total &&
+                     c.key_dtype == (int)d->x_dtype && c.bytes >= pbytes;
+    if (hit) return CP_OK;
+    if (c.bytes < pbytes) {
+        if (c.planes) cudaFree(c.planes);
+        c.planes = nullptr;
+        c.bytes = 0;
+        if (cudaMalloc(&c.planes, pbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return CP_ERR_NOMEM;
+        }
+        c.bytes = pbytes;
+    }
+    const int blocks = sms * 8;
+    if (d->x_dtype == CP_F32)
+        split_x_kernel<float><<<blocks, 256, 0, st>>>((const float*)X, (__nv_bfloat16*)c.planes, rows, sN, sNp);
+    else
+        split_x_kernel<double><<<blocks, 256, 0, st>>>((const double*)X, (__nv_bfloat16*)c.planes, rows, sN, sNp);
+    c.key_ptr = X;
+    c.key_version = d->x_version;
+    c.key_total = s.total;
+    c.key_dtype = (int)d->x_dtype;
+    return CP_OK;
+}
+
+// MTTKRP on planes [2][s1][mid][sNp] that are already in device memory.
+static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs<const double> A, Ptrs<double> M,
+                         unsigned mode_mask, int* status, cudaStream_t st) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return CP_ERR_UNSUPPORTED;
     int dev = 0, sms = 0;
@@ -690,32 +724,6 @@ static cp_status tc_run(SplitCache& c, const cp_desc* d, const Shape& s, const v
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int N = s.N, R = s.R;
     const int64_t s1 = s.dims[0], sN = s.dims[N - 1], mid = s.mid, sNp = pad8(sN);
-    const int64_t rows = s1 * mid;
-    // ---- split planes of X (cached by pointer / size / version)
-    const size_t pbytes = (size_t)2 * rows * sNp * sizeof(__nv_bfloat16);
-    const bool hit = c.planes && c.key_ptr == X && c.key_version == d->x_version && c.key_total == s.total &&
-                     c.key_dtype == (int)d->x_dtype && c.bytes >= pbytes;
-    if (!hit) {
-        if (c.bytes < pbytes) {
-            if (c.planes) cudaFree(c.planes);
-            c.planes = nullptr;
-            c.bytes = 0;
-            if (cudaMalloc(&c.planes, pbytes) != cudaSuccess) {
-                cudaGetLastError();
-                return CP_ERR_NOMEM;
-            }
-            c.bytes = pbytes;
-        }
-        const int blocks = sms * 8;
-        if (d->x_dtype == CP_F32)
-            split_x_kernel<float><<<blocks, 256, 0, st>>>((const float*)X, (__nv_bfloat16*)c.planes, rows, sN, sNp);
-        else
-            split_x_kernel<double><<<blocks, 256, 0, st>>>((const double*)X, (__nv_bfloat16*)c.planes, rows, sN, sNp);
-        c.key_ptr = X;
-        c.key_version = d->x_version;
-        c.key_total = s.total;
-        c.key_dtype = (int)d->x_dtype;
-    }
     // ---- workspace: factor planes and unit partials
     const TcGeom g = tc_geom(s, sms);
     int64_t midrows = 0;
@@ -771,7 +779,7 @@ static cp_status tc_run(SplitCache& c, const cp_desc* d, const Shape& s, const v
         cuuint64_t strides[3] = {(cuuint64_t)(sNp * 2), (cuuint64_t)(mid * sNp * 2), (cuuint64_t)(s1 * mid * sNp * 2)};
         cuuint32_t box[4] = {64, 1, (cuuint32_t)kBI, 2};
         cuuint32_t es[4] = {1, 1, 1, 1};
-        if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, c.planes, dims, strides, box, es,
+        if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(planes), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return CP_ERR_UNSUPPORTED;
@@ -809,6 +817,16 @@ static cp_status tc_run(SplitCache& c, const cp_desc* d, const Shape& s, const v
     return CP_OK;
 }
 
+static cp_status tc_run(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
+                        Ptrs<double> M, unsigned mode_mask, int* status, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const cp_status r = tc_split_x(c, d, s, X, sms, st);
+    if (r != CP_OK) return r;
+    return tc_main(c, c.planes, s, A, M, mode_mask, status, st);
+}
+
 cp_status tc_mttkrp_all(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
                         Ptrs<double> M, int* status, cudaStream_t st) {
     return tc_run(c, d, s, X, A, M, (1u << s.N) - 1u, status, st);
@@ -817,6 +835,11 @@ cp_status tc_mttkrp_all(SplitCache& c, const cp_desc* d, const Shape& s, const v
 cp_status tc_mttkrp_mode(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
                          Ptrs<double> M, int n, int* status, cudaStream_t st) {
     return tc_run(c, d, s, X, A, M, 1u << n, status, st);
+}
+
+cp_status tc_mttkrp_planes(SplitCache& c, const void* planes, const Shape& s, Ptrs<const double> A, Ptrs<double> M,
+                           int* status, cudaStream_t st) {
+    return tc_main(c, planes, s, A, M, (1u << s.N) - 1u, status, st);
 }
 
 }  // namespace cpgn

@@ -1,0 +1,152 @@
+// k_resid.cu -- the residual tensor E = X - [[A^(1), ..., A^(N)]] in
+// double-float arithmetic, written as bf16 high/low planes for the
+// tensor-core MTTKRP, with sum E^2 and sum X^2 accumulated in FP64.
+//
+// Why: the gradient of f (Eq. (2.3)) is G^(n) = A^(n) Gamma^(n) - X_(n) P^(n)
+// = -E_(n) P^(n), because [[A]]_(n) P^(n) = A^(n) (P^(n)T P^(n)) = A^(n) Gamma^(n).
+// Near the optimum E is small, so the MTTKRP of E in bf16x3 (relative error
+// ~1e-5 of |E| |P|) gives a gradient accurate to ~1e-5 * r relative to |M|,
+// where the direct form A Gamma - M cancels to the ~1e-5 error of M itself.
+// The reconstruction needs ~1e-10 relative accuracy, which FP32 cannot give;
+// it is evaluated as a double-float (hi + lo FP32 pair) dot product over the
+// rank with error-free products (two-product through fmaf, Dekker 1971) and
+// error-free sums (two-sum, Knuth), about 2^-44 relative, on the FP32 pipes,
+// which GB300 runs at 64x its FP64 rate.
+#include <cuda_bf16.h>
+
+#include "kernels.hpp"
+
+namespace cpgn {
+
+namespace {
+constexpr int TI = 64, TK = 64, RC = 32, NT = 256;
+
+__device__ __forceinline__ float2 split_df(double d) {
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
+}
+
+// acc += a * b in double-float (a, b, acc as (hi, lo)); the lo*lo term is dropped.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float pe = fmaf(a.x, b.x, -p);
+    pe = fmaf(a.x, b.y, pe);
+    pe = fmaf(a.y, b.x, pe);
+    const float t = sh + p;
+    const float z = t - sh;
+    const float err = (sh - (t - z)) + (p - z);
+    sh = t;
+    sl += err + pe;
+}
+}  // namespace
+
+template <typename TX>
+__global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __restrict__ X, Ptrs<const double> A,
+                                                        __nv_bfloat16* __restrict__ planes, int64_t sNp,
+                                                        DevStats* stats) {
+    __shared__ float2 As[RC][TI];
+    __shared__ float2 Bs[RC][TK];
+    __shared__ double ws[RC];
+    __shared__ double red[32];
+    const int64_t m = blockIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * TI, k0 = (int64_t)blockIdx.z * TK;
+    const int R = s.R, N = s.N;
+    const int64_t s1 = s.dims[0], sN = s.dims[N - 1], mid = s.mid;
+    int64_t idx[kMaxN];
+    {
+        int64_t t = m;
+        for (int q = N - 2; q >= 1; --q) {
+            idx[q] = t % s.dims[q];
+            t /= s.dims[q];
+        }
+    }
+    const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;  // rows ti*4+u, columns tk+16c
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sh[u][c] = sl[u][c] = 0.0f;
+    for (int r0 = 0; r0 < R; r0 += RC) {
+        if (threadIdx.x < RC) {
+            double w = 0.0;
+            if (r0 + (int)threadIdx.x < R) {
+                w = 1.0;
+                for (int q = 1; q + 1 < N; ++q) w *= A.p[q][idx[q] * R + r0 + threadIdx.x];
+            }
+            ws[threadIdx.x] = w;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < RC * TI; t += NT) {
+            const int rr = t / TI, ii = t % TI;
+            const int64_t i = i0 + ii;
+            const int r = r0 + rr;
+            As[rr][ii] = (i < s1 && r < R) ? split_df(A.p[0][i * R + r]) : make_float2(0.f, 0.f);
+        }
+        for (int t = threadIdx.x; t < RC * TK; t += NT) {
+            const int rr = t / TK, kk = t % TK;
+            const int64_t k = k0 + kk;
+            const int r = r0 + rr;
+            Bs[rr][kk] = (k < sN && r < R) ? split_df(ws[rr] * A.p[N - 1][k * R + r]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < RC; ++rr) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[rr][ti * 4 + u];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[rr][tk + 16 * c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) df_mac(sh[u][c], sl[u][c], a[u], b[c]);
+        }
+        __syncthreads();
+    }
+    double num = 0.0, den = 0.0;
+    const int64_t total_p = s1 * mid * sNp;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ti * 4 + u;
+        if (i >= s1) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t k = k0 + tk + 16 * c;
+            if (k >= sNp) continue;
+            float e = 0.0f;
+            if (k < sN) {
+                const TX x = X[(i * mid + m) * sN + k];
+                if constexpr (sizeof(TX) == 4) {
+                    // x - sh is exact when the reconstruction is close (Sterbenz)
+                    e = (x - sh[u][c]) - sl[u][c];
+                } else {
+                    e = (float)((x - (double)sh[u][c]) - (double)sl[u][c]);
+                }
+                num += (double)e * (double)e;
+                den += (double)x * (double)x;
+            }
+            const __nv_bfloat16 hi = __float2bfloat16_rn(e);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(e - __bfloat162float(hi));
+            const int64_t o = (i * mid + m) * sNp + k;
+            planes[o] = hi;
+            planes[total_p + o] = lo;
+        }
+    }
+    num = block_sum(num, red);
+    den = block_sum(den, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&stats->eres_num, num);
+        atomicAdd(&stats->eres_den, den);
+    }
+}
+
+void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
+                        int64_t sNp, DevStats* stats, cudaStream_t st) {
+    dim3 grid((unsigned)s.mid, (unsigned)((s.dims[0] + TI - 1) / TI), (unsigned)((sNp + TK - 1) / TK));
+    if (xdt == CP_F32)
+        resid_split_kernel<float><<<grid, NT, 0, st>>>(s, (const float*)X, A, (__nv_bfloat16*)planes, sNp, stats);
+    else
+        resid_split_kernel<double><<<grid, NT, 0, st>>>(s, (const double*)X, A, (__nv_bfloat16*)planes, sNp, stats);
+}
+
+}  // namespace cpgn

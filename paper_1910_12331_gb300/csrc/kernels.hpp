@@ -18,8 +18,10 @@ void launch_gram_partial(const Shape& s, Ptrs<const double> A, double* part, int
 void launch_gamma(const Shape& s, const double* part, int chunks, double* S, double* Gam, float* GamF,
                   cudaStream_t st);
 // G^(n) = A^(n) Gam[n][n] - M^(n) (packed G, packed M); norms into stats.
+// resid = true: M holds the MTTKRP of the residual tensor, G = -M and the
+// reported |M^(n)| is that of A^(n) Gam[n][n] - G^(n).
 void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
-                     DevStats* stats, cudaStream_t st);
+                     DevStats* stats, cudaStream_t st, bool resid = false);
 // Pinv[n] = (Gam[n][n] + lam I)^{-1} (FP64 Cholesky + inverse); PinvF float copy (may be null).
 // scratch: N*2*R*R doubles, used only when precond_smem_bytes(R) == 0.
 void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv, float* PinvF, double* scratch,
@@ -73,6 +75,10 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st);
 // Plain (non-persistent) FP64 matvec used by cp_gn_matvec: Q = (J^T J + lam I) W.
 void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
                        Ptrs<double> Q, double* Y, cudaStream_t st);
+
+// ---- residual tensor in double-float, as bf16 planes [2][s1][mid][sNp] (k_resid.cu)
+void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
+                        int64_t sNp, DevStats* stats, cudaStream_t st);
 
 // ---- residual (k_residual.cu) ------------------------------------------------------
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,

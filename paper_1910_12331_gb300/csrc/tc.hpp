@@ -34,4 +34,10 @@ cp_status tc_mttkrp_all(SplitCache& c, const cp_desc* d, const Shape& s, const v
 cp_status tc_mttkrp_mode(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
                          Ptrs<double> M, int n, int* status, cudaStream_t st);
 
+// All-mode MTTKRP of a tensor given directly as bf16 planes [2][s1][mid][pitch],
+// pitch = tc_row_pitch(s_N) (used for the residual tensor).
+cp_status tc_mttkrp_planes(SplitCache& c, const void* planes, const Shape& s, Ptrs<const double> A, Ptrs<double> M,
+                           int* status, cudaStream_t st);
+int64_t tc_row_pitch(int64_t sN);
+
 }  // namespace cpgn

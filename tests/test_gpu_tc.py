@@ -83,3 +83,76 @@ def test_mttkrp_bf16x3_exact_gradient_invariant(env):
         ref = Ad[n] @ G
         err = ((M[n] - ref).abs().max() / ref.abs().max()).item()
         assert err <= 3 * TOL_BF16X3, err
+
+
+def _near_exact(dims, R, seed, eps):
+    rng = np.random.default_rng(seed)
+    T = [rng.standard_normal((s, R)) for s in dims]
+    from tests import cpref
+
+    X = cpref.reconstruct(T).astype(np.float32)
+    A = [t + eps * rng.standard_normal(t.shape) for t in T]
+    return X, A
+
+
+@pytest.mark.parametrize("dims,R,eps", [((37, 70, 45), 6, 1e-6), ((30, 20, 24, 10), 5, 1e-5), ((130, 9, 140), 20, 1e-7)])
+def test_gradient_residual_mode_near_optimum(env, orc, dims, R, eps):
+    """G = -E_(n) P^(n) (E formed in double-float): near the optimum its error
+    is far below the bf16x3 error of A Gamma - M; measured against sum|M|."""
+    torch, api, h = env
+    X, A = _near_exact(dims, R, 3, eps)
+    Ad = [torch.from_numpy(a).cuda() for a in A]
+    Xd = torch.from_numpy(X).cuda()
+    Gr, gn, mn = api.cp_gradient(h, Xd, Ad, prec="residual")
+    Gam = orc.gamma(orc.gram(A))
+    M = orc.mttkrp(X, A)
+    Go, gno = orc.gradient(A, Gam, M)
+    msum = sum(np.linalg.norm(m) for m in M)
+    err = sum(np.linalg.norm(g.cpu().numpy() - o) for g, o in zip(Gr, Go)) / msum
+    Gb, _, _ = api.cp_gradient(h, Xd, Ad, prec="bf16x3")
+    err_b = sum(np.linalg.norm(g.cpu().numpy() - o) for g, o in zip(Gb, Go)) / msum
+    print("residual-mode gradient err", err, "bf16x3 err", err_b, "stationarity", sum(gno) / msum)
+    stat = sum(gno) / msum
+    # the error scales with |E|, i.e. with the stationarity, at the bf16x3 rate
+    assert err <= 3 * TOL_BF16X3 * stat + 1e-12
+    assert err < err_b / 10
+    np.testing.assert_allclose(mn, [np.linalg.norm(m) for m in M], rtol=1e-9)
+
+
+def test_gradient_residual_mode_far(env, orc):
+    torch, api, h = env
+    X, A = _problem((37, 70, 45), 13, 5)
+    Gr, _, _ = api.cp_gradient(h, torch.from_numpy(X).cuda(), [torch.from_numpy(a).cuda() for a in A], prec="residual")
+    Go, _ = orc.gradient(A, orc.gamma(orc.gram(A)), orc.mttkrp(X, A))
+    M = orc.mttkrp(X, A)
+    scale = max(np.abs(m).max() for m in M)
+    assert max(np.abs(g.cpu().numpy() - o).max() for g, o in zip(Gr, Go)) / scale <= 5 * TOL_BF16X3
+
+
+def test_step_entry_residual(env, orc):
+    torch, api, h = env
+    X, A = _near_exact((40, 30, 50), 7, 6, 1e-4)
+    Ad = [torch.from_numpy(a).cuda() for a in A]
+    params = api.gn_params(1e-3, 1e-9, 1e-3, prec="residual", cg_fp32=True)
+    _, st = api.cp_gn_step(h, torch.from_numpy(X).cuda(), Ad, params)
+    r = orc.residual(X, A)
+    assert abs(st["entry_residual"] - r) <= 1e-6 * r
+
+
+def test_mixed_solve_reaches_fp64_stationarity(env, orc):
+    """The mixed path (bf16x3 gradient, FP32 CG, residual-tensor refinement)
+    meets sum|G|/sum|M| <= 1e-8 as judged by the FP64 oracle's gradient."""
+    torch, api, h = env
+    from paper_1910_12331_gb300 import datagen
+
+    p = datagen.make_problem((48, 40, 36), 6, "normal", None, 1e-6, np.float32, seed=11)
+    hi, lo = orc.default_lambda(p["init"])
+    Ad = [torch.from_numpy(a.copy()).cuda() for a in p["init"]]
+    params = api.gn_params(hi, lo, hi, prec="bf16x3")
+    opts = api.solve_opts(max_iters=200, target_stationarity=1e-8, refine_below=3e-5)
+    _, res = api.cp_gn_solve(h, torch.from_numpy(p["X"]).cuda(), Ad, params, opts)
+    assert res["converged"] == 1 and res["iters_refined"] >= 1
+    A = [a.cpu().numpy() for a in Ad]
+    M = orc.mttkrp(p["X"], A)
+    _, gn = orc.gradient(A, orc.gamma(orc.gram(A)), M)
+    assert gn.sum() / sum(np.linalg.norm(m) for m in M) <= 2e-8
