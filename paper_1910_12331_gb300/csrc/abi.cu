@@ -365,8 +365,8 @@ template <typename T>
 static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller, const cp_gn_params* p) {
     const size_t RR = (size_t)s.R * s.R, len = (size_t)s.roff[s.N] * s.R;
     CP_TRY(grow(h->Ap, len * sizeof(T)));
-    CP_TRY(grow(h->vec, 5 * len * sizeof(T)));
-    CP_TRY(grow(h->Ypart, (size_t)4096 * RR * sizeof(T)));
+    CP_TRY(grow(h->vec, len * sizeof(T)));
+    CP_TRY(grow(h->Ypart, 2 * s.N * RR * sizeof(T)));
     CP_TRY(grow(h->Tm, s.N * RR * sizeof(T)));
     CP_TRY(grow(h->pcg_part, 3 * 4096 * sizeof(double)));
     CP_TRY(grow(h->bar, sizeof(GridBarrier)));
@@ -383,13 +383,8 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
         a.PinvT = (const T*)h->Pinv.p;
     }
     a.G = (const double*)h->Gp.p;
-    T* v = (T*)h->vec.p;
-    a.V = v;
-    a.Rv = v + len;
-    a.Z = v + 2 * len;
-    a.W = v + 3 * len;
-    a.Q = v + 4 * len;
-    a.Ypart = (T*)h->Ypart.p;
+    a.V = (T*)h->vec.p;
+    a.Yacc = (T*)h->Ypart.p;
     a.Tm = (T*)h->Tm.p;
     a.part = (double*)h->pcg_part.p;
     a.bar = (GridBarrier*)h->bar.p;
@@ -400,6 +395,7 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     a.maxit = p->cg_max_iter;
     a.spin_limit = p->spin_limit > 0 ? p->spin_limit : kDefaultSpin;
     CUDA_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(GridBarrier), h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->Ypart.p, 0, s.N * RR * sizeof(T), h->stream));  // first accumulator buffer
     CP_TRY(launch_pcg<T>(a, 0, h->stream));
     return CP_OK;
 }

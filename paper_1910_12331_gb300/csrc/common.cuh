@@ -67,10 +67,19 @@ __device__ __forceinline__ int ld_volatile_s32(const int* p) {
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
-// Grid-wide barrier for a co-resident (cooperatively launched) grid.  Every
-// wait is bounded by `limit` polls: on expiry the barrier records
-// CP_ERR_TIMEOUT, raises the abort flag and returns false, and so do all
-// later barriers of the launch, so that every block leaves the kernel.
+__device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid, on one
+// monotonic arrival counter (zeroed before the launch): the k-th barrier is
+// complete when the counter reaches k * nblocks.  Thread 0 of each block
+// publishes the block's writes (fence + release add) and polls with acquire
+// loads.  Every wait is bounded by `limit` polls: on expiry the barrier
+// records CP_ERR_TIMEOUT, raises the abort flag and returns false, and so do
+// all later barriers of the launch, so that every block leaves the kernel.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, unsigned int nblocks, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
@@ -79,27 +88,20 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, unsigne
         if (ld_volatile_s32(&bar->abort)) {
             ok = 0;
         } else {
-            const unsigned int g = ld_acquire_u32(&bar->gen);
             __threadfence();
-            const unsigned int prev = atomicAdd(&bar->count, 1u);
-            if (prev == nblocks - 1) {
-                atomicExch(&bar->count, 0u);
-                __threadfence();
-                atomicAdd(&bar->gen, 1u);
-            } else {
-                long long polls = 0;
-                while (ld_acquire_u32(&bar->gen) == g) {
-                    if (ld_volatile_s32(&bar->abort)) { ok = 0; break; }
-                    if (++polls > limit) {
-                        set_status(status, CP_ERR_TIMEOUT);
-                        atomicExch(&bar->abort, 1);
-                        ok = 0;
-                        break;
-                    }
-                    if (polls > 64) __nanosleep(64);
+            const unsigned int old = atom_add_release_u32(&bar->count, 1u);
+            const unsigned int target = (old / nblocks + 1u) * nblocks;
+            long long polls = 0;
+            while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
+                if (ld_volatile_s32(&bar->abort)) { ok = 0; break; }
+                if (++polls > limit) {
+                    set_status(status, CP_ERR_TIMEOUT);
+                    atomicExch(&bar->abort, 1);
+                    ok = 0;
+                    break;
                 }
+                if (polls > 256) __nanosleep(32);
             }
-            __threadfence();
         }
         s_ok = ok;
     }

@@ -11,8 +11,9 @@
 //
 // Persistent layout: every block owns a contiguous range of rows of ONE mode
 // and keeps its rows of A, V, R, Z, W, Q in shared memory for the whole
-// solve.  Only R x R partials and scalar partials cross blocks, through global
-// memory and bounded-spin grid barriers (4 per CG iteration).  Scalar
+// solve.  Only the R x R products A^(p)T W^(p) (accumulated with atomic adds
+// into a double-buffered global accumulator) and scalar partials cross
+// blocks, with 3 bounded-spin grid barriers per CG iteration.  Scalar
 // reductions (dot products, norms) are FP64 and are summed by every block in
 // the same fixed order, so every block takes the same alpha, beta and stop
 // decision.  Vectors are FP64 (plain path) or FP32 (mixed path).
@@ -26,29 +27,28 @@
 namespace cpgn {
 
 namespace {
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
 // a * b + c with one rounding, in the precision of T (no promotion to double)
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-template <typename T>
-struct Smem {
-    T* G;   // Gamma^(n,n), R x R (or a global pointer)
-    T* P;   // P_inv^(n),  R x R (or a global pointer)
-    T* Tt;  // T^(n) transposed, R x R (or a global pointer)
-    T* A;   // own rows of A^(n)
-    T* V; T* Rv; T* Z; T* W; T* Q;
-    double* red;
-};
+// Up to 8 partials per lane are loaded before any is consumed, so one L2
+// round trip serves a whole gather (at most 256 blocks).
+constexpr int kGatherPerLane = 8;
 
-// sum_{c in [c0, c1)} v[c], computed by warp 0 with lane-strided loads and a
-// shuffle tree (a fixed order, identical in every block) and broadcast to the
-// whole block through shared memory.
-__device__ __forceinline__ double block_gather_sum(const double* v, int c0, int c1, double* bcast) {
+// sum of v[0..nb), warp 0, fixed order; broadcast to the block
+__device__ __forceinline__ double gather_sum(const double* v, int nb, double* bcast) {
     if (threadIdx.x < 32) {
+        double x[kGatherPerLane];
+#pragma unroll
+        for (int u = 0; u < kGatherPerLane; ++u) {
+            const int c = (int)threadIdx.x + 32 * u;
+            x[u] = c < nb ? __ldcg(&v[c]) : 0.0;
+        }
         double acc = 0.0;
-        for (int c = c0 + (int)threadIdx.x; c < c1; c += 32) acc += __ldcg(&v[c]);
+#pragma unroll
+        for (int u = 0; u < kGatherPerLane; ++u) acc += x[u];
         acc = warp_sum(acc);
         if (threadIdx.x == 0) *bcast = acc;
     }
@@ -58,44 +58,286 @@ __device__ __forceinline__ double block_gather_sum(const double* v, int c0, int 
     return r;
 }
 
-template <typename T>
-__device__ __forceinline__ double dsum_rows(const T* x, const T* y, int len, double* red) {
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < len; e += blockDim.x) acc += (double)x[e] * (double)y[e];
-    return block_sum(acc, red);
+// One pass over the <R,Z> and |R|^2 partials: rz = sum of all rz partials,
+// rsum = sum over modes of sqrt(sum of that mode's |R|^2 partials).
+__device__ __forceinline__ void gather_rz_rn(const double* rzp, const double* rnp, int nb, const int* mode_blk0, int N,
+                                             double* bcast, double& rz, double& rsum) {
+    if (threadIdx.x < 32) {
+        double xz[kGatherPerLane], xn[kGatherPerLane];
+#pragma unroll
+        for (int u = 0; u < kGatherPerLane; ++u) {
+            const int c = (int)threadIdx.x + 32 * u;
+            xz[u] = c < nb ? __ldcg(&rzp[c]) : 0.0;
+            xn[u] = c < nb ? __ldcg(&rnp[c]) : 0.0;
+        }
+        double az = 0.0;
+#pragma unroll
+        for (int u = 0; u < kGatherPerLane; ++u) az += xz[u];
+        az = warp_sum(az);
+        double tot = 0.0;
+        for (int m = 0; m < N; ++m) {
+            double am = 0.0;
+#pragma unroll
+            for (int u = 0; u < kGatherPerLane; ++u) {
+                const int c = (int)threadIdx.x + 32 * u;
+                if (c >= mode_blk0[m] && c < mode_blk0[m + 1]) am += xn[u];
+            }
+            tot += sqrt(warp_sum(am));
+        }
+        if (threadIdx.x == 0) {
+            bcast[0] = az;
+            bcast[1] = tot;
+        }
+    }
+    __syncthreads();
+    rz = bcast[0];
+    rsum = bcast[1];
+    __syncthreads();
 }
 
-// out[k][r] = sum_z in[k][z] * M[z][r] for the block's rows (M symmetric or given as M[z][r]).
-template <typename T>
-__device__ __forceinline__ void rows_times(const T* in, const T* M, T* out, int rows, int R) {
-    for (int e = threadIdx.x; e < rows * R; e += blockDim.x) {
-        const int k = e / R, r = e % R;
-        const T* a = in + k * R;
-        T acc = 0;
-#pragma unroll 4
-        for (int z = 0; z < R; ++z) acc = fmadd(a[z], M[z * R + r], acc);
-        out[e] = acc;
-    }
+// ---- block-wide dot products of the block's rows.  FP32 vectors: each thread
+// forms its products and partial sum error-free in double-float (two-product
+// by fmaf, two-sum), the warps reduce (hi, lo) pairs with the same error-free
+// steps on the FP32 pipes, and one warp adds the per-warp results in FP64.
+// (GB300's FP64 pipe runs at 1/64 of FP32: a reduction in FP64 by every
+// thread would cost more than the whole row computation.)  FP64 vectors:
+// plain FP64 products and sums, the cross-warp step again in one warp.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
 }
 
-// Ypart[r][z] = sum over own rows k of A[k][r] W[k][z]
 template <typename T>
-__device__ __forceinline__ void y_partial(const T* A, const T* W, T* Yp, int rows, int R) {
-    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
-        const int r = q / R, z = q % R;
-        T acc = 0;
-#pragma unroll 4
-        for (int k = 0; k < rows; ++k) acc = fmadd(A[k * R + r], W[k * R + z], acc);
-        Yp[q] = acc;
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add_prod(float x, float y) {
+        const float p = x * y;
+        const float pe = fmaf(x, y, -p);
+        float s, e;
+        two_sum(h, p, s, e);
+        h = s;
+        l += e + pe;
     }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+            float s, e;
+            two_sum(h, oh, s, e);
+            h = s;
+            l += ol + e;
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+template <>
+struct DotAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add_prod(double x, double y) { v = fma(x, y, v); }
+    __device__ __forceinline__ void warp_reduce() { v = warp_sum(v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+
+// (sum x*y, sum u*w) over the block's rows; both results valid in every thread.
+// red: at least 2 * (blockDim.x / 32) + 2 doubles.
+template <typename T>
+__device__ __forceinline__ void dot2_rows(const T* x, const T* y, const T* u, const T* w, int len, double* red,
+                                          double& r0, double& r1) {
+    DotAcc<T> a, c;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        a.add_prod(x[e], y[e]);
+        if (u) c.add_prod(u[e], w[e]);
+    }
+    a.warp_reduce();
+    if (u) c.warp_reduce();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[warp] = a.value();
+        red[32 + warp] = u ? c.value() : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double s0 = lane < nw ? red[lane] : 0.0, s1 = lane < nw ? red[32 + lane] : 0.0;
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (lane == 0) {
+            red[64] = s0;
+            red[65] = s1;
+        }
+    }
+    __syncthreads();
+    r0 = red[64];
+    r1 = red[65];
 }
+
+
 }  // namespace
 
+#ifdef CPGN_PCG_TRACE
+__device__ long long g_pcg_trace[8 * 64];
+#define PCG_TRACE(ev)                                                                          \
+    do {                                                                                       \
+        if (blockIdx.x == 0 && threadIdx.x == 0 && it < 64) g_pcg_trace[(ev) * 64 + it] = clock64(); \
+    } while (0)
+#else
+#define PCG_TRACE(ev) \
+    do {              \
+    } while (0)
+#endif
+
+// ---- register-tiled row products on shared memory (row stride Rp = R rounded up to 4)
+template <typename T>
+struct V4;
+template <>
+struct V4<float> {
+    float v[4];
+    __device__ __forceinline__ void load(const float* p) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <>
+struct V4<double> {
+    double v[4];
+    __device__ __forceinline__ void load(const double* p) {
+        const double2 t0 = *reinterpret_cast<const double2*>(p);
+        const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+    }
+};
+
+// Tile shape of the row products: FP32 uses 2 x 4 register tiles (fewer
+// shared-memory loads per FMA); FP64 is DFMA-bound, so one output per thread
+// spreads the work over all four sub-partitions of the SM.
+template <typename T>
+struct Tile;
+template <>
+struct Tile<float> {
+    static constexpr int TR = 2, TC = 4;
+};
+template <>
+struct Tile<double> {
+    static constexpr int TR = 1, TC = 1;
+};
+
+template <typename T, int TC>
+__device__ __forceinline__ void load_cols(const T* p, T* v) {
+    if constexpr (TC == 4) {
+        V4<T> t;
+        t.load(p);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = t.v[u];
+    } else {
+#pragma unroll
+        for (int u = 0; u < TC; ++u) v[u] = p[u];
+    }
+}
+
+// out[k][c] = lam * X[k][c] + sum_z X[k][z] M1[z][c] + sum_z Y[k][z] M2[z][c]   (M2 may be null)
+// for k < rows, c < Rp; each thread computes a TR x TC tile.
+template <typename T>
+__device__ __forceinline__ void rows_mm(const T* X, const T* M1, const T* Yr, const T* M2, T lam, T* out, int rows,
+                                        int R, int Rp) {
+    constexpr int TR = Tile<T>::TR, TC = Tile<T>::TC;
+    const int tc_n = Rp / TC, tr_n = (rows + TR - 1) / TR;
+    for (int t = threadIdx.x; t < tr_n * tc_n; t += blockDim.x) {
+        const int tr = t / tc_n, tc = t - tr * tc_n;
+        const int k0 = TR * tr, c0 = TC * tc;
+        const T* xr[TR];
+        const T* yr[TR];
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            const int k = k0 + i < rows ? k0 + i : k0;
+            xr[i] = X + k * Rp;
+            yr[i] = M2 ? Yr + k * Rp : nullptr;
+        }
+        T acc[TR][TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int u = 0; u < TC; ++u) acc[i][u] = lam * xr[i][c0 + u];
+#pragma unroll 2
+        for (int z = 0; z < R; ++z) {
+            T m[TC];
+            load_cols<T, TC>(M1 + z * Rp + c0, m);
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                const T a = xr[i][z];
+#pragma unroll
+                for (int u = 0; u < TC; ++u) acc[i][u] = fmadd(a, m[u], acc[i][u]);
+            }
+        }
+        if (M2) {
+#pragma unroll 2
+            for (int z = 0; z < R; ++z) {
+                T m[TC];
+                load_cols<T, TC>(M2 + z * Rp + c0, m);
+#pragma unroll
+                for (int i = 0; i < TR; ++i) {
+                    const T a = yr[i][z];
+#pragma unroll
+                    for (int u = 0; u < TC; ++u) acc[i][u] = fmadd(a, m[u], acc[i][u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+            if (k0 + i < rows)
+#pragma unroll
+                for (int u = 0; u < TC; ++u) out[(k0 + i) * Rp + c0 + u] = acc[i][u];
+    }
+}
+
+// Yacc[r][c] += sum_k A[k][r] W[k][c] over the block's rows (TR x TC tiles,
+// atomic adds), Yacc row stride R.
+template <typename T>
+__device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int rows, int R, int Rp) {
+    constexpr int TR = Tile<T>::TR, TC = Tile<T>::TC;
+    const int tc_n = Rp / TC, tr_n = (R + TR - 1) / TR;
+    for (int t = threadIdx.x; t < tr_n * tc_n; t += blockDim.x) {
+        const int tr = t / tc_n, tc = t - tr * tc_n;
+        const int r0 = TR * tr, c0 = TC * tc;
+        T acc[TR][TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int u = 0; u < TC; ++u) acc[i][u] = 0;
+#pragma unroll 2
+        for (int k = 0; k < rows; ++k) {
+            T w[TC];
+            load_cols<T, TC>(W + k * Rp + c0, w);
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                const T a = A[k * Rp + r0 + i];  // r0 + i <= Rp - 1: the padding column is zero
+#pragma unroll
+                for (int u = 0; u < TC; ++u) acc[i][u] = fmadd(a, w[u], acc[i][u]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int u = 0; u < TC; ++u) {
+                const int r = r0 + i, c = c0 + u;
+                if (r < R && c < R) atomicAdd(&Yacc[r * R + c], acc[i][u]);
+            }
+    }
+}
+
+// Persistent CP-CG.  Per iteration: (B1) A^T W complete -> T^(n) and Q rows,
+// partial <W,Q>; (B2) alpha, V/R update, Z = R P_inv, partial <R,Z> and
+// |R^(n)|^2; (B3) beta, W update, A^T W accumulated into the other buffer.
+// Shared memory holds the block's Gamma^(n,p) (all p), P_inv^(n), T^(n) and
+// its rows of A, V, R, Z, W, Q, every matrix with row stride Rp (zero padded).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_mats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Shape& s = a.s;
     const int R = s.R, RR = R * R, N = s.N;
+    const int Rp = (R + 3) & ~3, RRp = R * Rp;
     const int b = blockIdx.x;
     int n = 0;
     while (n + 1 < N && b >= a.mode_blk0[n + 1]) ++n;
@@ -103,48 +345,49 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
     const int64_t row0 = (int64_t)j * a.rpb[n];
     const int64_t left = s.dims[n] - row0;
     const int rows = (int)(left < a.rpb[n] ? left : a.rpb[n]);
-    const int len = rows * R;
+    const int lenp = rows * Rp;
     const int64_t goff = (s.roff[n] + row0) * R;  // packed element offset of the block's rows
+    (void)stage_mats;
 
-    Smem<T> sm;
-    {
-        sm.red = reinterpret_cast<double*>(smem_raw);
-        T* p = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double));
-        if (stage_mats) {
-            sm.G = p; p += RR;
-            sm.P = p; p += RR;
-            sm.Tt = p; p += RR;
-        } else {
-            sm.G = const_cast<T*>(a.GamT) + ((int64_t)n * N + n) * RR;
-            sm.P = const_cast<T*>(a.PinvT) + (int64_t)n * RR;
-            sm.Tt = a.Tm + (int64_t)n * RR;
-        }
-        const int rl = a.rpb[n] * R;
-        sm.A = p; p += rl;
-        sm.V = p; p += rl;
-        sm.Rv = p; p += rl;
-        sm.Z = p; p += rl;
-        sm.W = p; p += rl;
-        sm.Q = p;
-    }
+    double* red = reinterpret_cast<double*>(smem_raw);
+    double* bcast = red + 72;
+    T* p = reinterpret_cast<T*>(smem_raw + 80 * sizeof(double));
+    T* Gx = p; p += (size_t)N * RRp;   // Gamma^(n,p), p = 0..N-1
+    T* Pm = p; p += RRp;               // P_inv^(n)
+    T* Tt = p; p += RRp;               // T^(n) transposed
+    const T* Gm = Gx + (size_t)n * RRp;
+    const int rl = a.rpb[n] * Rp;
+    T* sA = p; p += rl;
+    T* sV = p; p += rl;
+    T* sR = p; p += rl;
+    T* sZ = p; p += rl;
+    T* sW = p; p += rl;
+    T* sQ = p;
+
     double* const part_rz = a.part;
     double* const part_rn = a.part + a.nblocks;
     double* const part_wq = a.part + 2 * a.nblocks;
     int* const status = &a.stats->status;
     const unsigned nb = (unsigned)a.nblocks;
     const long long lim = a.spin_limit;
+    const size_t ysz = (size_t)N * RR;
 
-    // ---- set-up: stage constant matrices and own rows
-    if (stage_mats) {
-        for (int q = threadIdx.x; q < RR; q += blockDim.x) {
-            sm.G[q] = a.GamT[((int64_t)n * N + n) * RR + q];
-            sm.P[q] = a.PinvT[(int64_t)n * RR + q];
-        }
+    // ---- set-up: stage the constant matrices and the block's rows, zero padded
+    for (int q = threadIdx.x; q < N * RRp; q += blockDim.x) {
+        const int pp = q / RRp, e = q - pp * RRp, z = e / Rp, c = e - z * Rp;
+        Gx[q] = c < R ? a.GamT[((size_t)n * N + pp) * RR + z * R + c] : (T)0;
     }
-    for (int e = threadIdx.x; e < len; e += blockDim.x) {
-        sm.A[e] = a.Ap[goff + e];
-        sm.Rv[e] = (T)(-a.G[goff + e]);
-        sm.V[e] = (T)0;
+    for (int e = threadIdx.x; e < RRp; e += blockDim.x) {
+        const int z = e / Rp, c = e - z * Rp;
+        Pm[e] = c < R ? a.PinvT[(size_t)n * RR + z * R + c] : (T)0;
+        Tt[e] = (T)0;
+    }
+    for (int e = threadIdx.x; e < lenp; e += blockDim.x) {
+        const int k = e / Rp, c = e - k * Rp;
+        const bool in = c < R;
+        sA[e] = in ? a.Ap[goff + k * R + c] : (T)0;
+        sR[e] = in ? (T)(-a.G[goff + k * R + c]) : (T)0;
+        sV[e] = (T)0;
     }
     double gsum = 0.0, msum = 0.0;
     for (int m = 0; m < N; ++m) {
@@ -155,23 +398,19 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
     // Algorithm 1's loop test, evaluated on the device: a stationary point gets no update.
     const bool stationary = a.stop_ratio > 0.0 && gsum <= a.stop_ratio * msum;
     __syncthreads();
-    rows_times(sm.Rv, sm.P, sm.Z, rows, R);
+    rows_mm<T>(sR, Pm, nullptr, nullptr, (T)0, sZ, rows, R, Rp);
     __syncthreads();
-    for (int e = threadIdx.x; e < len; e += blockDim.x) sm.W[e] = sm.Z[e];
-    double rz_p = dsum_rows(sm.Rv, sm.Z, len, sm.red);
-    double rn_p = dsum_rows(sm.Rv, sm.Rv, len, sm.red);
+    for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = sZ[e];
+    double rz_p, rn_p;
+    dot2_rows(sR, sZ, sR, sR, lenp, red, rz_p, rn_p);
     if (threadIdx.x == 0) { part_rz[b] = rz_p; part_rn[b] = rn_p; }
-    y_partial(sm.A, sm.W, a.Ypart + (int64_t)b * RR, rows, R);
+    y_tiles(sA, sW, a.Yacc + (size_t)n * RR, rows, R, Rp);
 
     int it = 0;
     double rsum = 0.0, rz = 0.0;
     bool ok = grid_sync(a.bar, status, nb, lim);
-    double* const bcast = sm.red + 40;
     auto reduce_r = [&](double& rz_out, double& rsum_out) {
-        rz_out = block_gather_sum(part_rz, 0, (int)nb, bcast);
-        double tot = 0.0;
-        for (int m = 0; m < N; ++m) tot += sqrt(block_gather_sum(part_rn, a.mode_blk0[m], a.mode_blk0[m + 1], bcast));
-        rsum_out = tot;
+        gather_rz_rn(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_out, rsum_out);
     };
     if (ok) reduce_r(rz, rsum);
     if (stationary) {
@@ -182,83 +421,64 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         if (!(rsum > tol)) break;
         if (!isfinite(rsum) || !isfinite(rz)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
-        // ---- T phase: T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed.
-        // One warp per entry q: the lanes split the per-block partials of every
-        // Y^(p)_q, a shuffle reduction completes them, lane n forms T^(n)_q.
-        {
-            const int lane = threadIdx.x & 31;
-            const int64_t gw = ((int64_t)b * blockDim.x + threadIdx.x) >> 5;
-            const int64_t nw = ((int64_t)nb * blockDim.x) >> 5;
-            for (int64_t q = gw; q < RR; q += nw) {
-                T y[kMaxN];
+        PCG_TRACE(0);
+        const int buf = it & 1;
+        const T* Ycur = a.Yacc + buf * ysz;
+        T* Ynext = a.Yacc + (buf ^ 1) * ysz;
+        // ---- T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed (Tt[z][r] = T[r][z]);
+        // every thread issues its loads of Y for all modes before using them
+        for (int q0 = threadIdx.x; q0 < RR; q0 += 4 * blockDim.x) {
+            T y[4][kMaxN];
 #pragma unroll
-                for (int p = 0; p < kMaxN; ++p) {
-                    if (p >= N) break;
-                    T acc = 0;
-                    for (int c = a.mode_blk0[p] + lane; c < a.mode_blk0[p + 1]; c += 32)
-                        acc += ldcg(&a.Ypart[(int64_t)c * RR + q]);
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + u * blockDim.x;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                    y[p] = acc;
-                }
-                if (lane < N) {
-                    const int nn = lane;
-                    T t = 0;
+                for (int pp = 0; pp < kMaxN; ++pp)
+                    y[u][pp] = (pp < N && pp != n && q < RR) ? ldcg(&Ycur[(size_t)pp * RR + q]) : (T)0;
+            }
 #pragma unroll
-                    for (int p = 0; p < kMaxN; ++p) {
-                        if (p >= N) break;
-                        if (p != nn) t = fmadd(a.GamT[((int64_t)nn * N + p) * RR + q], y[p], t);
-                    }
-                    const int r = (int)(q / R), z = (int)(q % R);
-                    a.Tm[(int64_t)nn * RR + z * R + r] = t;
-                }
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + u * blockDim.x;
+                if (q >= RR) break;
+                const int r = q / R, z = q - r * R;
+                T t = 0;
+#pragma unroll
+                for (int pp = 0; pp < kMaxN; ++pp)
+                    if (pp < N && pp != n) t = fmadd(Gx[(size_t)pp * RRp + r * Rp + z], y[u][pp], t);
+                Tt[z * Rp + r] = t;
             }
         }
-        if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
-        // ---- Q phase: Q = lam W + W Gamma^(n,n) + A T^(n)^T
-        if (stage_mats)
-            for (int q = threadIdx.x; q < RR; q += blockDim.x) sm.Tt[q] = ldcg(&a.Tm[(int64_t)n * RR + q]);
+        // the accumulator of the next iteration is cleared here: it was last read
+        // before the previous iteration's second barrier
+        for (size_t q = (size_t)b * blockDim.x + threadIdx.x; q < ysz; q += (size_t)nb * blockDim.x) Ynext[q] = (T)0;
         __syncthreads();
-        const T lam = (T)a.lam;
-        for (int e = threadIdx.x; e < len; e += blockDim.x) {
-            const int k = e / R, r = e % R;
-            const T* w = sm.W + k * R;
-            const T* ar = sm.A + k * R;
-            T acc = lam * w[r];
-            if (stage_mats) {
-#pragma unroll 4
-                for (int z = 0; z < R; ++z) {
-                    acc = fmadd(w[z], sm.G[z * R + r], acc);
-                    acc = fmadd(ar[z], sm.Tt[z * R + r], acc);
-                }
-            } else {
-                for (int z = 0; z < R; ++z) {
-                    acc = fmadd(w[z], sm.G[z * R + r], acc);
-                    acc = fmadd(ar[z], ldcg(&sm.Tt[z * R + r]), acc);
-                }
-            }
-            sm.Q[e] = acc;
-        }
+        PCG_TRACE(1);
+        // ---- Q = lam W + W Gamma^(n,n) + A T^(n)^T, partial <W,Q>
+        rows_mm<T>(sW, Gm, sA, Tt, (T)a.lam, sQ, rows, R, Rp);
         __syncthreads();
-        const double wq_p = dsum_rows(sm.W, sm.Q, len, sm.red);
+        double wq_p, unused;
+        dot2_rows<T>(sW, sQ, nullptr, nullptr, lenp, red, wq_p, unused);
         if (threadIdx.x == 0) part_wq[b] = wq_p;
+        PCG_TRACE(2);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
-        const double wq = block_gather_sum(part_wq, 0, (int)nb, bcast);
+        PCG_TRACE(3);
+        const double wq = gather_sum(part_wq, (int)nb, bcast);
         if (!isfinite(wq)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (!(wq > 0.0)) { set_status(status, CP_ERR_BREAKDOWN); break; }
         const double alpha = rz / wq;
         const T al = (T)alpha;
-        for (int e = threadIdx.x; e < len; e += blockDim.x) {
-            sm.V[e] = fmadd(al, sm.W[e], sm.V[e]);
-            sm.Rv[e] = fmadd(-al, sm.Q[e], sm.Rv[e]);
+        for (int e = threadIdx.x; e < lenp; e += blockDim.x) {
+            sV[e] = fmadd(al, sW[e], sV[e]);
+            sR[e] = fmadd(-al, sQ[e], sR[e]);
         }
         __syncthreads();
-        rows_times(sm.Rv, sm.P, sm.Z, rows, R);
+        rows_mm<T>(sR, Pm, nullptr, nullptr, (T)0, sZ, rows, R, Rp);
         __syncthreads();
-        rz_p = dsum_rows(sm.Rv, sm.Z, len, sm.red);
-        rn_p = dsum_rows(sm.Rv, sm.Rv, len, sm.red);
+        dot2_rows(sR, sZ, sR, sR, lenp, red, rz_p, rn_p);
         if (threadIdx.x == 0) { part_rz[b] = rz_p; part_rn[b] = rn_p; }
+        PCG_TRACE(4);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
+        PCG_TRACE(5);
         double rz_new;
         reduce_r(rz_new, rsum);
         ++it;
@@ -267,13 +487,17 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         const double beta = rz_new / rz;
         rz = rz_new;
         const T be = (T)beta;
-        for (int e = threadIdx.x; e < len; e += blockDim.x) sm.W[e] = fmadd(be, sm.W[e], sm.Z[e]);
+        for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = fmadd(be, sW[e], sZ[e]);
         __syncthreads();
-        y_partial(sm.A, sm.W, a.Ypart + (int64_t)b * RR, rows, R);
+        y_tiles(sA, sW, Ynext + (size_t)n * RR, rows, R, Rp);
+        PCG_TRACE(6);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < len; e += blockDim.x) a.V[goff + e] = sm.V[e];
+    for (int e = threadIdx.x; e < lenp; e += blockDim.x) {
+        const int k = e / Rp, c = e - k * Rp;
+        if (c < R) a.V[goff + k * R + c] = sV[e];
+    }
     if (b == 0 && threadIdx.x == 0) {
         a.stats->cg_iters = it;
         a.stats->cg_rnorm = rsum;
@@ -281,8 +505,9 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
 }
 
 template <typename T>
-static size_t pcg_smem_bytes(int R, int rpb_max, bool stage) {
-    return (size_t)((stage ? 3 : 0) * R * R + 6 * rpb_max * R) * sizeof(T) + 64 * sizeof(double);
+static size_t pcg_smem_bytes(int N, int R, int rpb_max, bool /*stage*/) {
+    const size_t Rp = (size_t)((R + 3) & ~3);
+    return ((size_t)(N + 2) * R * Rp + 6 * (size_t)rpb_max * Rp) * sizeof(T) + 80 * sizeof(double);
 }
 
 template <typename T>
@@ -299,7 +524,6 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
                               : (sizeof(T) == 8 ? sms : (int)std::min<int64_t>(sms, (rows_total + 31) / 32));
     if (const char* env = getenv(sizeof(T) == 8 ? "CPGN_PCG_BLOCKS_F64" : "CPGN_PCG_BLOCKS_F32")) want = atoi(env);
     int target = std::max(s.N, std::min<int>(want, (int)std::min<int64_t>(rows_total, 4096)));
-    // choose the blocks per mode so that the smem of the largest block fits
     const size_t budget = 200 * 1024;
     for (int attempt = 0; attempt < 64; ++attempt) {
         int total = 0, rpb_max = 1;
@@ -315,10 +539,16 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
         }
         a.mode_blk0[s.N] = total;
         a.nblocks = total;
-        bool stage = pcg_smem_bytes<T>(s.R, rpb_max, true) <= budget;
-        size_t bytes = pcg_smem_bytes<T>(s.R, rpb_max, stage);
+        const bool stage = true;
+        const size_t bytes = pcg_smem_bytes<T>(s.N, s.R, rpb_max, stage);
+        if ((size_t)(s.N + 2) * s.R * ((s.R + 3) & ~3) * sizeof(T) + 80 * sizeof(double) > budget)
+            return CP_ERR_UNSUPPORTED;  // the R x R matrices alone exceed shared memory (large R)
         if (bytes > budget) {  // rows do not fit: more blocks
             target = target * 2;
+            continue;
+        }
+        if (total > 32 * kGatherPerLane) {  // the scalar gathers cover at most 256 blocks
+            target = 32 * kGatherPerLane - s.N;
             continue;
         }
         cudaFuncSetAttribute(pcg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -333,11 +563,20 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
         int stage_i = stage ? 1 : 0;
         void* args[] = {(void*)&a, (void*)&stage_i};
         cudaError_t e = cudaLaunchCooperativeKernel((void*)pcg_kernel<T>, dim3(total), dim3(kThreads), args, bytes, st);
-        return e == cudaSuccess ? CP_OK : CP_ERR_CUDA;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return CP_ERR_CUDA;
+        }
+        return CP_OK;
     }
     return CP_ERR_UNSUPPORTED;
 }
 template cp_status launch_pcg<double>(PcgArgs<double>&, int, cudaStream_t);
+#ifdef CPGN_PCG_TRACE
+extern "C" int cpgn_pcg_trace_copy(long long* host) {
+    return cudaMemcpyFromSymbol(host, g_pcg_trace, sizeof(long long) * 8 * 64) != cudaSuccess;
+}
+#endif
 template cp_status launch_pcg<float>(PcgArgs<float>&, int, cudaStream_t);
 
 // ------------------------------------------------------------ plain matvec

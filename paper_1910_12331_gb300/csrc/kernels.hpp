@@ -52,10 +52,10 @@ struct PcgArgs {
     const T* GamT;      // N*N*R*R Gamma in T
     const T* PinvT;     // N*R*R preconditioner in T
     const double* G;    // packed FP64 gradient
-    T* V; T* Rv; T* Z; T* W; T* Q;   // packed CG vectors
-    T* Ypart;           // [nblocks][R*R] per-block partial A^T W
-    T* Tm;              // N*R*R: T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p)
-    double* part;       // [4][nblocks] per-block partial scalars
+    T* V;               // packed update (output)
+    T* Yacc;            // [2][N][R*R]: A^(p)T W^(p) accumulated by all blocks (buffer 0 zeroed by the host)
+    T* Tm;              // N*R*R scratch for T^(n) when it does not fit in shared memory
+    double* part;       // [3][nblocks] per-block partial scalars
     GridBarrier* bar;
     DevStats* stats;
     double lam;
