@@ -41,7 +41,7 @@ struct cp_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch;
-    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes;
+    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf;
     DevStats* h_stats = nullptr;  // pinned
     SplitCache split;             // bf16 planes of X (tensor-core path)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
@@ -181,9 +181,11 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         CP_TRY(grow(h->stats, sizeof(DevStats)));
         CP_TRY(grow(h->resid_planes, (size_t)2 * s.dims[0] * s.mid * tc_row_pitch(s.dims[s.N - 1]) * 2));
         DevStats* ds = (DevStats*)h->stats.p;
-        launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, tc_row_pitch(s.dims[s.N - 1]), ds, h->stream);
+        CP_TRY(grow(h->Adf, (size_t)s.roff[s.N] * s.R * 2 * sizeof(float)));
+        launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, tc_row_pitch(s.dims[s.N - 1]), h->Adf.p, ds,
+                           h->stream);
         CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
-        h->launches += 1 + (s.R + 63) / 64 * (2 + (s.N - 2) + 2);
+        h->launches += 2 + (s.R + 63) / 64 * (2 + (s.N - 2) + 2);
     } else {
         return CP_ERR_ARG;
     }
@@ -242,7 +244,7 @@ cp_status cp_destroy(cp_handle h) {
         cudaStreamSynchronize(h->stream);
         DevBuf* bufs[] = {&h->gram_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
                           &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
-                          &h->stats, &h->Y, &h->resid_planes};
+                          &h->stats, &h->Y, &h->resid_planes, &h->Adf};
         for (DevBuf* b : bufs)
             if (b->p) cudaFree(b->p);
         if (h->h_stats) cudaFreeHost(h->h_stats);

@@ -19,11 +19,21 @@
 namespace cpgn {
 
 namespace {
-constexpr int TI = 64, TK = 64, RC = 32, NT = 256;
+constexpr int TI = 64, TK = 64, RC = 32, NT = 128;
 
 __device__ __forceinline__ float2 split_df(double d) {
     const float hi = (float)d;
     return make_float2(hi, (float)(d - (double)hi));
+}
+
+// (hi, lo) product of two double-float numbers (lo*lo dropped), normalised
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
 }
 
 // acc += a * b in double-float (a, b, acc as (hi, lo)); the lo*lo term is dropped.
@@ -40,13 +50,32 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float2 a, float2 b)
 }
 }  // namespace
 
+// Error-free sum s + e = a + b (Knuth two-sum)
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+// acc (hi, lo) += x * x in double-float
+__device__ __forceinline__ void df_sq_acc(float& h, float& l, float x) {
+    const float p = x * x;
+    const float pe = fmaf(x, x, -p);
+    float s, e;
+    two_sum_f(h, p, s, e);
+    h = s;
+    l += e + pe;
+}
+
+// Block tile 64 (i) x 64 (k) outputs, 128 threads, each an 8 x 4 register tile
+// (rows 8*ti + u, columns tk + 16 c).
 template <typename TX>
-__global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __restrict__ X, Ptrs<const double> A,
+__global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __restrict__ X,
+                                                        const float2* __restrict__ Adf,
                                                         __nv_bfloat16* __restrict__ planes, int64_t sNp,
                                                         DevStats* stats) {
     __shared__ float2 As[RC][TI];
     __shared__ float2 Bs[RC][TK];
-    __shared__ double ws[RC];
+    __shared__ float2 ws[RC];
     __shared__ double red[32];
     const int64_t m = blockIdx.x;
     const int64_t i0 = (int64_t)blockIdx.y * TI, k0 = (int64_t)blockIdx.z * TK;
@@ -60,18 +89,18 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
             t /= s.dims[q];
         }
     }
-    const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;  // rows ti*4+u, columns tk+16c
-    float sh[4][4], sl[4][4];
+    const int ti = threadIdx.x >> 4, tk = threadIdx.x & 15;
+    float sh[8][4], sl[8][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
         for (int c = 0; c < 4; ++c) sh[u][c] = sl[u][c] = 0.0f;
     for (int r0 = 0; r0 < R; r0 += RC) {
         if (threadIdx.x < RC) {
-            double w = 0.0;
+            float2 w = make_float2(0.f, 0.f);
             if (r0 + (int)threadIdx.x < R) {
-                w = 1.0;
-                for (int q = 1; q + 1 < N; ++q) w *= A.p[q][idx[q] * R + r0 + threadIdx.x];
+                w = make_float2(1.f, 0.f);
+                for (int q = 1; q + 1 < N; ++q) w = df_mul(w, Adf[(s.roff[q] + idx[q]) * R + r0 + threadIdx.x]);
             }
             ws[threadIdx.x] = w;
         }
@@ -80,34 +109,35 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
             const int rr = t / TI, ii = t % TI;
             const int64_t i = i0 + ii;
             const int r = r0 + rr;
-            As[rr][ii] = (i < s1 && r < R) ? split_df(A.p[0][i * R + r]) : make_float2(0.f, 0.f);
+            As[rr][ii] = (i < s1 && r < R) ? Adf[i * R + r] : make_float2(0.f, 0.f);
         }
         for (int t = threadIdx.x; t < RC * TK; t += NT) {
             const int rr = t / TK, kk = t % TK;
             const int64_t k = k0 + kk;
             const int r = r0 + rr;
-            Bs[rr][kk] = (k < sN && r < R) ? split_df(ws[rr] * A.p[N - 1][k * R + r]) : make_float2(0.f, 0.f);
+            Bs[rr][kk] = (k < sN && r < R) ? df_mul(ws[rr], Adf[(s.roff[N - 1] + k) * R + r]) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll 4
-        for (int rr = 0; rr < RC; ++rr) {
-            float2 a[4], b[4];
+        const int rn = R - r0 < RC ? R - r0 : RC;
+#pragma unroll 2
+        for (int rr = 0; rr < rn; ++rr) {
+            float2 a[8], b[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = As[rr][ti * 4 + u];
+            for (int u = 0; u < 8; ++u) a[u] = As[rr][ti * 8 + u];
 #pragma unroll
             for (int c = 0; c < 4; ++c) b[c] = Bs[rr][tk + 16 * c];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) df_mac(sh[u][c], sl[u][c], a[u], b[c]);
         }
         __syncthreads();
     }
-    double num = 0.0, den = 0.0;
+    float nh = 0.f, nl = 0.f, dh = 0.f, dl = 0.f;
     const int64_t total_p = s1 * mid * sNp;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int64_t i = i0 + ti * 4 + u;
+    for (int u = 0; u < 8; ++u) {
+        const int64_t i = i0 + ti * 8 + u;
         if (i >= s1) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -119,11 +149,13 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
                 if constexpr (sizeof(TX) == 4) {
                     // x - sh is exact when the reconstruction is close (Sterbenz)
                     e = (x - sh[u][c]) - sl[u][c];
+                    df_sq_acc(dh, dl, x);
                 } else {
                     e = (float)((x - (double)sh[u][c]) - (double)sl[u][c]);
+                    const float xh = (float)x;
+                    df_sq_acc(dh, dl, xh);
                 }
-                num += (double)e * (double)e;
-                den += (double)x * (double)x;
+                df_sq_acc(nh, nl, e);
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(e);
             const __nv_bfloat16 lo = __float2bfloat16_rn(e - __bfloat162float(hi));
@@ -132,21 +164,32 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
             planes[total_p + o] = lo;
         }
     }
-    num = block_sum(num, red);
-    den = block_sum(den, red);
+    // per-thread double-float partials, combined in FP64 across the block
+    double num = block_sum((double)nh + (double)nl, red);
+    double den = block_sum((double)dh + (double)dl, red);
     if (threadIdx.x == 0) {
         atomicAdd(&stats->eres_num, num);
         atomicAdd(&stats->eres_den, den);
     }
 }
 
+// packed double-float copy of every factor: Adf[row][r] = (hi, lo) of A^(n)[i][r]
+__global__ void factors_df_kernel(Shape s, Ptrs<const double> A, float2* Adf) {
+    const int n = blockIdx.y;
+    const int64_t len = s.dims[n] * s.R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+        Adf[s.roff[n] * s.R + e] = split_df(A.p[n][e]);
+}
+
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                        int64_t sNp, DevStats* stats, cudaStream_t st) {
+                        int64_t sNp, void* Adf_scratch, DevStats* stats, cudaStream_t st) {
+    float2* Adf = (float2*)Adf_scratch;
+    factors_df_kernel<<<dim3(32, s.N), 256, 0, st>>>(s, A, Adf);
     dim3 grid((unsigned)s.mid, (unsigned)((s.dims[0] + TI - 1) / TI), (unsigned)((sNp + TK - 1) / TK));
     if (xdt == CP_F32)
-        resid_split_kernel<float><<<grid, NT, 0, st>>>(s, (const float*)X, A, (__nv_bfloat16*)planes, sNp, stats);
+        resid_split_kernel<float><<<grid, NT, 0, st>>>(s, (const float*)X, Adf, (__nv_bfloat16*)planes, sNp, stats);
     else
-        resid_split_kernel<double><<<grid, NT, 0, st>>>(s, (const double*)X, A, (__nv_bfloat16*)planes, sNp, stats);
+        resid_split_kernel<double><<<grid, NT, 0, st>>>(s, (const double*)X, Adf, (__nv_bfloat16*)planes, sNp, stats);
 }
 
 }  // namespace cpgn
