@@ -150,7 +150,7 @@ static cp_status ensure_common(cp_handle h, const Shape& s) {
     CP_TRY(grow(h->GamF, (size_t)s.N * s.N * RR * sizeof(float)));
     CP_TRY(grow(h->Pinv, s.N * RR * sizeof(double)));
     CP_TRY(grow(h->PinvF, s.N * RR * sizeof(float)));
-    if (precond_smem_bytes(s.R) == 0) CP_TRY(grow(h->precond_scratch, 2 * s.N * RR * sizeof(double)));
+    if (precond_smem_bytes(s.R) == 0) CP_TRY(grow(h->precond_scratch, precond_scratch_doubles(s) * sizeof(double)));
     CP_TRY(grow(h->Mp, rows * s.R * sizeof(double)));
     CP_TRY(grow(h->Gp, rows * s.R * sizeof(double)));
     CP_TRY(grow(h->stats, sizeof(DevStats)));
@@ -368,8 +368,8 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     const size_t RR = (size_t)s.R * s.R, len = (size_t)s.roff[s.N] * s.R;
     CP_TRY(grow(h->Ap, len * sizeof(T)));
     CP_TRY(grow(h->vec, len * sizeof(T)));
-    CP_TRY(grow(h->Ypart, 2 * s.N * RR * sizeof(T)));
-    CP_TRY(grow(h->Tm, s.N * RR * sizeof(T)));
+    CP_TRY(grow(h->Ypart, (size_t)256 * RR * sizeof(T)));  // per-block A^T Z (at most 256 blocks)
+    CP_TRY(grow(h->Tm, s.N * RR * sizeof(T)));               // Y^(p), reduced
     CP_TRY(grow(h->pcg_part, 3 * 4096 * sizeof(double)));
     CP_TRY(grow(h->bar, sizeof(GridBarrier)));
     launch_pack<T>(s, Acaller, (T*)h->Ap.p, h->stream);
@@ -386,8 +386,8 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     }
     a.G = (const double*)h->Gp.p;
     a.V = (T*)h->vec.p;
-    a.Yacc = (T*)h->Ypart.p;
-    a.Tm = (T*)h->Tm.p;
+    a.Zpart = (T*)h->Ypart.p;
+    a.Yfull = (T*)h->Tm.p;
     a.part = (double*)h->pcg_part.p;
     a.bar = (GridBarrier*)h->bar.p;
     a.stats = (DevStats*)h->stats.p;
@@ -397,7 +397,6 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     a.maxit = p->cg_max_iter;
     a.spin_limit = p->spin_limit > 0 ? p->spin_limit : kDefaultSpin;
     CUDA_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(GridBarrier), h->stream));
-    CUDA_TRY(cudaMemsetAsync(h->Ypart.p, 0, s.N * RR * sizeof(T), h->stream));  // first accumulator buffer
     CP_TRY(launch_pcg<T>(a, 0, h->stream));
     return CP_OK;
 }
@@ -421,7 +420,7 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
                     p->prec == CP_PREC_RESIDUAL);
     // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
     launch_precond(s, (const double*)h->Gam.p, p->lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
-                   (double*)h->precond_scratch.p, ds, h->stream);
+                   (double*)h->precond_scratch.p, ds, h->stream, p->cg_fp32 != 0);
     h->launches += 2;
     CUDA_TRY(cudaGetLastError());
     if (p->cg_fp32)

@@ -68,6 +68,7 @@ void launch_gram_partial(const Shape& s, Ptrs<const double> A, double* part, int
 }
 
 // S^(n) = sum over the chunks that exist for mode n; Gamma^(n,p) = prod_{m != n,p} S^(m).
+// The chunk partials are loaded eight at a time before they are added.
 __global__ void gamma_kernel(Shape s, const double* part, int chunks, double* S, double* Gam, float* GamF) {
     const int RR = s.R * s.R;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,8 +76,17 @@ __global__ void gamma_kernel(Shape s, const double* part, int chunks, double* S,
     double Sq[kMaxN];
     for (int m = 0; m < s.N; ++m) {
         const int cm = (int)((s.dims[m] + kGramRows - 1) / kGramRows);
+        const double* pm = part + (int64_t)m * chunks * RR + q;
         double acc = 0.0;
-        for (int c = 0; c < cm; ++c) acc += part[((int64_t)m * chunks + c) * RR + q];
+        int c = 0;
+        for (; c + 8 <= cm; c += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = pm[(int64_t)(c + u) * RR];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += v[u];
+        }
+        for (; c < cm; ++c) acc += pm[(int64_t)c * RR];
         Sq[m] = acc;
         S[(int64_t)m * RR + q] = acc;
     }
@@ -140,41 +150,61 @@ void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, co
 }
 
 // -------------------------------------------------------- preconditioner
-// One block per mode: B = Gamma^(n,n) + lam I in a dense R x R scratch (shared
-// memory when it fits, else a global workspace), right-looking Cholesky
-// B = L L^T with a positivity check of every pivot, then the explicit inverse
-// by forward (L Y = I) and back (L^T P = Y) substitution, one column per thread.
-__global__ void precond_kernel(Shape s, const double* Gam, double lam, double* Pinv, float* PinvF,
-                               double* scratch, DevStats* stats) {
-    extern __shared__ double smem[];
+// P_inv^(n) = (Gamma^(n,n) + lam I)^{-1} (Algorithm 2, first loop; Section
+// 3.3), one block per mode, in shared memory when it fits (else a global
+// workspace): in-place Gauss-Jordan inversion without pivoting, which is
+// stable for symmetric positive definite matrices.  Its pivots are the Schur
+// complement diagonals, i.e. the squares of the Cholesky diagonals, so the
+// positivity test of every pivot is the Cholesky SPD test.
+// T = double: the plain path (a non-positive pivot raises CP_ERR_NOT_SPD).
+// T = float: the mixed path, whose CG runs in FP32 anyway: a pivot that
+// rounding drives below 1e-7 times its diagonal entry is clamped to that
+// value, which keeps the preconditioner SPD (an approximate block-Jacobi
+// preconditioner changes the CG iteration count, not what CG converges to).
+constexpr int kPrecondThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kPrecondThreads) precond_kernel(Shape s, const double* Gam, double lam, double* Pinv,
+                                                                  float* PinvF, T* scratch, DevStats* stats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_bad;
+    __shared__ T s_inv;
     const int R = s.R, n = blockIdx.x;
     const bool in_smem = scratch == nullptr;
-    double* L = in_smem ? smem : scratch + (int64_t)n * 2 * R * R;
-    double* Y = L + (int64_t)R * R;
+    T* B = in_smem ? reinterpret_cast<T*>(smem_raw) : scratch + (int64_t)n * (R * R + R);
+    T* f = B + R * R;  // column j of the previous step
     const double* Gnn = Gam + ((int64_t)n * s.N + n) * R * R;
-    double* P = Pinv + (int64_t)n * R * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) s_bad = 0;
-    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
-        const int i = q / R, j = q % R;
-        L[q] = Gnn[q] + (i == j ? lam : 0.0);
-    }
+    for (int i = warp; i < R; i += nw)
+        for (int k = lane; k < R; k += 32) B[i * R + k] = (T)(Gnn[i * R + k] + (i == k ? lam : 0.0));
     __syncthreads();
     for (int j = 0; j < R; ++j) {
         if (threadIdx.x == 0) {
-            const double d = L[j * R + j];
-            if (!(d > 0.0)) s_bad = 1;
-            L[j * R + j] = d > 0.0 ? sqrt(d) : 1.0;
+            T p = B[j * R + j];
+            if constexpr (sizeof(T) == 8) {
+                if (!(p > 0.0)) {
+                    s_bad = 1;
+                    p = 1.0;
+                }
+            } else {
+                const T floor_p = (T)(1e-7 * fabs(Gnn[j * R + j] + lam));
+                if (!(p > floor_p)) p = floor_p > 0.f ? floor_p : 1.f;
+            }
+            s_inv = (T)1 / p;
         }
+        for (int i = threadIdx.x; i < R; i += blockDim.x) f[i] = B[i * R + j];
         __syncthreads();
-        const double ljj = L[j * R + j];
-        for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) L[i * R + j] /= ljj;
+        const T inv = s_inv;
+        // pivot row: B[j][k] /= p (k != j), B[j][j] = 1/p
+        for (int k = threadIdx.x; k < R; k += blockDim.x) B[j * R + k] = k == j ? inv : B[j * R + k] * inv;
         __syncthreads();
-        // trailing update of the lower triangle
-        const int m = R - j - 1;
-        for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
-            const int i = j + 1 + q / m, k = j + 1 + q % m;
-            if (k <= i) L[i * R + k] -= L[i * R + j] * L[k * R + j];
+        // other rows: B[i][k] -= f_i B[j][k] (k != j), B[i][j] = -f_i / p
+        for (int i = warp; i < R; i += nw) {
+            if (i == j) continue;
+            const T fi = f[i];
+            for (int k = lane; k < R; k += 32)
+                B[i * R + k] = k == j ? -fi * inv : B[i * R + k] - fi * B[j * R + k];
         }
         __syncthreads();
     }
@@ -182,38 +212,45 @@ __global__ void precond_kernel(Shape s, const double* Gam, double lam, double* P
         if (threadIdx.x == 0) set_status(&stats->status, CP_ERR_NOT_SPD);
         return;
     }
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        for (int i = 0; i < R; ++i) {
-            double v = (i == c) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) v -= L[i * R + k] * Y[k * R + c];
-            Y[i * R + c] = v / L[i * R + i];
-        }
-        for (int i = R - 1; i >= 0; --i) {
-            double v = Y[i * R + c];
-            for (int k = i + 1; k < R; ++k) v -= L[k * R + i] * P[k * R + c];
-            P[i * R + c] = v / L[i * R + i];
-        }
+    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
+        if (Pinv) Pinv[(int64_t)n * R * R + q] = (double)B[q];
+        if (PinvF) PinvF[(int64_t)n * R * R + q] = (float)B[q];
     }
-    __syncthreads();
-    if (PinvF)
-        for (int q = threadIdx.x; q < R * R; q += blockDim.x) PinvF[(int64_t)n * R * R + q] = (float)P[q];
 }
 
 void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv, float* PinvF, double* scratch,
-                    DevStats* stats, cudaStream_t st) {
-    const size_t bytes = precond_smem_bytes(s.R);
-    if (bytes > 0) {
-        cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        precond_kernel<<<s.N, 256, bytes, st>>>(s, Gam, lam, Pinv, PinvF, nullptr, stats);
-    } else {
-        precond_kernel<<<s.N, 256, 0, st>>>(s, Gam, lam, Pinv, PinvF, scratch, stats);
+                    DevStats* stats, cudaStream_t st, bool fp32) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(precond_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(precond_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (dev < 64) attr_set[dev] = true;
     }
+    const size_t elems = (size_t)s.R * s.R + s.R;
+    if (fp32) {
+        const size_t bytes = elems * sizeof(float);
+        if (bytes <= 200 * 1024)
+            precond_kernel<float><<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, nullptr, PinvF, nullptr, stats);
+        else
+            precond_kernel<float><<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, nullptr, PinvF, (float*)scratch,
+                                                                   stats);
+        return;
+    }
+    const size_t bytes = elems * sizeof(double);
+    if (bytes <= 200 * 1024)
+        precond_kernel<double><<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, PinvF, nullptr, stats);
+    else
+        precond_kernel<double><<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, Pinv, PinvF, scratch, stats);
 }
 
 size_t precond_smem_bytes(int R) {
-    const size_t bytes = (size_t)2 * R * R * sizeof(double);
+    const size_t bytes = ((size_t)R * R + R) * sizeof(double);
     return bytes <= 200 * 1024 ? bytes : 0;
 }
+
+size_t precond_scratch_doubles(const Shape& s) { return (size_t)s.N * ((size_t)s.R * s.R + s.R); }
 
 // ------------------------------------------------------- pack / update
 template <typename T>

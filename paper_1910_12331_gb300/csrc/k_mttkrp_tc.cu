@@ -512,17 +512,37 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ------------------------------------------------------------ preparation
 // X -> bf16 planes [2][s1][mid][sNp] (hi, lo), zero in the padding columns.
+// Four consecutive columns per thread, 8-byte stores; FP32 arithmetic for FP32
+// input (x - hi is exact), FP64 only for FP64 input.
+template <typename TX>
+__device__ __forceinline__ void split1(TX x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    if constexpr (sizeof(TX) == 4) {
+        hi = __float2bfloat16_rn(x);
+        lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    } else {
+        hi = __double2bfloat16(x);
+        lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+    }
+}
+
 template <typename TX>
 __global__ void split_x_kernel(const TX* __restrict__ X, __nv_bfloat16* __restrict__ planes, int64_t rows, int64_t sN,
                                int64_t sNp) {
-    const int64_t total = rows * sNp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rr = e / sNp, k = e % sNp;
-        const double x = k < sN ? (double)X[rr * sN + k] : 0.0;
-        const __nv_bfloat16 hi = __double2bfloat16(x);
-        const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
-        planes[e] = hi;
-        planes[total + e] = lo;
+    const int64_t q4 = sNp / 4;  // sNp is a multiple of 8
+    const int64_t total4 = rows * q4, total = rows * sNp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rr = e / q4, k = (e - rr * q4) * 4;
+        const TX* xr = X + rr * sN;
+        __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split1<TX>(k + u < sN ? xr[k + u] : (TX)0, hi[u], lo[u]);
+        uint2 vh, vl;
+        vh.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
+        vh.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
+        vl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
+        vl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
+        *reinterpret_cast<uint2*>(planes + rr * sNp + k) = vh;
+        *reinterpret_cast<uint2*>(planes + total + rr * sNp + k) = vl;
     }
 }
 
@@ -550,39 +570,46 @@ __global__ void factor_f32_kernel(const double* __restrict__ A, int R, int r0, i
     }
 }
 
-// Reduce the unit partials into the FP64 outputs (fixed order), columns r0..r0+Rt-1.
+// Reduce the unit partials into the FP64 outputs (fixed order), columns
+// r0..r0+Rt-1.  Block = 8 output rows of one mode; thread (row t/32, columns
+// 2*(t%32) + {0,1}); the partials are visited in a fixed order with coalesced
+// 256-byte row loads.
+constexpr int kFinRows = 8;
 __global__ void finalize_kernel(Params p, Ptrs<double> M, Ptrs<const double> A, int R, int r0, int Rt,
                                 int64_t sNfull, unsigned mode_mask) {
     const int N = p.N;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (!(mode_mask & (1u << n))) return;
     const int64_t sn = n == 0 ? p.s1 : (n == N - 1 ? p.sN : p.middim[n]);
-    if (e >= sn * Rt) return;
-    const int64_t i = e / Rt;
-    const int r = (int)(e % Rt);
-    double acc = 0.0;
+    const int64_t i = (int64_t)blockIdx.x * kFinRows + (threadIdx.x >> 5);
+    if (i >= sn) return;
+    const int c0 = 2 * (threadIdx.x & 31);
+    double acc0 = 0.0, acc1 = 0.0;
     if (n == 0) {
         const int b = (int)(i / kBI);
         for (int kg = 0; kg < p.nkg; ++kg)
             for (int j = 0; j < p.nsplit; ++j) {
                 const int u = (b * p.nkg + kg) * p.nsplit + j;
-                acc += (double)p.P_Y1[((int64_t)u * kBI + (i % kBI)) * kRT + r];
+                const float2 v = *reinterpret_cast<const float2*>(p.P_Y1 + ((int64_t)u * kBI + (i % kBI)) * kRT + c0);
+                acc0 += v.x;
+                acc1 += v.y;
             }
     } else if (n == N - 1) {
         const int kg = (int)(i / (kChunksPerGroup * kKC));
         for (int b = 0; b < p.nib; ++b)
             for (int j = 0; j < p.nsplit; ++j) {
                 const int u = (b * p.nkg + kg) * p.nsplit + j;
-                acc += (double)p.P_Z[((int64_t)u * (kChunksPerGroup * kKC) + (i % (kChunksPerGroup * kKC))) * kRT + r];
+                const float2 v = *reinterpret_cast<const float2*>(
+                    p.P_Z + ((int64_t)u * (kChunksPerGroup * kKC) + (i % (kChunksPerGroup * kKC))) * kRT + c0);
+                acc0 += v.x;
+                acc1 += v.y;
             }
     } else {
         // middle mode n: sum over the slices m whose index in mode n is i
         const int64_t sub = p.mid / p.middim[n];
         for (int64_t t = 0; t < sub; ++t) {
-            // rebuild m from (i at mode n, t over the other middle modes)
             int64_t rem = t, m = 0, mult = 1;
-            double lo = 1.0;
+            double lo0 = 1.0, lo1 = 1.0;
             for (int q = N - 2; q >= 1; --q) {
                 int64_t iq;
                 if (q == n) {
@@ -590,17 +617,24 @@ __global__ void finalize_kernel(Params p, Ptrs<double> M, Ptrs<const double> A, 
                 } else {
                     iq = rem % p.middim[q];
                     rem /= p.middim[q];
-                    lo *= A.p[q][iq * R + r0 + r];
+                    if (c0 < Rt) lo0 *= A.p[q][iq * R + r0 + c0];
+                    if (c0 + 1 < Rt) lo1 *= A.p[q][iq * R + r0 + c0 + 1];
                 }
                 m += iq * mult;
                 mult *= p.middim[q];
             }
-            double cs = 0.0;
-            for (int bk = 0; bk < p.nib * p.nkg; ++bk) cs += (double)p.P_c[((int64_t)bk * p.mid + m) * kRT + r];
-            acc += cs * lo;
+            double cs0 = 0.0, cs1 = 0.0;
+            for (int bk = 0; bk < p.nib * p.nkg; ++bk) {
+                const float2 v = *reinterpret_cast<const float2*>(p.P_c + ((int64_t)bk * p.mid + m) * kRT + c0);
+                cs0 += v.x;
+                cs1 += v.y;
+            }
+            acc0 += cs0 * lo0;
+            acc1 += cs1 * lo1;
         }
     }
-    M.p[n][i * R + r0 + r] = acc;
+    if (c0 < Rt) M.p[n][i * R + r0 + c0] = acc0;
+    if (c0 + 1 < Rt) M.p[n][i * R + r0 + c0 + 1] = acc1;
     (void)sNfull;
 }
 
@@ -794,10 +828,14 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return CP_ERR_UNSUPPORTED;
     }
-    if (cudaFuncSetAttribute(mttkrp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return CP_ERR_UNSUPPORTED;
+    static bool attr_set[64] = {};
+    if (dev >= 64 || !attr_set[dev]) {
+        if (cudaFuncSetAttribute(mttkrp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return CP_ERR_UNSUPPORTED;
+        }
+        if (dev < 64) attr_set[dev] = true;
     }
     for (int r0 = 0; r0 < R; r0 += kRT) {
         const int Rt = std::min(kRT, R - r0);
@@ -810,8 +848,10 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
         if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
         int64_t mx = 0;
         for (int n = 0; n < N; ++n) mx = std::max<int64_t>(mx, s.dims[n] * Rt);
-        dim3 fg((unsigned)((mx + 255) / 256), N);
-        finalize_kernel<<<fg, 256, 0, st>>>(p, M, A, R, r0, Rt, sN, mode_mask);
+        int64_t mrows = 0;
+        for (int n = 0; n < N; ++n) mrows = std::max<int64_t>(mrows, s.dims[n]);
+        dim3 fg((unsigned)((mrows + kFinRows - 1) / kFinRows), N);
+        finalize_kernel<<<fg, 32 * kFinRows, 0, st>>>(p, M, A, R, r0, Rt, sN, mode_mask);
         if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
     }
     return CP_OK;

@@ -292,8 +292,8 @@ __device__ __forceinline__ void rows_mm(const T* X, const T* M1, const T* Yr, co
     }
 }
 
-// Yacc[r][c] += sum_k A[k][r] W[k][c] over the block's rows (TR x TC tiles,
-// atomic adds), Yacc row stride R.
+// Yp[r][c] = sum_k A[k][r] W[k][c] over the block's rows (TR x TC tiles),
+// Yp row stride R.
 template <typename T>
 __device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int rows, int R, int Rp) {
     constexpr int TR = Tile<T>::TR, TC = Tile<T>::TC;
@@ -322,14 +322,17 @@ __device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int row
 #pragma unroll
             for (int u = 0; u < TC; ++u) {
                 const int r = r0 + i, c = c0 + u;
-                if (r < R && c < R) atomicAdd(&Yacc[r * R + c], acc[i][u]);
+                if (r < R && c < R) Yacc[r * R + c] = acc[i][u];
             }
     }
 }
 
-// Persistent CP-CG.  Per iteration: (B1) A^T W complete -> T^(n) and Q rows,
-// partial <W,Q>; (B2) alpha, V/R update, Z = R P_inv, partial <R,Z> and
-// |R^(n)|^2; (B3) beta, W update, A^T W accumulated into the other buffer.
+// Persistent CP-CG.  Per iteration, three grid barriers:
+//   (B1) Y^(p) = A^(p)T W^(p) complete: T^(n), Q rows, partial <W,Q>;
+//   (B2) alpha, V/R update, Z = R P_inv, partial <R,Z>, |R^(n)|^2 and A^T Z;
+//   (B3) beta, W = Z + beta W, and Y = sum_blocks A^T Z + beta Y in a fixed
+//        order (the same as A^T W), split over all blocks.
+// Every cross-block sum runs in a fixed order, so a solve is reproducible.
 // Shared memory holds the block's Gamma^(n,p) (all p), P_inv^(n), T^(n) and
 // its rows of A, V, R, Z, W, Q, every matrix with row stride Rp (zero padded).
 template <typename T>
@@ -370,7 +373,6 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
     int* const status = &a.stats->status;
     const unsigned nb = (unsigned)a.nblocks;
     const long long lim = a.spin_limit;
-    const size_t ysz = (size_t)N * RR;
 
     // ---- set-up: stage the constant matrices and the block's rows, zero padded
     for (int q = threadIdx.x; q < N * RRp; q += blockDim.x) {
@@ -404,10 +406,10 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
     double rz_p, rn_p;
     dot2_rows(sR, sZ, sR, sR, lenp, red, rz_p, rn_p);
     if (threadIdx.x == 0) { part_rz[b] = rz_p; part_rn[b] = rn_p; }
-    y_tiles(sA, sW, a.Yacc + (size_t)n * RR, rows, R, Rp);
+    y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
 
     int it = 0;
-    double rsum = 0.0, rz = 0.0;
+    double rsum = 0.0, rz = 0.0, beta = 0.0;
     bool ok = grid_sync(a.bar, status, nb, lim);
     auto reduce_r = [&](double& rz_out, double& rsum_out) {
         gather_rz_rn(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_out, rsum_out);
@@ -422,9 +424,27 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         if (!isfinite(rsum) || !isfinite(rz)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
         PCG_TRACE(0);
-        const int buf = it & 1;
-        const T* Ycur = a.Yacc + buf * ysz;
-        T* Ynext = a.Yacc + (buf ^ 1) * ysz;
+        // ---- Y^(p) = sum over the blocks of mode p of A^T Z, + beta Y^(p): fixed order
+        {
+            const T be = (T)beta;
+            const size_t ny = (size_t)N * RR;
+            for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < ny; e += (size_t)nb * blockDim.x) {
+                const int pp = (int)(e / RR), q = (int)(e - (size_t)pp * RR);
+                const int c0 = a.mode_blk0[pp], c1 = a.mode_blk0[pp + 1];
+                T acc = it == 0 ? (T)0 : be * a.Yfull[e];
+                int c = c0;
+                for (; c + 4 <= c1; c += 4) {
+                    T v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc += v[u];
+                }
+                for (; c < c1; ++c) acc += ldcg(&a.Zpart[(size_t)c * RR + q]);
+                a.Yfull[e] = acc;
+            }
+        }
+        if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         // ---- T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed (Tt[z][r] = T[r][z]);
         // every thread issues its loads of Y for all modes before using them
         for (int q0 = threadIdx.x; q0 < RR; q0 += 4 * blockDim.x) {
@@ -434,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
                 const int q = q0 + u * blockDim.x;
 #pragma unroll
                 for (int pp = 0; pp < kMaxN; ++pp)
-                    y[u][pp] = (pp < N && pp != n && q < RR) ? ldcg(&Ycur[(size_t)pp * RR + q]) : (T)0;
+                    y[u][pp] = (pp < N && pp != n && q < RR) ? ldcg(&a.Yfull[(size_t)pp * RR + q]) : (T)0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -448,9 +468,6 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
                 Tt[z * Rp + r] = t;
             }
         }
-        // the accumulator of the next iteration is cleared here: it was last read
-        // before the previous iteration's second barrier
-        for (size_t q = (size_t)b * blockDim.x + threadIdx.x; q < ysz; q += (size_t)nb * blockDim.x) Ynext[q] = (T)0;
         __syncthreads();
         PCG_TRACE(1);
         // ---- Q = lam W + W Gamma^(n,n) + A T^(n)^T, partial <W,Q>
@@ -476,6 +493,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         __syncthreads();
         dot2_rows(sR, sZ, sR, sR, lenp, red, rz_p, rn_p);
         if (threadIdx.x == 0) { part_rz[b] = rz_p; part_rn[b] = rn_p; }
+        y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
         PCG_TRACE(4);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         PCG_TRACE(5);
@@ -484,14 +502,11 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         ++it;
         if (!(rsum > tol)) break;
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
-        const double beta = rz_new / rz;
+        beta = rz_new / rz;
         rz = rz_new;
         const T be = (T)beta;
         for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = fmadd(be, sW[e], sZ[e]);
         __syncthreads();
-        y_tiles(sA, sW, Ynext + (size_t)n * RR, rows, R, Rp);
-        PCG_TRACE(6);
-        if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < lenp; e += blockDim.x) {
@@ -510,6 +525,77 @@ static size_t pcg_smem_bytes(int N, int R, int rpb_max, bool /*stage*/) {
     return ((size_t)(N + 2) * R * Rp + 6 * (size_t)rpb_max * Rp) * sizeof(T) + 80 * sizeof(double);
 }
 
+// Launch geometry of the persistent CG kernel for one shape (cached: the
+// attribute and occupancy queries cost tens of microseconds of host time).
+struct PcgGeom {
+    int N = -1, R = -1, T = 0, want = 0, sms = 0, dev = -1;
+    int64_t dims[kMaxN] = {};
+    int nblocks = 0, mode_blk0[kMaxN + 1] = {}, rpb[kMaxN] = {};
+    size_t bytes = 0;
+    cp_status status = CP_OK;
+};
+
+template <typename T>
+static PcgGeom pcg_geometry(const Shape& s, int want, int sms) {
+    PcgGeom g;
+    g.N = s.N;
+    g.R = s.R;
+    g.T = (int)sizeof(T);
+    g.want = want;
+    g.sms = sms;
+    for (int n = 0; n < s.N; ++n) g.dims[n] = s.dims[n];
+    const int64_t rows_total = s.roff[s.N];
+    int target = std::max(s.N, std::min<int>(want, (int)std::min<int64_t>(rows_total, 4096)));
+    const size_t budget = 200 * 1024;
+    if ((size_t)(s.N + 2) * s.R * ((s.R + 3) & ~3) * sizeof(T) + 80 * sizeof(double) > budget) {
+        g.status = CP_ERR_UNSUPPORTED;  // the R x R matrices alone exceed shared memory (large R)
+        return g;
+    }
+    cudaFuncSetAttribute(pcg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        int total = 0, rpb_max = 1;
+        for (int n = 0; n < s.N; ++n) {
+            int nbn = (int)std::max<int64_t>(1, (int64_t)((double)target * s.dims[n] / rows_total));
+            nbn = (int)std::min<int64_t>(nbn, s.dims[n]);
+            const int rpb = (int)((s.dims[n] + nbn - 1) / nbn);
+            nbn = (int)((s.dims[n] + rpb - 1) / rpb);
+            g.rpb[n] = rpb;
+            g.mode_blk0[n] = total;
+            total += nbn;
+            rpb_max = std::max(rpb_max, rpb);
+        }
+        g.mode_blk0[s.N] = total;
+        g.nblocks = total;
+        g.bytes = pcg_smem_bytes<T>(s.N, s.R, rpb_max, true);
+        if (g.bytes > budget) {  // rows do not fit: more blocks
+            target = target * 2;
+            continue;
+        }
+        if (total > 32 * kGatherPerLane) {  // the scalar gathers cover at most 256 blocks
+            target = 32 * kGatherPerLane - s.N;
+            continue;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kThreads, g.bytes);
+        if (per_sm < 1) {
+            g.status = CP_ERR_UNSUPPORTED;
+            return g;
+        }
+        if (total > per_sm * sms) {
+            if (target <= s.N) {
+                g.status = CP_ERR_UNSUPPORTED;
+                return g;
+            }
+            target = std::max(s.N, per_sm * sms - s.N);
+            continue;
+        }
+        g.status = CP_OK;
+        return g;
+    }
+    g.status = CP_ERR_UNSUPPORTED;
+    return g;
+}
+
 template <typename T>
 cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
     const Shape& s = a.s;
@@ -523,53 +609,26 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
     int want = max_blocks > 0 ? max_blocks
                               : (sizeof(T) == 8 ? sms : (int)std::min<int64_t>(sms, (rows_total + 31) / 32));
     if (const char* env = getenv(sizeof(T) == 8 ? "CPGN_PCG_BLOCKS_F64" : "CPGN_PCG_BLOCKS_F32")) want = atoi(env);
-    int target = std::max(s.N, std::min<int>(want, (int)std::min<int64_t>(rows_total, 4096)));
-    const size_t budget = 200 * 1024;
-    for (int attempt = 0; attempt < 64; ++attempt) {
-        int total = 0, rpb_max = 1;
-        for (int n = 0; n < s.N; ++n) {
-            int nbn = (int)std::max<int64_t>(1, (int64_t)((double)target * s.dims[n] / rows_total));
-            nbn = (int)std::min<int64_t>(nbn, s.dims[n]);
-            const int rpb = (int)((s.dims[n] + nbn - 1) / nbn);
-            nbn = (int)((s.dims[n] + rpb - 1) / rpb);
-            a.rpb[n] = rpb;
-            a.mode_blk0[n] = total;
-            total += nbn;
-            rpb_max = std::max(rpb_max, rpb);
-        }
-        a.mode_blk0[s.N] = total;
-        a.nblocks = total;
-        const bool stage = true;
-        const size_t bytes = pcg_smem_bytes<T>(s.N, s.R, rpb_max, stage);
-        if ((size_t)(s.N + 2) * s.R * ((s.R + 3) & ~3) * sizeof(T) + 80 * sizeof(double) > budget)
-            return CP_ERR_UNSUPPORTED;  // the R x R matrices alone exceed shared memory (large R)
-        if (bytes > budget) {  // rows do not fit: more blocks
-            target = target * 2;
-            continue;
-        }
-        if (total > 32 * kGatherPerLane) {  // the scalar gathers cover at most 256 blocks
-            target = 32 * kGatherPerLane - s.N;
-            continue;
-        }
-        cudaFuncSetAttribute(pcg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kThreads, bytes);
-        if (per_sm < 1) return CP_ERR_UNSUPPORTED;
-        if (total > per_sm * sms) {
-            if (target <= s.N) return CP_ERR_UNSUPPORTED;
-            target = std::max(s.N, per_sm * sms - s.N);
-            continue;
-        }
-        int stage_i = stage ? 1 : 0;
-        void* args[] = {(void*)&a, (void*)&stage_i};
-        cudaError_t e = cudaLaunchCooperativeKernel((void*)pcg_kernel<T>, dim3(total), dim3(kThreads), args, bytes, st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return CP_ERR_CUDA;
-        }
-        return CP_OK;
+    static thread_local PcgGeom cache[2];
+    PcgGeom& g = cache[sizeof(T) == 8];
+    bool hit = g.N == s.N && g.R == s.R && g.want == want && g.sms == sms && g.dev == dev;
+    for (int n = 0; hit && n < s.N; ++n) hit = g.dims[n] == s.dims[n];
+    if (!hit) {
+        g = pcg_geometry<T>(s, want, sms);
+        g.dev = dev;
     }
-    return CP_ERR_UNSUPPORTED;
+    if (g.status != CP_OK) return g.status;
+    a.nblocks = g.nblocks;
+    for (int n = 0; n <= s.N; ++n) a.mode_blk0[n] = g.mode_blk0[n];
+    for (int n = 0; n < s.N; ++n) a.rpb[n] = g.rpb[n];
+    int stage_i = 1;
+    void* args[] = {(void*)&a, (void*)&stage_i};
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)pcg_kernel<T>, dim3(g.nblocks), dim3(kThreads), args, g.bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CP_ERR_CUDA;
+    }
+    return CP_OK;
 }
 template cp_status launch_pcg<double>(PcgArgs<double>&, int, cudaStream_t);
 #ifdef CPGN_PCG_TRACE

@@ -23,10 +23,12 @@ void launch_gamma(const Shape& s, const double* part, int chunks, double* S, dou
 void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
                      DevStats* stats, cudaStream_t st, bool resid = false);
 // Pinv[n] = (Gam[n][n] + lam I)^{-1} (FP64 Cholesky + inverse); PinvF float copy (may be null).
-// scratch: N*2*R*R doubles, used only when precond_smem_bytes(R) == 0.
+// scratch: precond_scratch_doubles(s) doubles, used only when precond_smem_bytes(R) == 0.
+// fp32: the FP32 factorisation with clamped pivots (writes PinvF only).
 void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv, float* PinvF, double* scratch,
-                    DevStats* stats, cudaStream_t st);
+                    DevStats* stats, cudaStream_t st, bool fp32 = false);
 size_t precond_smem_bytes(int R);
+size_t precond_scratch_doubles(const Shape& s);
 // Packed copy of the factors in T.
 template <typename T>
 void launch_pack(const Shape& s, Ptrs<const double> A, T* Ap, cudaStream_t st);
@@ -53,7 +55,8 @@ struct PcgArgs {
     const T* PinvT;     // N*R*R preconditioner in T
     const double* G;    // packed FP64 gradient
     T* V;               // packed update (output)
-    T* Yacc;            // [2][N][R*R]: A^(p)T W^(p) accumulated by all blocks (buffer 0 zeroed by the host)
+    T* Zpart;           // [nblocks][R*R]: each block's A^T Z over its rows
+    T* Yfull;           // [N][R*R]: Y^(p) = A^(p)T W^(p), reduced in a fixed order
     T* Tm;              // N*R*R scratch for T^(n) when it does not fit in shared memory
     double* part;       // [3][nblocks] per-block partial scalars
     GridBarrier* bar;
