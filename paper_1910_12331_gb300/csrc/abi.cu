@@ -179,13 +179,12 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
     } else if (prec == CP_PREC_RESIDUAL) {
         // MTTKRP of the residual tensor E = X - [[A]] (double-float), as bf16 planes
         CP_TRY(grow(h->stats, sizeof(DevStats)));
-        CP_TRY(grow(h->resid_planes, (size_t)2 * s.dims[0] * s.mid * tc_row_pitch(s.dims[s.N - 1]) * 2));
+        CP_TRY(grow(h->resid_planes, (size_t)PlaneTiling::of(s).total() * 2));
         DevStats* ds = (DevStats*)h->stats.p;
         CP_TRY(grow(h->Adf, (size_t)s.roff[s.N] * s.R * 2 * sizeof(float)));
-        launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, tc_row_pitch(s.dims[s.N - 1]), h->Adf.p, ds,
-                           h->stream);
+        launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, h->stream);
         CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
-        h->launches += 2 + (s.R + 63) / 64 * (2 + (s.N - 2) + 2);
+        h->launches += 2 + (s.R + 63) / 64 * 3;
     } else {
         return CP_ERR_ARG;
     }

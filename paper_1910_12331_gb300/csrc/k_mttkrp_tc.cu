@@ -1,32 +1,46 @@
-// k_mttkrp_tc.cu -- all-mode MTTKRP on tcgen05 tensor cores (sm_103a), bf16x3.
+// k_mttkrp_tc.cu -- all-mode MTTKRP on tcgen05 tensor cores (sm_103a), bf16 split products.
 //
 // Arithmetic.  Every operand value v is split into bf16 parts v = v_hi + v_lo
-// (+ O(2^-17 |v|)); a product is formed as x_hi*b_hi + x_hi*b_lo + x_lo*b_hi,
-// each term exact in the FP32 tensor-core accumulator (the split of
-// Henry, Tang and Heinecke, "Leveraging the bfloat16 artificial intelligence
-// datatype for higher-precision computations", ARITH 2019).  Accumulation is
-// FP32; the cross-block reductions and the outputs are FP64.
+// (+ O(2^-17 |v|)); products are sums of bf16 x bf16 terms, each exact in the
+// FP32 tensor-core accumulator (the split of Henry, Tang and Heinecke,
+// "Leveraging the bfloat16 artificial intelligence datatype for
+// higher-precision computations", ARITH 2019).  GEMM-Y forms
+// x_hi*b_hi + x_lo*b_hi + x_hi*b_lo (bf16x3) with two MMAs per K-step, the B
+// operand stacking [b_hi; b_lo] in its N rows for the x_hi product.  GEMM-Z
+// stacks hi and lo in both operands (A rows 2r, 2r+1 = hi, lo of column r;
+// B columns = [x_hi | x_lo]) and so forms all four products (bf16x4) in one
+// MMA per K-step.  Accumulation is FP32; the partials are reduced in FP64.
 //
-// Algorithm (Section 2.2's dimension tree, evaluated in one pass over X).  X is
-// viewed as s_1 x mid x s_N.  For every slice m of the middle modes, with
-// w_m[r] = prod_{middle q} a^(q)_{i_q(m) r}:
-//   GEMM-Y  Y_m = X(:, m, :) A^(N)                  (M = i rows, K = k)
-//   GEMM-Z  Z   = X(:, m, :)^T (A^(1) * w_m)        (M = k rows, K = i)
-// GEMM-Z folds w_m into its B operand, so its TMEM accumulator sums over all
-// slices of a work unit and directly holds a partial M^(N).  Y_m is read out
-// per slice: M^(1) += w_m * Y_m (registers) and c_m = colsum(A^(1) * Y_m)
-// feeds the middle modes.  Both GEMMs read the same shared-memory tile of X:
-// K-major for GEMM-Y and MN-major for GEMM-Z.
+// Algorithm (Section 2.2's dimension tree, one pass over X).  X is viewed as
+// s_1 x mid x s_N.  For a slice m of the middle modes,
+// w_m[r] = prod_{middle q} a^(q)_{i_q(m) r}.  A step (b, g, m) covers the 128
+// rows i of block b and the 128 columns k of group g (two 64-column chunks):
+//   GEMM-Y     D_Y[i][r]    = sum_k X[i,m,k] a^(N)_{kr}              (Y_m, partial over k)
+//   GEMM-Z^T   D_Z[c][r][k] += sum_i (a^(1)_{ir} w_m[r]) X[i,m,k]    (M^(N), per chunk c)
+// GEMM-Z folds w_m into its A operand (B_Z, rebuilt per step), so D_Z
+// accumulates in TMEM over the steps of a segment (at most kLmax steps of one
+// (b, g) run).  D_Y is read out per step: M^(1)[i] += w_m * D_Y[i]
+// (registers, per run) and c_m = sum_i a^(1)_{ir} D_Y[i][r] feeds the middle
+// modes.  Both GEMMs read the same shared-memory X chunk: GEMM-Y as a K-major
+// A operand, GEMM-Z as an MN-major B operand.
 //
-// Kernel structure: persistent, one CTA per SM, 6 warps.
-//   warp 0      TMA producer: X tiles (128 i x 128 k, both planes) and the
-//               matching B_Y tile of A^(N), 2-stage ring, mbarrier complete_tx.
-//   warp 1      TMEM allocator and single-thread tcgen05.mma issuer.
-//   warps 2..5  epilogue: build B_Z = (A^(1) * w_m) planes in shared memory,
-//               read Y_m from TMEM (double-buffered), accumulate M^(1),
-//               reduce c_m, and at the end of a unit read the M^(N) partial.
-// A work unit is (i-block of 128 rows, k-group of <= 512 columns, slice range).
-// Units write FP32 partials to workspace; a finalize kernel reduces them in a
+// Kernel: persistent, one CTA per SM, 16 warps; CTA g owns a contiguous range
+// of steps in (b, g, m) order (m fastest).
+//   warp 0      producer: the step's X chunk tiles (128 i x 64 k, both planes,
+//               32 KB each, stored pre-swizzled so that linear bulk copies land
+//               them) into one of two step slots; the w_m rows a few steps
+//               ahead; at each run start the group's B_Y = [hi; lo] a^(N)^T
+//               (2 x 16 KB by TMA, resident for the run).
+//   warp 1      TMEM allocator and GEMM-Y issuer (one thread).
+//   warp 2      GEMM-Z issuer (one thread).
+//   warps 3-6   B_Z builders: B_Z = split(a^(1)(block b) * w_m)^T, K-major,
+//               double-buffered.
+//   warps 8-15  epilogue (two warps per TMEM lane quadrant, 32 rank columns
+//               each): D_Y (double-buffered in TMEM) -> M^(1), c_m; D_Z at
+//               segment end.
+//   warp 7      idle.  Warp w runs on sub-partition w mod 4, so every
+//               sub-partition holds one builder and two epilogue warps.
+// Partials go to workspace in FP32 and a finalize kernel reduces them in a
 // fixed order into the FP64 outputs (no atomics, deterministic).
 // Every mbarrier wait is bounded: on expiry the CTA records CP_ERR_TIMEOUT,
 // raises a CTA-local abort flag, drains what it issued (bounded) and frees TMEM.
@@ -43,43 +57,79 @@ namespace cpgn {
 
 namespace tc {
 
-constexpr int kThreads = 192;           // 6 warps
-constexpr int kStages = 2;
-constexpr int kBI = 128;                // rows of an i-block (MMA M of GEMM-Y)
-constexpr int kKC = 128;                // columns of a k-chunk (MMA M of GEMM-Z)
-constexpr int kRT = 64;                 // rank columns per launch (MMA N)
-constexpr int kChunksPerGroup = 4;      // k-group = 512 columns
-constexpr uint32_t kXSub = 32 * 1024;   // one 64-column sub-tile of X, both planes
-constexpr uint32_t kXPlane = 16 * 1024; // one plane of a sub-tile (128 rows x 128 B)
-constexpr uint32_t kBYSub = 16 * 1024;  // one 64-column sub-tile of B_Y, both planes
-constexpr uint32_t kBYPlane = 8 * 1024;
-constexpr uint32_t kStageBytes = 2 * kXSub + 2 * kBYSub;  // 96 KB
-constexpr uint32_t kBZBytes = 32 * 1024;
-constexpr uint32_t kDynSmem = kStages * kStageBytes + kBZBytes + 1024;  // + alignment slack
-constexpr uint32_t kTmemCols = 512;
+constexpr int kThreads = 512;            // 16 warps
+constexpr int kEpi = 256;                // epilogue threads (two warps per TMEM lane quadrant)
+constexpr int kStages = 4;               // X chunk tiles in flight
+constexpr int kBI = 128;                 // rows of an i-block (M of GEMM-Y, K of GEMM-Z)
+constexpr int kKC = 64;                  // columns of a chunk
+constexpr int kGroup = 2;                // chunks per step
+constexpr int kRT = 64;                  // rank columns per launch
+constexpr int kLmax = 32;                // steps per segment at most (bounds the FP32 TMEM chains)
+constexpr uint32_t kTile = 32 * 1024;    // X chunk tile [plane][128 i][64 k] bf16
+constexpr uint32_t kXPlane = 16 * 1024;  // one plane of a tile
+constexpr uint32_t kOpSub = 16 * 1024;   // 128 rows x 64 bf16 of a K-major operand
+constexpr uint32_t kBYBytes = kGroup * kOpSub;  // B_Y: [chunk][128 rows: r hi, r lo][64 k]
+constexpr uint32_t kBZBytes = 2 * kOpSub;       // B_Z: [i / 64][128 rows: 2r hi, 2r+1 lo][64 i]
+constexpr uint32_t kPayload = kStages * kTile + kBYBytes + 2 * kBZBytes;  // 1024-aligned operand buffers
+constexpr int kWRing = 6;                // w_m rows in flight (shared by builders and epilogue)
+constexpr int kWAhead = 3;               // the producer loads w_m this many steps ahead of its X loads
+constexpr uint32_t kTmemCols = 512;      // D_Y x2 (128 columns each) + D_Z x2 chunks (128 each)
 constexpr long long kWaitLimit = 1LL << 26;
+#ifndef CPGN_TC_PREFETCH
+#define CPGN_TC_PREFETCH 0
+#endif
+// The producer asks L2 for the X tiles of the step this many steps ahead, so
+// that the shared-memory ring only has to cover L2 latency, not DRAM latency
+// under load.
+constexpr int kPrefetchSteps = CPGN_TC_PREFETCH;
+#ifndef CPGN_TC_L2PROMO
+#define CPGN_TC_L2PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+#endif
+constexpr CUtensorMapL2promotion kL2Promo = CPGN_TC_L2PROMO;
 
 struct Params {
     int N;
     int R;              // columns of this rank tile (<= 64)
+    const unsigned char* planes;  // bf16 planes of X in PlaneTiling layout
+    PlaneTiling pt;
     int64_t s1, mid, sN;
-    int nib, nkg, nsplit, nunits;
+    int nib, nch, ngr;  // i-blocks, 64-column chunks, groups of two chunks
+    int64_t steps;      // nib * ngr * mid
+    int smax;           // segment slots per CTA
+    int64_t middim[kMaxN];  // s_q of the middle modes (index q)
     const float* A1f;   // [s1][64] rows of A^(1) (rank tile), FP32, zero padded
-    const float* midf;  // middle factors [rows][64], FP32
-    int64_t midoff[kMaxN];
-    int64_t middim[kMaxN];
-    float* P_Y1;        // [nunits][128][64]
-    float* P_Z;         // [nunits][512][64]
-    float* P_c;         // [nib * nkg][mid][64]
+    const float* W;     // [mid][64] w_m (rank tile), FP32, zero padded
+    float* P_Y1;        // [slot][128 i][64 r]        M^(1) partial of a run (when seg[slot].y)
+    float* P_Z;         // [slot][2 chunks][64 r][64 k]  M^(N) partial of a segment
+    float* P_c;         // [nib][ngr][mid][64]        c_m partial of a step
+    int4* seg;          // [slot]: (b, g, y, 0) of the segment in a slot; b = -1 if unused
     int* status;
     long long* trace;   // event timestamps of block 0 (trace builds only), else null
 };
 
+// Barriers, flags and small arrays, placed after the operand buffers in the
+// one dynamic shared-memory region (the kernel uses no static shared memory,
+// so the region starts on the 1024-byte boundary the swizzled operands need;
+// the kernel checks this and reports CP_ERR_UNSUPPORTED otherwise).
+struct SmemCtl {
+    uint64_t full[2], empty[2];  // per step slot (two chunk stages each)
+    uint64_t bz_full[2], bz_empty[2], dy_full[2], dy_empty[2];
+    uint64_t by_full, by_empty, dz_full, dz_empty, drain[2];
+    uint64_t w_full[kWRing], w_empty[kWRing];
+    uint32_t tmem_base;
+    int abort_flag;
+    int dec[2];
+    alignas(16) float red[4][kRT];       // per-warp column sums of the epilogue
+    alignas(16) float wring[kWRing][kRT];  // w_m rows, filled by bulk copies
+};
+constexpr uint32_t kDynSmem = kPayload + (uint32_t)sizeof(SmemCtl);
+static_assert(kDynSmem <= 227 * 1024, "shared memory above the per-block limit");
+
 // Optional event trace of block 0 (compiled in with -DCPGN_TC_TRACE): slot
 // ev * 1024 + idx receives clock64() at event ev, occurrence idx.
 #ifdef CPGN_TC_TRACE
-#define TC_TRACE(ev, idx)                                                                  \
-    do {                                                                                   \
+#define TC_TRACE(ev, idx)                                                                          \
+    do {                                                                                           \
         if (p.trace && blockIdx.x == 0 && (idx) < 1024) p.trace[(ev) * 1024 + (idx)] = clock64(); \
     } while (0)
 #else
@@ -124,13 +174,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     atomicCAS(status, 0, CP_ERR_TIMEOUT);
     return false;
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(dst),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
+// Bounded wait that ignores the abort flag: used to drain copies and MMAs that
+// were issued (they complete on their own) before shared memory and TMEM go.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, int* status) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try(bar, parity)) return;
+        if (i > 256) __nanosleep(32);
+    }
+    atomicCAS(status, 0, CP_ERR_TIMEOUT);
+}
+// Linear bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Fire-and-forget L2 prefetch of a linear range (no shared memory, no completion).
+__device__ __forceinline__ void bulk_prefetch(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
     asm volatile(
@@ -153,19 +214,16 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
+// 16 consecutive FP32 columns of this thread's TMEM lane (completion via tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor, 128-byte swizzle, version 1 (sm_100 family).
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
@@ -177,22 +235,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo_bytes, uin
     d |= (uint64_t)2 << 61;
     return d;
 }
-// Instruction descriptor: D F32, A/B BF16, M = 128, N = 64, A K- or MN-major, B K-major.
-__device__ __forceinline__ uint32_t idesc_bf16(bool a_mn_major) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(kRT >> 3) << 17) |
-           ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptor: D F32, A/B BF16, M = 128, the given N; A and B K- or MN-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int n, bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-// Column of the value v[j] held by `lane` after butterfly_reduce64 (2 per lane).
-__device__ __forceinline__ int butterfly_col(int lane, int j) {
-    return ((lane >> 4) & 1) * 32 + ((lane >> 3) & 1) * 16 + ((lane >> 2) & 1) * 8 + ((lane >> 1) & 1) * 4 +
-           (lane & 1) * 2 + j;
-}
-// Reduce 64 per-lane values over the 32 lanes of a warp; lane ends with the
-// sums of columns butterfly_col(lane, 0) and butterfly_col(lane, 1) in v[0], v[1].
-__device__ __forceinline__ void butterfly_reduce64(float* v, int lane) {
+// Sum 16 per-lane values over the 32 lanes of a warp.  Afterwards lane l holds
+// in v[0] the warp total of column butterfly16_col(l) (lanes l and l^1 agree).
+__device__ __forceinline__ void butterfly16(float* v, int lane) {
 #pragma unroll
-    for (int off = 16, w = 32; off >= 1; off >>= 1, w >>= 1) {
+    for (int off = 16, w = 8; off >= 2; off >>= 1, w >>= 1) {
         const bool upper = (lane & off) != 0;
 #pragma unroll
         for (int j = 0; j < w; ++j) {
@@ -201,65 +254,108 @@ __device__ __forceinline__ void butterfly_reduce64(float* v, int lane) {
             v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ int butterfly16_col(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-__device__ __forceinline__ void named_sync_epi() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 __host__ __device__ __forceinline__ int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 
-struct Unit {
-    int b, kg;
-    int64_t m0, m1;
+// Step (b, g, m) of linear index t = (b * ngr + g) * mid + m.  Decoded once
+// per role; the loops then advance it without divisions.
+struct StepId {
+    int b, g;
+    int64_t m;
+    __device__ __forceinline__ void next(const Params& p) {
+        if (++m == p.mid) {
+            m = 0;
+            if (++g == p.ngr) {
+                g = 0;
+                ++b;
+            }
+        }
+    }
 };
-__device__ __forceinline__ Unit unit_of(const Params& p, int u) {
-    Unit r;
-    const int j = u % p.nsplit;
-    const int bk = u / p.nsplit;
-    r.b = bk / p.nkg;
-    r.kg = bk % p.nkg;
-    r.m0 = (int64_t)j * p.mid / p.nsplit;
-    r.m1 = (int64_t)(j + 1) * p.mid / p.nsplit;
+__device__ __forceinline__ StepId step_of(const Params& p, int64_t t) {
+    StepId r;
+    r.m = t % p.mid;
+    const int64_t bg = t / p.mid;
+    r.g = (int)(bg % p.ngr);
+    r.b = (int)(bg / p.ngr);
     return r;
+}
+// Segment bookkeeping shared by the MMA issuer and the epilogue: a run is a
+// maximal range of steps with fixed (b, g) inside the CTA's range; a segment
+// is at most kLmax consecutive steps of one run.
+struct SegTrack {
+    int zs = -1, zl = 0;
+    // call once per step, in order; returns (run_start, seg_start)
+    __device__ __forceinline__ void enter(int64_t t, int64_t T0, int64_t m, bool& run_start, bool& seg_start) {
+        run_start = t == T0 || m == 0;
+        seg_start = run_start || zl == kLmax;
+        if (seg_start) {
+            ++zs;
+            zl = 0;
+        }
+        ++zl;
+    }
+};
+__device__ __forceinline__ bool run_last(const Params& p, int64_t t, int64_t T1, int64_t m) {
+    return t + 1 == T1 || m + 1 == p.mid;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBY, Params p) {
+    mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tmBY, Params p) {
     extern __shared__ __align__(1024) unsigned char dsmem[];
-    __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
-    __shared__ __align__(8) uint64_t bar_bz_full, bar_bz_empty, bar_dy_full[2], bar_dy_empty[2], bar_dz_full,
-        bar_dz_empty, bar_drain;
-    __shared__ int dec_s;
-    __shared__ uint32_t tmem_base_s;
-    __shared__ volatile int abort_s;
-    __shared__ float w_s[2][kRT];
-    __shared__ float red_s[4][kRT];
-
-    unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
+    if (smem_u32(dsmem) & 1023u) {  // block-uniform: nothing has been issued yet
+        if (threadIdx.x == 0) atomicCAS(p.status, 0, CP_ERR_UNSUPPORTED);
+        return;
+    }
+    unsigned char* base = dsmem;
+    SmemCtl& C = *reinterpret_cast<SmemCtl*>(base + kPayload);
+    volatile int* abort_s = &C.abort_flag;
     const uint32_t sbase = smem_u32(base);
     const uint32_t s_stage0 = sbase;
-    const uint32_t s_bz = sbase + kStages * kStageBytes;
-    unsigned char* bz_gen = base + kStages * kStageBytes;
+    const uint32_t s_by = sbase + kStages * kTile;
+    const uint32_t s_bz0 = s_by + kBYBytes;
+    unsigned char* bz_gen0 = base + kStages * kTile + kBYBytes;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Rows of the last i-block beyond its tile's rows are never copied in; they
+    // must hold finite values (they meet zero rows of B_Z and unused rows of D_Y).
+    for (int e = threadIdx.x; e < (int)(kStages * kTile / 16); e += kThreads)
+        reinterpret_cast<uint4*>(base)[e] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), 1);
-        }
-        mbar_init(smem_u32(&bar_bz_full), 128);
-        mbar_init(smem_u32(&bar_bz_empty), 1);
         for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&bar_dy_full[s]), 1);
-            mbar_init(smem_u32(&bar_dy_empty[s]), 128);
+            mbar_init(smem_u32(&C.full[s]), 1);
+            mbar_init(smem_u32(&C.empty[s]), 2);  // released by both MMA issuers
+            mbar_init(smem_u32(&C.drain[s]), 1);
         }
-        mbar_init(smem_u32(&bar_dz_full), 1);
-        mbar_init(smem_u32(&bar_dz_empty), 128);
-        mbar_init(smem_u32(&bar_drain), 1);
-        abort_s = 0;
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&C.bz_full[s]), 128);
+            mbar_init(smem_u32(&C.bz_empty[s]), 1);
+            mbar_init(smem_u32(&C.dy_full[s]), 1);
+            mbar_init(smem_u32(&C.dy_empty[s]), kEpi);
+        }
+        for (int s = 0; s < kWRing; ++s) {
+            mbar_init(smem_u32(&C.w_full[s]), 1);
+            mbar_init(smem_u32(&C.w_empty[s]), 128 + kEpi);  // every builder and epilogue thread
+        }
+        mbar_init(smem_u32(&C.by_full), 1);
+        mbar_init(smem_u32(&C.by_empty), 1);
+        mbar_init(smem_u32(&C.dz_full), 1);
+        mbar_init(smem_u32(&C.dz_empty), kEpi);
+        *abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&C.tmem_base)),
                      "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -267,239 +363,357 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base_s;
-    const uint32_t t_dy0 = tmem, t_dz = tmem + 2 * kRT;
-    const int G = gridDim.x;
+    const uint32_t tmem = C.tmem_base;
+    const uint32_t t_dy0 = tmem, t_dz0 = tmem + 256;
+    const int64_t T0 = (int64_t)blockIdx.x * p.steps / gridDim.x;
+    const int64_t T1 = (int64_t)(blockIdx.x + 1) * p.steps / gridDim.x;
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            int it = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < p.nunits && ok; u += G) {
-                const Unit U = unit_of(p, u);
-                const int c0 = U.kg * kChunksPerGroup;
-                const int c1 = (int)imin(c0 + kChunksPerGroup, (p.sN + kKC - 1) / kKC);
-                for (int64_t m = U.m0; m < U.m1 && ok; ++m)
-                    for (int c = c0; c < c1; ++c, ++it) {
-                        const int s = it % kStages;
-                        const uint32_t ph = (it / kStages) & 1;
-                        if (!(ok = mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1, &abort_s, p.status))) break;
-                        TC_TRACE(0, it);
-                        const uint32_t fb = smem_u32(&bar_full[s]);
-                        mbar_expect_tx(fb, kStageBytes);
-                        const uint32_t st = s_stage0 + s * kStageBytes;
-                        tma_load_4d(st, &tmX, c * kKC, (int)m, U.b * kBI, 0, fb);
-                        tma_load_4d(st + kXSub, &tmX, c * kKC + 64, (int)m, U.b * kBI, 0, fb);
-                        tma_load_2d(st + 2 * kXSub, &tmBY, c * kKC, 0, fb);
-                        tma_load_2d(st + 2 * kXSub + kBYSub, &tmBY, c * kKC + 64, 0, fb);
-                    }
+            int yg = -1;
+            int64_t it = 0;
+            StepId pf = step_of(p, T0);  // the step kPrefetchSteps ahead
+            auto prefetch = [&]() {
+                const int nq = (int)imin(kGroup, p.nch - pf.g * kGroup);
+                const uint32_t bytes = 2u * p.pt.rows(pf.b) * 128u;
+                for (int cc = 0; cc < nq; ++cc)
+                    bulk_prefetch(p.planes + 2 * p.pt.tile(pf.b, pf.g * kGroup + cc, pf.m), bytes);
+                pf.next(p);
+            };
+            for (int64_t t = T0; t < T0 + kPrefetchSteps && t < T1; ++t) prefetch();
+            StepId sp = step_of(p, T0), wsp = sp;  // wsp: the next step whose w_m row is loaded
+            int64_t wl = 0;                         // w_m rows loaded so far
+            for (int64_t t = T0; t < T1 && ok; ++t, sp.next(p)) {
+                if (t + kPrefetchSteps < T1) prefetch();
+                for (; ok && wl <= (t - T0) + kWAhead && T0 + wl < T1; ++wl, wsp.next(p)) {
+                    const int ws = (int)(wl % kWRing);
+                    if (!(ok = mbar_wait(smem_u32(&C.w_empty[ws]), (uint32_t)(((wl / kWRing) & 1) ^ 1), abort_s,
+                                         p.status)))
+                        break;
+                    const uint32_t wb = smem_u32(&C.w_full[ws]);
+                    mbar_expect_tx(wb, kRT * sizeof(float));
+                    bulk_load(smem_u32(&C.wring[ws][0]), p.W + wsp.m * kRT, kRT * sizeof(float), wb);
+                }
+                if (!ok) break;
+                if (t == T0 || sp.m == 0) {  // run start: the group's B_Y (both chunks; missing ones read as zero)
+                    ++yg;
+                    if (!(ok = mbar_wait(smem_u32(&C.by_empty), (uint32_t)((yg & 1) ^ 1), abort_s, p.status)))
+                        break;
+                    const uint32_t fb = smem_u32(&C.by_full);
+                    mbar_expect_tx(fb, kBYBytes);
+                    for (int cc = 0; cc < kGroup; ++cc)
+                        tma_load_2d(s_by + cc * kOpSub, &tmBY, (sp.g * kGroup + cc) * kKC, 0, fb);
+                }
+                // the step's chunks go to the two stages of step slot tt & 1
+                const int nc = (int)imin(kGroup, p.nch - sp.g * kGroup);
+                const uint32_t pbytes = (uint32_t)p.pt.rows(sp.b) * 128u;  // one plane of a tile
+                const int slot = (int)(it & 1);
+                if (!(ok = mbar_wait(smem_u32(&C.empty[slot]), (uint32_t)(((it >> 1) & 1) ^ 1), abort_s, p.status)))
+                    break;
+                TC_TRACE(0, (int)it);
+                const uint32_t fb = smem_u32(&C.full[slot]);
+                mbar_expect_tx(fb, 2 * nc * pbytes);
+                for (int cc = 0; cc < nc; ++cc) {
+                    const unsigned char* src = p.planes + 2 * p.pt.tile(sp.b, sp.g * kGroup + cc, sp.m);
+                    const uint32_t dst = s_stage0 + (2 * slot + cc) * kTile;
+                    bulk_load(dst, src, pbytes, fb);
+                    bulk_load(dst + kXPlane, src + pbytes, pbytes, fb);
+                }
+                ++it;
             }
-            // drain: every issued stage must have landed before the CTA may exit
-            for (int k = (it > kStages ? it - kStages : 0); k < it; ++k)
-                mbar_wait(smem_u32(&bar_full[k % kStages]), (k / kStages) & 1, &abort_s, p.status);
+            // every issued copy must have landed before the CTA may exit
+            for (int64_t k = (it > 2 ? it - 2 : 0); k < it; ++k)
+                mbar_drain(smem_u32(&C.full[k & 1]), (uint32_t)((k >> 1) & 1), p.status);
+            for (int64_t k = (wl > kWRing ? wl - kWRing : 0); k < wl; ++k)
+                mbar_drain(smem_u32(&C.w_full[k % kWRing]), (uint32_t)((k / kWRing) & 1), p.status);
+            if (yg >= 0) mbar_drain(smem_u32(&C.by_full), (uint32_t)(yg & 1), p.status);
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------------------------------------------------------- MMA
+        // ------------------------------------------------------ GEMM-Y issuer
+        // (also the TMEM allocator).  D_Y[i][0:64] += X_hi B_hi + X_lo B_hi,
+        // D_Y[i][64:128] += X_hi B_lo over both chunks of a step.  Descriptors
+        // are a base descriptor plus the K-step's byte offset / 16 (the 14-bit
+        // address field cannot carry: shared memory is below 256 KB).
         if (lane == 0) {
-            const uint32_t id_y = idesc_bf16(false), id_z = idesc_bf16(true);
-            int it = 0;
-            int64_t t = 0;  // slice counter
-            int v = 0;      // unit counter
+            const uint32_t id_y128 = idesc_bf16(128, false, false), id_y64 = idesc_bf16(64, false, false);
             bool ok = true;
-            for (int u = blockIdx.x; u < p.nunits && ok; u += G, ++v) {
-                const Unit U = unit_of(p, u);
-                const int c0 = U.kg * kChunksPerGroup;
-                const int c1 = (int)imin(c0 + kChunksPerGroup, (p.sN + kKC - 1) / kKC);
-                const int ivalid = (int)imin(kBI, p.s1 - (int64_t)U.b * kBI);
-                const int zsteps = (ivalid + 15) / 16;
-                bool zfirst[kChunksPerGroup] = {true, true, true, true};
-                // the epilogue must have read the previous unit's M^(N) partial
-                if (!(ok = mbar_wait(smem_u32(&bar_dz_empty), (v & 1) ^ 1, &abort_s, p.status))) break;
-                for (int64_t m = U.m0; m < U.m1 && ok; ++m, ++t) {
-                    const int buf = (int)(t & 1);
-                    const uint32_t dph = (uint32_t)((t >> 1) & 1);
-                    if (!(ok = mbar_wait(smem_u32(&bar_dy_empty[buf]), dph ^ 1, &abort_s, p.status))) break;
-                    tc_fence_after();
-                    const uint32_t t_dy = t_dy0 + buf * kRT;
-                    bool yfirst = true;
-                    for (int c = c0; c < c1; ++c, ++it) {
-                        const int s = it % kStages;
-                        if (!(ok = mbar_wait(smem_u32(&bar_full[s]), (it / kStages) & 1, &abort_s, p.status))) break;
-                        TC_TRACE(1, it);
-                        tc_fence_after();
-                        const uint32_t st = s_stage0 + s * kStageBytes;
-                        // GEMM-Y: D_Y(128 i x 64 r) += X(i, k) * B_Y(k, r), k in this chunk
-                        const int kvalid = (int)imin(kKC, p.sN - (int64_t)c * kKC);
-                        const int ysteps = (kvalid + 15) / 16;
-                        for (int ks = 0; ks < ysteps; ++ks) {
-                            const int sub = ks >> 2, kk = ks & 3;
-                            const uint32_t xa = st + sub * kXSub + kk * 32;
-                            const uint32_t ba = st + 2 * kXSub + sub * kBYSub + kk * 32;
-                            const uint64_t xh = sdesc(xa, 16, 1024), xl = sdesc(xa + kXPlane, 16, 1024);
-                            const uint64_t bh = sdesc(ba, 16, 1024), bl = sdesc(ba + kBYPlane, 16, 1024);
-                            tc_mma(t_dy, xh, bh, id_y, yfirst ? 0 : 1);
-                            tc_mma(t_dy, xh, bl, id_y, 1);
-                            tc_mma(t_dy, xl, bh, id_y, 1);
-                            yfirst = false;
-                        }
-                        // GEMM-Z needs this slice's B_Z = A^(1) * w_m
-                        if (c == c0) {
-                            if (!(ok = mbar_wait(smem_u32(&bar_bz_full), (uint32_t)(t & 1), &abort_s, p.status))) break;
-                            TC_TRACE(2, (int)t);
-                            tc_fence_after();
-                        }
-                        // GEMM-Z: D_Z[c](128 k x 64 r) += X(i, k)^T * B_Z(i, r), i in this block
-                        const uint32_t t_z = t_dz + (c - c0) * kRT;
-                        for (int ks = 0; ks < zsteps; ++ks) {
-                            const uint32_t xa = st + ks * 2048;
-                            const uint32_t ba = s_bz + (ks >> 2) * 16384 + (ks & 3) * 32;
-                            const uint64_t xh = sdesc(xa, kXSub, 1024), xl = sdesc(xa + kXPlane, kXSub, 1024);
-                            const uint64_t bh = sdesc(ba, 16, 1024), bl = sdesc(ba + 8192, 16, 1024);
-                            tc_mma(t_z, xh, bh, id_z, zfirst[c - c0] ? 0 : 1);
-                            tc_mma(t_z, xh, bl, id_z, 1);
-                            tc_mma(t_z, xl, bh, id_z, 1);
-                            zfirst[c - c0] = false;
-                        }
-                        tc_commit(smem_u32(&bar_empty[s]));
-                        TC_TRACE(3, it);
-                    }
-                    if (!ok) break;
-                    tc_commit(smem_u32(&bar_dy_full[buf]));
-                    tc_commit(smem_u32(&bar_bz_empty));
+            int yg = -1;
+            StepId sp = step_of(p, T0);
+            for (int64_t t = T0, tt = 0; t < T1 && ok; ++t, ++tt, sp.next(p)) {
+                if (t == T0 || sp.m == 0) {
+                    ++yg;
+                    if (!(ok = mbar_wait(smem_u32(&C.by_full), (uint32_t)(yg & 1), abort_s, p.status))) break;
                 }
-                if (ok) tc_commit(smem_u32(&bar_dz_full));
+                const int slot = (int)(tt & 1), db = slot;
+                const uint32_t ph = (uint32_t)((tt >> 1) & 1);
+                // K-steps of 16 columns in each chunk of the step (0 for a missing second chunk)
+                const int64_t k0 = (int64_t)sp.g * kGroup * kKC;
+                const int ys0 = (int)((imin(kKC, p.sN - k0) + 15) / 16);
+                const int ys1 = p.sN > k0 + kKC ? (int)((imin(kKC, p.sN - k0 - kKC) + 15) / 16) : 0;
+                if (!(ok = mbar_wait(smem_u32(&C.dy_empty[db]), ph ^ 1, abort_s, p.status))) break;
+                if (!(ok = mbar_wait(smem_u32(&C.full[slot]), ph, abort_s, p.status))) break;
+                TC_TRACE(1, (int)tt);
+                tc_fence_after();
+                const uint32_t t_dy = t_dy0 + db * 128;
+                const uint64_t dx0 = sdesc(s_stage0 + (2 * slot) * kTile, 16, 1024), dby0 = sdesc(s_by, 16, 1024);
+#pragma unroll
+                for (int cc = 0; cc < kGroup; ++cc) {
+                    const int ysteps = cc == 0 ? ys0 : ys1;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        if (ks < ysteps) {
+                            const uint64_t xo = (uint64_t)((cc * kTile + ks * 32) >> 4);
+                            const uint64_t bo = (uint64_t)((cc * kOpSub + ks * 32) >> 4);
+                            tc_mma(t_dy, dx0 + xo, dby0 + bo, id_y128, (cc | ks) != 0);
+                            tc_mma(t_dy, dx0 + xo + (kXPlane >> 4), dby0 + bo, id_y64, 1);
+                        }
+                    }
+                }
+                tc_commit(smem_u32(&C.dy_full[db]));
+                tc_commit(smem_u32(&C.empty[slot]));
+                if (run_last(p, t, T1, sp.m)) tc_commit(smem_u32(&C.by_empty));
+                TC_TRACE(2, (int)tt);
             }
-            // drain: every issued MMA must have completed before TMEM is freed
-            tc_commit(smem_u32(&bar_drain));
-            mbar_wait(smem_u32(&bar_drain), 0, &abort_s, p.status);
+            // every issued MMA must have completed before TMEM is freed
+            tc_commit(smem_u32(&C.drain[0]));
+            mbar_drain(smem_u32(&C.drain[0]), 0, p.status);
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------------------ epilogue
-        const int q = warp & 3;           // TMEM lane quadrant of this warp
-        const int row = q * 32 + lane;    // row within the i-block / k-chunk
-        const int et = threadIdx.x - 64;  // 0..127
-        // bounded wait with a decision shared by all 128 epilogue threads, so that
-        // they leave together and no named barrier is left waiting
-        auto epi_wait = [&](uint32_t bar, uint32_t parity) -> bool {
-            mbar_wait(bar, parity, &abort_s, p.status);
-            named_sync_epi();
-            if (et == 0) dec_s = abort_s;
-            named_sync_epi();
-            return dec_s == 0;
+    } else if (warp == 2) {
+        // ------------------------------------------------------ GEMM-Z issuer
+        // D_Z[rho][n] += sum_i B_Z[rho][i] [X_hi c0 | X_lo c0 | X_hi c1 | X_lo c1][i][n]:
+        // one N = 256 MMA per K-step covers both chunks (the two stages of a
+        // step slot are adjacent, so the four 64-column atoms are 16 KB apart).
+        if (lane == 0) {
+            const uint32_t id_z = idesc_bf16(256, false, true);
+            bool ok = true;
+            SegTrack seg;
+            bool zfirst = true;
+            StepId sp = step_of(p, T0);
+            for (int64_t t = T0, tt = 0; t < T1 && ok; ++t, ++tt, sp.next(p)) {
+                bool run_start, seg_start;
+                seg.enter(t, T0, sp.m, run_start, seg_start);
+                if (seg_start) {
+                    // the epilogue must have read the previous segment's D_Z
+                    if (!(ok = mbar_wait(smem_u32(&C.dz_empty), (uint32_t)((seg.zs & 1) ^ 1), abort_s, p.status)))
+                        break;
+                    zfirst = true;
+                }
+                const int slot = (int)(tt & 1), db = slot;
+                const uint32_t ph = (uint32_t)((tt >> 1) & 1);
+                const int zsteps = (int)((imin(kBI, p.s1 - (int64_t)sp.b * kBI) + 15) / 16);
+                if (!(ok = mbar_wait(smem_u32(&C.full[slot]), ph, abort_s, p.status))) break;
+                if (!(ok = mbar_wait(smem_u32(&C.bz_full[db]), ph, abort_s, p.status))) break;
+                tc_fence_after();
+                const uint64_t dbz = sdesc(s_bz0 + db * kBZBytes, 16, 1024);
+                const uint64_t dxz = sdesc(s_stage0 + (2 * slot) * kTile, kXPlane, 1024);
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks) {
+                    if (ks < zsteps) {
+                        const uint64_t ao = (uint64_t)((((ks >> 2) * kOpSub) + (ks & 3) * 32) >> 4);
+                        const uint64_t bo = (uint64_t)((ks * 2048) >> 4);
+                        tc_mma(t_dz0, dbz + ao, dxz + bo, id_z, (ks == 0 && zfirst) ? 0 : 1);
+                    }
+                }
+                zfirst = false;
+                tc_commit(smem_u32(&C.bz_empty[db]));
+                tc_commit(smem_u32(&C.empty[slot]));
+                if (run_last(p, t, T1, sp.m) || seg.zl == kLmax) tc_commit(smem_u32(&C.dz_full));
+            }
+            tc_commit(smem_u32(&C.drain[1]));
+            mbar_drain(smem_u32(&C.drain[1]), 0, p.status);
+        }
+        __syncwarp();
+    } else if (warp >= 3 && warp <= 6) {
+        // ------------------------------------------------------- B_Z builders
+        // (warps 3-6: one per sub-partition)
+        // thread: rows i0, i0 + 1 of the i-block, rank columns rh .. rh + 31.
+        // B_Z row 2r holds the hi part of column r, row 2r + 1 the lo part.
+        const int et = (warp - 3) * 32 + lane;  // 0..127
+        const int i0 = 2 * (et & 63), rh = 32 * (et >> 6);
+        auto grp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
+            mbar_wait(bar, parity, abort_s, p.status);
+            named_sync(1, 128);
+            if (et == 0) C.dec[0] = *abort_s;
+            named_sync(1, 128);
+            return C.dec[0] == 0;
         };
-        float a1r[kRT];
-        float m1acc[kRT];
-        int64_t t = 0;
-        int v = 0;
-        bool ok = true;
-        for (int u = blockIdx.x; u < p.nunits && ok; u += G, ++v) {
-            const Unit U = unit_of(p, u);
-            const int64_t gi = (int64_t)U.b * kBI + row;
-            const bool rowok = gi < p.s1;
+        // byte address of element (row, i0) in buffer 0 is sub + (row & 7 term) + row * 128
+        unsigned char* rowbase[8];
+        {
+            const int ii = i0 & 63;
+            unsigned char* sub = bz_gen0 + (i0 >> 6) * kOpSub + 2 * rh * 128;
 #pragma unroll
-            for (int r = 0; r < kRT; ++r) {
-                a1r[r] = rowok ? p.A1f[gi * kRT + r] : 0.0f;
-                m1acc[r] = 0.0f;
-            }
-            float* Pc = p.P_c + (int64_t)(U.b * p.nkg + U.kg) * p.mid * kRT;
-            const int64_t nsl = U.m1 - U.m0;
-            const int64_t t0 = t;
-            for (int64_t j = 0; j <= nsl && ok; ++j) {
-                if (j < nsl) {
-                    // ---- w_m and B_Z(m) = A^(1)(block) * w_m, bf16 hi/lo, K-major swizzled
-                    const int64_t tt = t0 + j, m = U.m0 + j;
-                    const int wb = (int)(tt & 1);
-                    if (!(ok = epi_wait(smem_u32(&bar_bz_empty), (uint32_t)((tt & 1) ^ 1)))) break;
-                    if (et == 0) TC_TRACE(4, (int)tt);
-                    if (et < kRT) {
-                        float w = 1.0f;
-                        int64_t rem = m;
-                        for (int qq = p.N - 2; qq >= 1; --qq) {
-                            const int64_t iq = rem % p.middim[qq];
-                            rem /= p.middim[qq];
-                            w *= p.midf[(p.midoff[qq] + iq) * kRT + et];
-                        }
-                        w_s[wb][et] = w;
-                    }
-                    named_sync_epi();
-                    {
-                        const int i = row;  // K index of B_Z
-                        unsigned char* sub = bz_gen + (i >> 6) * 16384;
-                        const int ii = i & 63;
-#pragma unroll 8
-                        for (int r = 0; r < kRT; ++r) {
-                            const float pv = a1r[r] * w_s[wb][r];
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(pv);
-                            const __nv_bfloat16 lo = __float2bfloat16_rn(pv - __bfloat162float(hi));
-                            const uint32_t off = r * 128 + ((((ii >> 3) ^ (r & 7)) & 7) << 4) + (ii & 7) * 2;
-                            *reinterpret_cast<__nv_bfloat16*>(sub + off) = hi;
-                            *reinterpret_cast<__nv_bfloat16*>(sub + 8192 + off) = lo;
-                        }
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_arrive(smem_u32(&bar_bz_full));
-                    if (et == 0) TC_TRACE(5, (int)tt);
-                }
-                if (j > 0) {
-                    // ---- epilogue of the previous slice: Y_m
-                    const int64_t tp = t0 + j - 1, m = U.m0 + j - 1;
-                    const int buf = (int)(tp & 1);
-                    if (!(ok = epi_wait(smem_u32(&bar_dy_full[buf]), (uint32_t)((tp >> 1) & 1)))) break;
-                    if (et == 0) TC_TRACE(6, (int)tp);
-                    tc_fence_after();
-                    float y[kRT];
-                    const uint32_t ta = t_dy0 + buf * kRT + ((uint32_t)(q * 32) << 16);
+            for (int x = 0; x < 8; ++x) rowbase[x] = sub + ((((ii >> 3) ^ x) & 7) << 4) + (ii & 7) * 2;
+        }
+        float a0[32], a1[32];
+        StepId sp = step_of(p, T0);
+        int pb = -1;
+        int64_t tt = 0;
+        for (int64_t t = T0; t < T1; ++t, ++tt, sp.next(p)) {
+            if (sp.b != pb) {
+                pb = sp.b;
+                const int64_t g0 = (int64_t)sp.b * kBI + i0;
 #pragma unroll
-                    for (int jj = 0; jj < kRT; jj += 16) tmem_ld16(ta + jj, y + jj);
-                    tc_fence_before();
-                    mbar_arrive(smem_u32(&bar_dy_empty[buf]));
-#pragma unroll
-                    for (int r = 0; r < kRT; ++r) {
-                        m1acc[r] = fmaf(w_s[buf][r], y[r], m1acc[r]);
-                        y[r] *= a1r[r];
-                    }
-                    if (p.N >= 3) {
-                        butterfly_reduce64(y, lane);
-                        red_s[q][butterfly_col(lane, 0)] = y[0];
-                        red_s[q][butterfly_col(lane, 1)] = y[1];
-                        named_sync_epi();
-                        if (et < kRT) {
-                            const float cm = red_s[0][et] + red_s[1][et] + red_s[2][et] + red_s[3][et];
-                            Pc[m * kRT + et] = cm;
-                        }
-                        named_sync_epi();
-                    }
-                    if (et == 0) TC_TRACE(7, (int)tp);
+                for (int r = 0; r < 32; ++r) {
+                    a0[r] = g0 < p.s1 ? p.A1f[g0 * kRT + rh + r] : 0.0f;
+                    a1[r] = g0 + 1 < p.s1 ? p.A1f[(g0 + 1) * kRT + rh + r] : 0.0f;
                 }
             }
-            t = t0 + nsl;
-            if (!ok) break;
-            // ---- unit end: M^(1) partial from registers, M^(N) partial from TMEM
-            float* py = p.P_Y1 + ((int64_t)u * kBI + row) * kRT;
+            const int db = (int)(tt & 1);
+            const int ws = (int)(tt % kWRing);
+            if (!grp_wait(smem_u32(&C.bz_empty[db]), (uint32_t)(((tt >> 1) & 1) ^ 1))) break;
+            if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tt / kWRing) & 1))) break;
+            if (et == 0) TC_TRACE(3, (int)tt);
+            const uint32_t boff = db * kBZBytes;
+            const float4* wv = reinterpret_cast<const float4*>(&C.wring[ws][rh]);
 #pragma unroll
-            for (int r = 0; r < kRT; r += 4)
-                *reinterpret_cast<float4*>(py + r) = make_float4(m1acc[r], m1acc[r + 1], m1acc[r + 2], m1acc[r + 3]);
-            if (!(ok = epi_wait(smem_u32(&bar_dz_full), (uint32_t)(v & 1)))) break;
+            for (int r4 = 0; r4 < 32; r4 += 4) {
+                const float4 w4 = wv[r4 >> 2];
+                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = r4 + u;
+                    const float p0 = a0[r] * w[u], p1 = a1[r] * w[u];
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
+                    const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - __low2float(hi), p1 - __high2float(hi));
+                    *reinterpret_cast<__nv_bfloat162*>(rowbase[(2 * r) & 7] + boff + (2 * r) * 128) = hi;
+                    *reinterpret_cast<__nv_bfloat162*>(rowbase[(2 * r + 1) & 7] + boff + (2 * r + 1) * 128) = lo;
+                }
+            }
+            mbar_arrive(smem_u32(&C.w_empty[ws]));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&C.bz_full[db]));
+            if (et == 0) TC_TRACE(7, (int)tt);
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------------------------ epilogue
+        // Two warps per TMEM lane quadrant; warp half h takes rank columns
+        // 32h .. 32h + 31 of its 32 rows (and the same k columns of D_Z).
+        const int q = warp & 3;                // TMEM lane quadrant of this warp
+        const int cb = 32 * ((warp - 8) >> 2);  // first column of this warp
+        const int row = q * 32 + lane;         // lane of D_Y (row i) and of D_Z (row rho)
+        const int et = threadIdx.x - 256;      // 0..255
+        auto grp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
+            mbar_wait(bar, parity, abort_s, p.status);
+            named_sync(2, kEpi);
+            if (et == 0) C.dec[1] = *abort_s;
+            named_sync(2, kEpi);
+            return C.dec[1] == 0;
+        };
+        float a1r[32], m1acc[32];
+        StepId sp = step_of(p, T0);
+        SegTrack seg;
+        int done = 0, pb = -1;
+        int64_t tt = 0;
+        for (int64_t t = T0; t < T1; ++t, ++tt, sp.next(p)) {
+            bool run_start, seg_start;
+            seg.enter(t, T0, sp.m, run_start, seg_start);
+            if (run_start) {
+                if (sp.b != pb) {
+                    pb = sp.b;
+                    const int64_t gi = (int64_t)sp.b * kBI + row;
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) a1r[r] = gi < p.s1 ? p.A1f[gi * kRT + cb + r] : 0.0f;
+                }
+#pragma unroll
+                for (int r = 0; r < 32; ++r) m1acc[r] = 0.0f;
+            }
+            const int db = (int)(tt & 1);
+            const int ws = (int)(tt % kWRing);
+            if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tt / kWRing) & 1))) break;
+            if (!grp_wait(smem_u32(&C.dy_full[db]), (uint32_t)((tt >> 1) & 1))) break;
+            if (et == 0) TC_TRACE(4, (int)tt);
             tc_fence_after();
-            const int c0 = U.kg * kChunksPerGroup;
-            const int c1 = (int)imin(c0 + kChunksPerGroup, (p.sN + kKC - 1) / kKC);
-            for (int c = c0; c < c1; ++c) {
-                float z[kRT];
-                const uint32_t ta = t_dz + (c - c0) * kRT + ((uint32_t)(q * 32) << 16);
+            const uint32_t ta = t_dy0 + db * 128 + cb + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-                for (int j = 0; j < kRT; j += 16) tmem_ld16(ta + j, z + j);
-                float* pz = p.P_Z + ((int64_t)u * (kChunksPerGroup * kKC) + (c - c0) * kKC + row) * kRT;
+            for (int j = 0; j < 32; j += 16) {
+                uint32_t ra[16], rb[16];
+                tmem_ld16(ta + j, ra);
+                tmem_ld16(ta + 64 + j, rb);
+                tmem_wait_ld();
+                float v[16];
 #pragma unroll
-                for (int r = 0; r < kRT; r += 4)
-                    *reinterpret_cast<float4*>(pz + r) = make_float4(z[r], z[r + 1], z[r + 2], z[r + 3]);
+                for (int u = 0; u < 16; u += 4) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(&C.wring[ws][cb + j + u]);
+                    const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const float y = __uint_as_float(ra[u + x]) + __uint_as_float(rb[u + x]);
+                        m1acc[j + u + x] = fmaf(w[x], y, m1acc[j + u + x]);
+                        v[u + x] = y * a1r[j + u + x];
+                    }
+                }
+                if (p.N >= 3) {
+                    butterfly16(v, lane);
+                    if ((lane & 1) == 0) C.red[q][cb + j + butterfly16_col(lane)] = v[0];
+                }
             }
             tc_fence_before();
-            mbar_arrive(smem_u32(&bar_dz_empty));
+            mbar_arrive(smem_u32(&C.dy_empty[db]));
+            mbar_arrive(smem_u32(&C.w_empty[ws]));
+            if (p.N >= 3) {
+                named_sync(2, kEpi);
+                if (et < kRT)
+                    p.P_c[(((int64_t)sp.b * p.ngr + sp.g) * p.mid + sp.m) * kRT + et] =
+                        C.red[0][et] + C.red[1][et] + C.red[2][et] + C.red[3][et];
+                named_sync(2, kEpi);
+            }
+            if (et == 0) TC_TRACE(5, (int)tt);
+            const bool rl = run_last(p, t, T1, sp.m);
+            if (rl || seg.zl == kLmax) {
+                const bool slot_ok = seg.zs < p.smax;
+                const int64_t slot = (int64_t)blockIdx.x * p.smax + seg.zs;
+                if (rl && slot_ok) {
+                    float* py = p.P_Y1 + (slot * kBI + row) * kRT + cb;
+#pragma unroll
+                    for (int r = 0; r < 32; r += 4)
+                        *reinterpret_cast<float4*>(py + r) =
+                            make_float4(m1acc[r], m1acc[r + 1], m1acc[r + 2], m1acc[r + 3]);
+                }
+                if (!grp_wait(smem_u32(&C.dz_full), (uint32_t)(seg.zs & 1))) break;
+                tc_fence_after();
+                // D_Z[cc][rho][n]: rho = 2r + (lo part); n < 64: x_hi column k = n, else x_lo column n - 64
+                const int nc = (int)imin(kGroup, p.nch - sp.g * kGroup);
+                for (int cc = 0; cc < nc; ++cc) {
+                    float* pz = p.P_Z + ((slot * kGroup + cc) * kRT + (row >> 1)) * kKC + cb;
+                    const uint32_t tz = t_dz0 + cc * 128 + cb + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+                    for (int j = 0; j < 32; j += 16) {
+                        uint32_t za[16], zb[16];
+                        tmem_ld16(tz + j, za);
+                        tmem_ld16(tz + 64 + j, zb);
+                        tmem_wait_ld();
+                        float z[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            z[u] = __uint_as_float(za[u]) + __uint_as_float(zb[u]);
+                            z[u] += __shfl_xor_sync(0xffffffffu, z[u], 1);  // hi + lo rows of column r
+                        }
+                        if (slot_ok && (lane & 1) == 0) {
+#pragma unroll
+                            for (int u = 0; u < 16; u += 4)
+                                *reinterpret_cast<float4*>(pz + j + u) = make_float4(z[u], z[u + 1], z[u + 2], z[u + 3]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&C.dz_empty));
+                if (et == 0) {
+                    if (slot_ok)
+                        p.seg[slot] = make_int4(sp.b, sp.g, rl ? 1 : 0, 0);
+                    else
+                        atomicCAS(p.status, 0, CP_ERR_UNSUPPORTED);  // segment count above the host's bound
+                }
+                done = seg.zs + 1;
+            }
         }
-        (void)et;
+        // slots without a (complete) segment are marked unused
+        if (et == 0)
+            for (int k = done; k < p.smax; ++k) p.seg[(int64_t)blockIdx.x * p.smax + k] = make_int4(-1, -1, 0, 0);
     }
     // ---- teardown: every role has left its loop (all waits are bounded)
     tc_fence_before();
@@ -511,9 +725,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------ preparation
-// X -> bf16 planes [2][s1][mid][sNp] (hi, lo), zero in the padding columns.
-// Four consecutive columns per thread, 8-byte stores; FP32 arithmetic for FP32
-// input (x - hi is exact), FP64 only for FP64 input.
+// X -> bf16 planes in PlaneTiling layout (hi, lo; zero outside the tensor).
+// A block handles rows (i, m) of the padded range, a thread four consecutive
+// columns (8-byte stores, which stay contiguous under the 16-byte swizzle).
+// FP32 arithmetic for FP32 input (x - hi is exact), FP64 only for FP64 input.
 template <typename TX>
 __device__ __forceinline__ void split1(TX x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
     if constexpr (sizeof(TX) == 4) {
@@ -526,116 +741,210 @@ __device__ __forceinline__ void split1(TX x, __nv_bfloat16& hi, __nv_bfloat16& l
 }
 
 template <typename TX>
-__global__ void split_x_kernel(const TX* __restrict__ X, __nv_bfloat16* __restrict__ planes, int64_t rows, int64_t sN,
-                               int64_t sNp) {
-    const int64_t q4 = sNp / 4;  // sNp is a multiple of 8
-    const int64_t total4 = rows * q4, total = rows * sNp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total4; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rr = e / q4, k = (e - rr * q4) * 4;
-        const TX* xr = X + rr * sN;
-        __nv_bfloat16 hi[4], lo[4];
+__global__ void split_x_kernel(const TX* __restrict__ X, __nv_bfloat16* __restrict__ planes, PlaneTiling pt) {
+    const int nq = pt.nch * 16;  // quads per padded row
+    const int64_t nrows = pt.rows_padded() * pt.mid;
+    for (int64_t rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+        const int64_t i = rr / pt.mid, m = rr - (rr / pt.mid) * pt.mid;
+        const TX* xr = X + (i * pt.mid + m) * pt.sN;
+        const bool row_ok = i < pt.s1;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const int64_t k = 4 * (int64_t)q;
+            __nv_bfloat16 hi[4], lo[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) split1<TX>(k + u < sN ? xr[k + u] : (TX)0, hi[u], lo[u]);
-        uint2 vh, vl;
-        vh.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
-        vh.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
-        vl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
-        vl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
-        *reinterpret_cast<uint2*>(planes + rr * sNp + k) = vh;
-        *reinterpret_cast<uint2*>(planes + total + rr * sNp + k) = vl;
+            for (int u = 0; u < 4; ++u) split1<TX>(row_ok && k + u < pt.sN ? xr[k + u] : (TX)0, hi[u], lo[u]);
+            uint2 vh, vl;
+            vh.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
+            vh.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
+            vl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
+            vl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
+            *reinterpret_cast<uint2*>(planes + pt.elem(i, m, k, 0)) = vh;
+            *reinterpret_cast<uint2*>(planes + pt.elem(i, m, k, 1)) = vl;
+        }
     }
 }
 
-// B_Y planes [128][sNp]: rows 0..63 = hi of A^(N)[:, r0 + r]^T, rows 64..127 = lo.
-__global__ void split_by_kernel(const double* __restrict__ AN, int R, int r0, int64_t sN, int64_t sNp,
-                                __nv_bfloat16* __restrict__ BY) {
-    const int64_t total = (int64_t)kRT * sNp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / sNp);
-        const int64_t k = e % sNp;
-        const double a = (k < sN && r0 + r < R) ? AN[k * R + r0 + r] : 0.0;
-        const __nv_bfloat16 hi = __double2bfloat16(a);
-        BY[e] = hi;
-        BY[total + e] = __double2bfloat16(a - (double)__bfloat162float(hi));
+// One launch prepares a rank tile r0 .. r0 + 63.  blockIdx.y selects the part:
+// 0 = B_Y planes [128][pitch] (rows 0..63 hi of a^(N)[:, r0 + r]^T, rows
+// 64..127 lo), 1 = FP32 rows of A^(1) [s1][64], 2 = w_m for every slice
+// [mid][64] (the product over the middle modes in FP64, rounded once); all
+// zero padded in r.
+__global__ void prep_kernel(Shape s, Ptrs<const double> A, int r0, int64_t pitch, __nv_bfloat16* __restrict__ BY,
+                            float* __restrict__ A1f, float* __restrict__ W) {
+    const int R = s.R, N = s.N;
+    const int part = blockIdx.y;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (part == 0) {
+        const double* AN = A.p[N - 1];
+        const int64_t total = (int64_t)kRT * pitch, sN = s.dims[N - 1];
+        for (int64_t e = e0; e < total; e += stride) {
+            const int r = (int)(e / pitch);
+            const int64_t k = e % pitch;
+            const double a = (k < sN && r0 + r < R) ? AN[k * R + r0 + r] : 0.0;
+            const __nv_bfloat16 hi = __double2bfloat16(a);
+            BY[e] = hi;
+            BY[total + e] = __double2bfloat16(a - (double)__bfloat162float(hi));
+        }
+    } else if (part == 1) {
+        const int64_t total = s.dims[0] * kRT;
+        for (int64_t e = e0; e < total; e += stride) {
+            const int64_t i = e / kRT;
+            const int r = (int)(e % kRT);
+            A1f[e] = (r0 + r < R) ? (float)A.p[0][i * R + r0 + r] : 0.0f;
+        }
+    } else {
+        const int64_t total = s.mid * kRT;
+        for (int64_t e = e0; e < total; e += stride) {
+            int64_t m = e / kRT;
+            const int r = (int)(e % kRT);
+            double w = r0 + r < R ? 1.0 : 0.0;
+            for (int q = N - 2; q >= 1 && r0 + r < R; --q) {  // the last middle mode varies fastest in m
+                const int64_t iq = m % s.dims[q];
+                m /= s.dims[q];
+                w *= A.p[q][iq * R + r0 + r];
+            }
+            W[e] = (float)w;
+        }
     }
 }
 
-// FP32 copy of rows of a factor for columns r0..r0+63 (zero padded): out[rows][64]
-__global__ void factor_f32_kernel(const double* __restrict__ A, int R, int r0, int64_t rows, float* __restrict__ out) {
-    const int64_t total = rows * kRT;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / kRT;
-        const int r = (int)(e % kRT);
-        out[e] = (r0 + r < R) ? (float)A[i * R + r0 + r] : 0.0f;
-    }
-}
-
-// Reduce the unit partials into the FP64 outputs (fixed order), columns
-// r0..r0+Rt-1.  Block = 8 output rows of one mode; thread (row t/32, columns
-// 2*(t%32) + {0,1}); the partials are visited in a fixed order with coalesced
-// 256-byte row loads.
+// Reduce the partials into the FP64 outputs in a fixed order, columns r0 .. r0+Rt-1.
+// grid.y = mode.  Mode 1: block = 8 rows i of one i-block x 32 threads (two
+// columns each).  Mode N: block = 64 columns k of one chunk x 4 ranks, one
+// output per thread.  Both list the slots of their i-block (chunk's group) in
+// increasing order, kFinList at a time (the slot records are staged in shared
+// memory by all threads, then compacted by one warp), and sum the listed
+// partials with eight independent loads in flight.  Middle modes: block = 8
+// rows x 32 threads, summing the per-step column sums c_m times the other
+// middle factors.
 constexpr int kFinRows = 8;
-__global__ void finalize_kernel(Params p, Ptrs<double> M, Ptrs<const double> A, int R, int r0, int Rt,
-                                int64_t sNfull, unsigned mode_mask) {
+constexpr int kFinList = 1024;
+__device__ __forceinline__ int fin_list(const Params& p, int e0, int e1, int which, int key, int* list, int4* stage) {
+    __shared__ int cnt_s;
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) stage[e - e0] = p.seg[e];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int cnt = 0;
+        for (int e = e0; e < e1; e += 32) {
+            const int ee = e + lane;
+            bool hit = false;
+            if (ee < e1) {
+                const int4 sg = stage[ee - e0];
+                hit = sg.x >= 0 && (which == 0 ? (sg.x == key && sg.z != 0) : sg.y == key);
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            if (hit) list[cnt + __popc(mask & ((1u << lane) - 1u))] = ee;
+            cnt += __popc(mask);
+        }
+        if (lane == 0) cnt_s = cnt;
+    }
+    __syncthreads();
+    return cnt_s;
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M, Ptrs<const double> A, int R, int r0,
+                                                       int Rt, int nslots, unsigned mode_mask) {
+    __shared__ int list[kFinList];
+    __shared__ int4 stage[kFinList];
     const int N = p.N;
     const int n = blockIdx.y;
     if (!(mode_mask & (1u << n))) return;
-    const int64_t sn = n == 0 ? p.s1 : (n == N - 1 ? p.sN : p.middim[n]);
-    const int64_t i = (int64_t)blockIdx.x * kFinRows + (threadIdx.x >> 5);
-    if (i >= sn) return;
+    if (n == N - 1) {
+        const int c = blockIdx.x >> 4, rq = blockIdx.x & 15;  // chunk, group of 4 ranks
+        if (c >= p.nch) return;  // uniform over the block
+        const int kk = threadIdx.x & 63, r = rq * 4 + (threadIdx.x >> 6);
+        const int64_t k = (int64_t)c * kKC + kk;
+        const int g = c / kGroup, cc = c % kGroup;
+        const float* src = p.P_Z + ((int64_t)cc * kRT + r) * kKC + kk;
+        const int64_t sstride = (int64_t)kGroup * kRT * kKC;  // floats per slot
+        double acc = 0.0;
+        for (int e0 = 0; e0 < nslots; e0 += kFinList) {
+            const int cnt = fin_list(p, e0, min(nslots, e0 + kFinList), 1, g, list, stage);
+            for (int j = 0; j < cnt; j += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = j + u < cnt ? src[(int64_t)list[j + u] * sstride] : 0.0f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += v[u];
+            }
+            __syncthreads();
+        }
+        if (k < p.sN && r < Rt) M.p[n][k * R + r0 + r] = acc;
+        return;
+    }
+    const int64_t sn = n == 0 ? p.s1 : p.middim[n];
+    const int64_t i0 = (int64_t)blockIdx.x * kFinRows;
+    if (i0 >= sn) return;  // uniform over the block
+    const int64_t i = i0 + (threadIdx.x >> 5);
     const int c0 = 2 * (threadIdx.x & 31);
     double acc0 = 0.0, acc1 = 0.0;
     if (n == 0) {
-        const int b = (int)(i / kBI);
-        for (int kg = 0; kg < p.nkg; ++kg)
-            for (int j = 0; j < p.nsplit; ++j) {
-                const int u = (b * p.nkg + kg) * p.nsplit + j;
-                const float2 v = *reinterpret_cast<const float2*>(p.P_Y1 + ((int64_t)u * kBI + (i % kBI)) * kRT + c0);
-                acc0 += v.x;
-                acc1 += v.y;
+        const int b = (int)(i0 / kBI);  // 8 divides 128: the block's rows share an i-block
+        for (int e0 = 0; e0 < nslots; e0 += kFinList) {
+            const int cnt = fin_list(p, e0, min(nslots, e0 + kFinList), 0, b, list, stage);
+            if (i < sn) {
+                const float* src = p.P_Y1 + (i % kBI) * kRT + c0;
+                for (int j = 0; j < cnt; j += 8) {
+                    float2 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        v[u] = j + u < cnt ? *reinterpret_cast<const float2*>(src + (int64_t)list[j + u] * kBI * kRT)
+                                           : make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        acc0 += v[u].x;
+                        acc1 += v[u].y;
+                    }
+                }
             }
-    } else if (n == N - 1) {
-        const int kg = (int)(i / (kChunksPerGroup * kKC));
-        for (int b = 0; b < p.nib; ++b)
-            for (int j = 0; j < p.nsplit; ++j) {
-                const int u = (b * p.nkg + kg) * p.nsplit + j;
-                const float2 v = *reinterpret_cast<const float2*>(
-                    p.P_Z + ((int64_t)u * (kChunksPerGroup * kKC) + (i % (kChunksPerGroup * kKC))) * kRT + c0);
-                acc0 += v.x;
-                acc1 += v.y;
-            }
+            __syncthreads();
+        }
     } else {
-        // middle mode n: sum over the slices m whose index in mode n is i
-        const int64_t sub = p.mid / p.middim[n];
+        if (i >= sn) return;
+        // middle mode n: sum over the slices m whose index in mode n is i of
+        // (sum over the (b, g) partials of c_m) * (product of the other middle factors)
+        const int64_t sub = p.mid / sn;
+        const int nbg = p.nib * p.ngr;
         for (int64_t t = 0; t < sub; ++t) {
             int64_t rem = t, m = 0, mult = 1;
             double lo0 = 1.0, lo1 = 1.0;
             for (int q = N - 2; q >= 1; --q) {
+                const int64_t dq = p.middim[q];
                 int64_t iq;
                 if (q == n) {
                     iq = i;
                 } else {
-                    iq = rem % p.middim[q];
-                    rem /= p.middim[q];
+                    iq = rem % dq;
+                    rem /= dq;
                     if (c0 < Rt) lo0 *= A.p[q][iq * R + r0 + c0];
                     if (c0 + 1 < Rt) lo1 *= A.p[q][iq * R + r0 + c0 + 1];
                 }
                 m += iq * mult;
-                mult *= p.middim[q];
+                mult *= dq;
             }
+            const float* src = p.P_c + m * kRT + c0;
             double cs0 = 0.0, cs1 = 0.0;
-            for (int bk = 0; bk < p.nib * p.nkg; ++bk) {
-                const float2 v = *reinterpret_cast<const float2*>(p.P_c + ((int64_t)bk * p.mid + m) * kRT + c0);
-                cs0 += v.x;
-                cs1 += v.y;
+            for (int j = 0; j < nbg; j += 8) {
+                float2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = j + u < nbg ? *reinterpret_cast<const float2*>(src + (int64_t)(j + u) * p.mid * kRT)
+                                       : make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    cs0 += v[u].x;
+                    cs1 += v[u].y;
+                }
             }
             acc0 += cs0 * lo0;
             acc1 += cs1 * lo1;
         }
     }
+    if (i >= sn) return;
     if (c0 < Rt) M.p[n][i * R + r0 + c0] = acc0;
     if (c0 + 1 < Rt) M.p[n][i * R + r0 + c0 + 1] = acc1;
-    (void)sNfull;
 }
 
 // ------------------------------------------------------------ host side
@@ -658,7 +967,7 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-static int64_t pad8(int64_t v) { return (v + 7) / 8 * 8; }
+
 #ifdef CPGN_TC_TRACE
 long long* tc_trace_ptr = nullptr;
 #endif
@@ -667,17 +976,13 @@ long long* tc_trace_ptr = nullptr;
 
 using namespace tc;
 
-size_t split_cache_bytes(const cp_desc* d) {
-    int64_t rows = 1;
-    for (int n = 0; n + 1 < d->order; ++n) rows *= d->dims[n];
-    return (size_t)(2 * rows * pad8(d->dims[d->order - 1]) * sizeof(__nv_bfloat16));
-}
+size_t split_cache_bytes(const cp_desc* d) { return (size_t)PlaneTiling::of(make_shape(d)).total() * sizeof(__nv_bfloat16); }
 
 int tc_launch_count(const SplitCache& c, const cp_desc* d, const Shape& s) {
     const bool hit = c.planes && c.key_ptr != nullptr && c.key_version == d->x_version && c.key_total == s.total &&
                      c.key_dtype == (int)d->x_dtype;
     const int tiles = (s.R + kRT - 1) / kRT;
-    return (hit ? 0 : 1) + tiles * (2 + (s.N - 2) + 2);
+    return (hit ? 0 : 1) + tiles * 3;  // per rank tile: prep, main, finalize
 }
 
 void split_cache_free(SplitCache& c) {
@@ -699,30 +1004,33 @@ static cp_status ensure_buf(void*& p, size_t& cur, size_t need) {
     return CP_OK;
 }
 
-// Launch geometry of one tensor-core MTTKRP over the shape.
+
+// Launch geometry: grid = min(SMs, steps); CTA g takes steps
+// [g T / G, (g + 1) T / G), at most ceil(T / G) of them.  Segments start at
+// the range start, at every run start (m = 0) and after kLmax steps of a run,
+// so a CTA has at most floor(per / kLmax) + ceil(per / mid) + 2 of them.
 struct TcGeom {
-    int nib, nkg, nsplit, nunits, grid;
+    int nib, nch, ngr, grid, smax;
+    int64_t steps;
 };
 static TcGeom tc_geom(const Shape& s, int sms) {
     TcGeom g;
+    const int64_t mid = s.mid;
     g.nib = (int)((s.dims[0] + kBI - 1) / kBI);
-    const int64_t chunks = (s.dims[s.N - 1] + kKC - 1) / kKC;
-    g.nkg = (int)((chunks + kChunksPerGroup - 1) / kChunksPerGroup);
-    const int pairs = g.nib * g.nkg;
-    g.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(s.mid, (sms + pairs - 1) / pairs));
-    g.nunits = pairs * g.nsplit;
-    g.grid = std::min(g.nunits, sms);
+    g.nch = (int)((s.dims[s.N - 1] + kKC - 1) / kKC);
+    g.ngr = (g.nch + kGroup - 1) / kGroup;
+    g.steps = (int64_t)g.nib * g.ngr * mid;
+    g.grid = (int)imin(sms, g.steps);
+    const int64_t per = (g.steps + g.grid - 1) / g.grid;
+    g.smax = (int)(per / kLmax + (per + mid - 1) / mid + 2);
     return g;
 }
-
-int64_t tc_row_pitch(int64_t sN) { return pad8(sN); }
 
 // bf16 planes of X, cached by pointer / size / version.
 static cp_status tc_split_x(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, int sms,
                             cudaStream_t st) {
-    const int N = s.N;
-    const int64_t sN = s.dims[N - 1], sNp = pad8(sN), rows = s.dims[0] * s.mid;
-    const size_t pbytes = (size_t)2 * rows * sNp * sizeof(__nv_bfloat16);
+    const PlaneTiling pt = PlaneTiling::of(s);
+    const size_t pbytes = (size_t)pt.total() * sizeof(__nv_bfloat16);
     const bool hit = c.planes && c.key_ptr == X && c.key_version == d->x_version && c.key_total == s.total &&
                      c.key_dtype == (int)d->x_dtype && c.bytes >= pbytes;
     if (hit) return CP_OK;
@@ -736,11 +1044,11 @@ static cp_status tc_split_x(SplitCache& c, const cp_desc* d, const Shape& s, con
         }
         c.bytes = pbytes;
     }
-    const int blocks = sms * 8;
+    const int blocks = sms * 16;
     if (d->x_dtype == CP_F32)
-        split_x_kernel<float><<<blocks, 256, 0, st>>>((const float*)X, (__nv_bfloat16*)c.planes, rows, sN, sNp);
+        split_x_kernel<float><<<blocks, 128, 0, st>>>((const float*)X, (__nv_bfloat16*)c.planes, pt);
     else
-        split_x_kernel<double><<<blocks, 256, 0, st>>>((const double*)X, (__nv_bfloat16*)c.planes, rows, sN, sNp);
+        split_x_kernel<double><<<blocks, 128, 0, st>>>((const double*)X, (__nv_bfloat16*)c.planes, pt);
     c.key_ptr = X;
     c.key_version = d->x_version;
     c.key_total = s.total;
@@ -748,7 +1056,7 @@ static cp_status tc_split_x(SplitCache& c, const cp_desc* d, const Shape& s, con
     return CP_OK;
 }
 
-// MTTKRP on planes [2][s1][mid][sNp] that are already in device memory.
+// MTTKRP on bf16 planes (PlaneTiling layout) that are already in device memory.
 static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs<const double> A, Ptrs<double> M,
                          unsigned mode_mask, int* status, cudaStream_t st) {
     EncodeTiledFn enc = encode_fn();
@@ -757,44 +1065,41 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int N = s.N, R = s.R;
-    const int64_t s1 = s.dims[0], sN = s.dims[N - 1], mid = s.mid, sNp = pad8(sN);
-    // ---- workspace: factor planes and unit partials
+    const int64_t s1 = s.dims[0], sN = s.dims[N - 1], mid = s.mid;
     const TcGeom g = tc_geom(s, sms);
-    int64_t midrows = 0;
+    const int64_t pitch = (int64_t)g.nch * kKC;  // row pitch of the B_Y planes
+    const int nslots = g.grid * g.smax;
     Params p{};
     p.N = N;
+    p.planes = (const unsigned char*)planes;
+    p.pt = PlaneTiling::of(s);
     p.s1 = s1;
     p.mid = mid;
     p.sN = sN;
     p.nib = g.nib;
-    p.nkg = g.nkg;
-    p.nsplit = g.nsplit;
-    p.nunits = g.nunits;
-    for (int q = 1; q + 1 < N; ++q) {
-        p.midoff[q] = midrows;
-        p.middim[q] = s.dims[q];
-        midrows += s.dims[q];
-    }
-    const size_t by_b = (size_t)2 * kRT * sNp * sizeof(__nv_bfloat16);
-    const size_t a1_b = (size_t)s1 * kRT * sizeof(float);
-    const size_t mid_b = (size_t)std::max<int64_t>(midrows, 1) * kRT * sizeof(float);
-    const size_t py_b = (size_t)g.nunits * kBI * kRT * sizeof(float);
-    const size_t pz_b = (size_t)g.nunits * kChunksPerGroup * kKC * kRT * sizeof(float);
-    const size_t pc_b = (size_t)g.nib * g.nkg * mid * kRT * sizeof(float);
-    const size_t off_a1 = (by_b + 255) / 256 * 256;
-    const size_t off_mid = off_a1 + (a1_b + 255) / 256 * 256;
-    const size_t off_py = off_mid + (mid_b + 255) / 256 * 256;
-    const size_t off_pz = off_py + (py_b + 255) / 256 * 256;
-    const size_t off_pc = off_pz + (pz_b + 255) / 256 * 256;
-    const size_t total_b = off_pc + pc_b;
-    if (ensure_buf(c.fac, c.fac_bytes, total_b) != CP_OK) return CP_ERR_NOMEM;
+    p.nch = g.nch;
+    p.ngr = g.ngr;
+    p.steps = g.steps;
+    p.smax = g.smax;
+    for (int q = 1; q + 1 < N; ++q) p.middim[q] = s.dims[q];
+    // ---- workspace: operand planes and partials
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t by_b = al((size_t)2 * kRT * pitch * sizeof(__nv_bfloat16));
+    const size_t a1_b = al((size_t)s1 * kRT * sizeof(float));
+    const size_t w_b = al((size_t)mid * kRT * sizeof(float));
+    const size_t py_b = al((size_t)nslots * kBI * kRT * sizeof(float));
+    const size_t pz_b = al((size_t)nslots * kGroup * kRT * kKC * sizeof(float));
+    const size_t pc_b = al((size_t)g.nib * g.ngr * mid * kRT * sizeof(float));
+    const size_t sg_b = al((size_t)nslots * sizeof(int4));
+    if (ensure_buf(c.fac, c.fac_bytes, by_b + a1_b + w_b + py_b + pz_b + pc_b + sg_b) != CP_OK) return CP_ERR_NOMEM;
     unsigned char* wb = (unsigned char*)c.fac;
     __nv_bfloat16* BY = (__nv_bfloat16*)wb;
-    p.A1f = (const float*)(wb + off_a1);
-    p.midf = (const float*)(wb + off_mid);
-    p.P_Y1 = (float*)(wb + off_py);
-    p.P_Z = (float*)(wb + off_pz);
-    p.P_c = (float*)(wb + off_pc);
+    p.A1f = (const float*)(wb += by_b);
+    p.W = (const float*)(wb += a1_b);
+    p.P_Y1 = (float*)(wb += w_b);
+    p.P_Z = (float*)(wb += py_b);
+    p.P_c = (float*)(wb += pz_b);
+    p.seg = (int4*)(wb += pc_b);
     p.status = status;
     p.trace = nullptr;
 #ifdef CPGN_TC_TRACE
@@ -806,26 +1111,15 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
         tc_trace_ptr = trace_buf;
     }
 #endif
-    // ---- tensor maps
-    CUtensorMap tmX, tmBY;
+    // ---- tensor map of the B_Y planes (rows of s_N elements; the pitch padding reads as zero)
+    CUtensorMap tmBY;
     {
-        cuuint64_t dims[4] = {(cuuint64_t)sNp, (cuuint64_t)mid, (cuuint64_t)s1, 2};
-        cuuint64_t strides[3] = {(cuuint64_t)(sNp * 2), (cuuint64_t)(mid * sNp * 2), (cuuint64_t)(s1 * mid * sNp * 2)};
-        cuuint32_t box[4] = {64, 1, (cuuint32_t)kBI, 2};
-        cuuint32_t es[4] = {1, 1, 1, 1};
-        if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(planes), dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return CP_ERR_UNSUPPORTED;
-    }
-    {
-        cuuint64_t dims[2] = {(cuuint64_t)sNp, 128};
-        cuuint64_t strides[1] = {(cuuint64_t)(sNp * 2)};
-        cuuint32_t box[2] = {64, 128};
+        cuuint64_t dims[2] = {(cuuint64_t)sN, 128};
+        cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+        cuuint32_t box[2] = {(cuuint32_t)kKC, 128};
         cuuint32_t es[2] = {1, 1};
         if (enc(&tmBY, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, BY, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                CU_TENSOR_MAP_SWIZZLE_128B, kL2Promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return CP_ERR_UNSUPPORTED;
     }
     static bool attr_set[64] = {};
@@ -837,21 +1131,17 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
         }
         if (dev < 64) attr_set[dev] = true;
     }
+    int64_t rows = s1;
+    for (int q = 1; q + 1 < N; ++q) rows = std::max<int64_t>(rows, s.dims[q]);
+    const int64_t fx = std::max<int64_t>((rows + kFinRows - 1) / kFinRows, (int64_t)g.nch * 16);
+    const dim3 fgrid((unsigned)fx, (unsigned)N);
     for (int r0 = 0; r0 < R; r0 += kRT) {
         const int Rt = std::min(kRT, R - r0);
         p.R = Rt;
-        split_by_kernel<<<sms, 256, 0, st>>>(A.p[N - 1], R, r0, sN, sNp, BY);
-        factor_f32_kernel<<<sms, 256, 0, st>>>(A.p[0], R, r0, s1, (float*)p.A1f);
-        for (int q = 1; q + 1 < N; ++q)
-            factor_f32_kernel<<<64, 256, 0, st>>>(A.p[q], R, r0, s.dims[q], (float*)p.midf + p.midoff[q] * kRT);
-        mttkrp_tc_kernel<<<g.grid, kThreads, kDynSmem, st>>>(tmX, tmBY, p);
+        prep_kernel<<<dim3(sms, 3), 256, 0, st>>>(s, A, r0, pitch, BY, (float*)p.A1f, (float*)p.W);
+        mttkrp_tc_kernel<<<g.grid, kThreads, kDynSmem, st>>>(tmBY, p);
         if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
-        int64_t mx = 0;
-        for (int n = 0; n < N; ++n) mx = std::max<int64_t>(mx, s.dims[n] * Rt);
-        int64_t mrows = 0;
-        for (int n = 0; n < N; ++n) mrows = std::max<int64_t>(mrows, s.dims[n]);
-        dim3 fg((unsigned)((mrows + kFinRows - 1) / kFinRows), N);
-        finalize_kernel<<<fg, 32 * kFinRows, 0, st>>>(p, M, A, R, r0, Rt, sN, mode_mask);
+        finalize_kernel<<<fgrid, 256, 0, st>>>(p, M, A, R, r0, Rt, nslots, mode_mask);
         if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
     }
     return CP_OK;
@@ -885,7 +1175,7 @@ cp_status tc_mttkrp_planes(SplitCache& c, const void* planes, const Shape& s, Pt
 }  // namespace cpgn
 
 #ifdef CPGN_TC_TRACE
-// trace builds only: device pointer of the last trace buffer (8 x 1024 int64)
+// trace builds only: copy the last trace buffer (8 x 1024 int64) to the host
 extern "C" int cpgn_tc_trace_copy(long long* host) {
     if (!cpgn::tc::tc_trace_ptr) return 1;
     return cudaMemcpy(host, cpgn::tc::tc_trace_ptr, 8 * 1024 * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess;

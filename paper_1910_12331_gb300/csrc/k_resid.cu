@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include "kernels.hpp"
+#include "tc.hpp"
 
 namespace cpgn {
 
@@ -71,7 +72,7 @@ __device__ __forceinline__ void df_sq_acc(float& h, float& l, float x) {
 template <typename TX>
 __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __restrict__ X,
                                                         const float2* __restrict__ Adf,
-                                                        __nv_bfloat16* __restrict__ planes, int64_t sNp,
+                                                        __nv_bfloat16* __restrict__ planes, PlaneTiling pt,
                                                         DevStats* stats) {
     __shared__ float2 As[RC][TI];
     __shared__ float2 Bs[RC][TK];
@@ -134,17 +135,18 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
         __syncthreads();
     }
     float nh = 0.f, nl = 0.f, dh = 0.f, dl = 0.f;
-    const int64_t total_p = s1 * mid * sNp;
+    // every row and column of every tile is written (zero outside the tensor)
+    const int64_t iw = pt.rows_padded(), kw = (int64_t)pt.nch * 64;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int64_t i = i0 + ti * 8 + u;
-        if (i >= s1) continue;
+        if (i >= iw) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int64_t k = k0 + tk + 16 * c;
-            if (k >= sNp) continue;
+            if (k >= kw) continue;
             float e = 0.0f;
-            if (k < sN) {
+            if (k < sN && i < s1) {
                 const TX x = X[(i * mid + m) * sN + k];
                 if constexpr (sizeof(TX) == 4) {
                     // x - sh is exact when the reconstruction is close (Sterbenz)
@@ -159,9 +161,8 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(e);
             const __nv_bfloat16 lo = __float2bfloat16_rn(e - __bfloat162float(hi));
-            const int64_t o = (i * mid + m) * sNp + k;
-            planes[o] = hi;
-            planes[total_p + o] = lo;
+            planes[pt.elem(i, m, k, 0)] = hi;
+            planes[pt.elem(i, m, k, 1)] = lo;
         }
     }
     // per-thread double-float partials, combined in FP64 across the block
@@ -182,14 +183,15 @@ __global__ void factors_df_kernel(Shape s, Ptrs<const double> A, float2* Adf) {
 }
 
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                        int64_t sNp, void* Adf_scratch, DevStats* stats, cudaStream_t st) {
+                        void* Adf_scratch, DevStats* stats, cudaStream_t st) {
     float2* Adf = (float2*)Adf_scratch;
     factors_df_kernel<<<dim3(32, s.N), 256, 0, st>>>(s, A, Adf);
-    dim3 grid((unsigned)s.mid, (unsigned)((s.dims[0] + TI - 1) / TI), (unsigned)((sNp + TK - 1) / TK));
+    const PlaneTiling pt = PlaneTiling::of(s);
+    dim3 grid((unsigned)s.mid, (unsigned)((pt.rows_padded() + TI - 1) / TI), (unsigned)((pt.nch * 64 + TK - 1) / TK));
     if (xdt == CP_F32)
-        resid_split_kernel<float><<<grid, NT, 0, st>>>(s, (const float*)X, Adf, (__nv_bfloat16*)planes, sNp, stats);
+        resid_split_kernel<float><<<grid, NT, 0, st>>>(s, (const float*)X, Adf, (__nv_bfloat16*)planes, pt, stats);
     else
-        resid_split_kernel<double><<<grid, NT, 0, st>>>(s, (const double*)X, Adf, (__nv_bfloat16*)planes, sNp, stats);
+        resid_split_kernel<double><<<grid, NT, 0, st>>>(s, (const double*)X, Adf, (__nv_bfloat16*)planes, pt, stats);
 }
 
 }  // namespace cpgn

@@ -79,10 +79,10 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st);
 void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
                        Ptrs<double> Q, double* Y, cudaStream_t st);
 
-// ---- residual tensor in double-float, as bf16 planes [2][s1][mid][sNp] (k_resid.cu)
+// ---- residual tensor in double-float, as bf16 planes in PlaneTiling layout (k_resid.cu)
 // Adf_scratch: (sum_n s_n) * R float2 (double-float copy of the factors).
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                        int64_t sNp, void* Adf_scratch, DevStats* stats, cudaStream_t st);
+                        void* Adf_scratch, DevStats* stats, cudaStream_t st);
 
 // ---- residual (k_residual.cu) ------------------------------------------------------
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,
