@@ -156,16 +156,13 @@ void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, co
 // stable for symmetric positive definite matrices.  Its pivots are the Schur
 // complement diagonals, i.e. the squares of the Cholesky diagonals, so the
 // positivity test of every pivot is the Cholesky SPD test.
-// T = double: the plain path (a non-positive pivot raises CP_ERR_NOT_SPD).
-// T = float: the mixed path, whose CG runs in FP32 anyway: a pivot that
-// rounding drives below 1e-7 times its diagonal entry is clamped to that
-// value, which keeps the preconditioner SPD (an approximate block-Jacobi
-// preconditioner changes the CG iteration count, not what CG converges to).
+// A non-positive pivot raises CP_ERR_NOT_SPD.  The inverse is written in FP64
+// (Pinv) and, for the mixed path, rounded to FP32 (PinvF).
 constexpr int kPrecondThreads = 512;
 
-template <typename T>
 __global__ void __launch_bounds__(kPrecondThreads) precond_kernel(Shape s, const double* Gam, double lam, double* Pinv,
-                                                                  float* PinvF, T* scratch, DevStats* stats) {
+                                                                  float* PinvF, double* scratch, DevStats* stats) {
+    using T = double;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_bad;
     __shared__ T s_inv;
@@ -182,14 +179,9 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_kernel(Shape s, const
     for (int j = 0; j < R; ++j) {
         if (threadIdx.x == 0) {
             T p = B[j * R + j];
-            if constexpr (sizeof(T) == 8) {
-                if (!(p > 0.0)) {
-                    s_bad = 1;
-                    p = 1.0;
-                }
-            } else {
-                const T floor_p = (T)(1e-7 * fabs(Gnn[j * R + j] + lam));
-                if (!(p > floor_p)) p = floor_p > 0.f ? floor_p : 1.f;
+            if (!(p > 0.0)) {
+                s_bad = 1;
+                p = 1.0;
             }
             s_inv = (T)1 / p;
         }
@@ -224,25 +216,18 @@ void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv,
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 64 || !attr_set[dev]) {
-        cudaFuncSetAttribute(precond_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(precond_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (dev < 64) attr_set[dev] = true;
     }
-    const size_t elems = (size_t)s.R * s.R + s.R;
-    if (fp32) {
-        const size_t bytes = elems * sizeof(float);
-        if (bytes <= 200 * 1024)
-            precond_kernel<float><<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, nullptr, PinvF, nullptr, stats);
-        else
-            precond_kernel<float><<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, nullptr, PinvF, (float*)scratch,
-                                                                   stats);
-        return;
-    }
-    const size_t bytes = elems * sizeof(double);
+    // The elimination always runs in FP64: the blocks Gamma^(n,n) + lam I of a
+    // collinear problem at small lam are too ill-conditioned for an FP32
+    // elimination.  The FP32 CG of the mixed path gets the FP64 inverse rounded once.
+    const size_t bytes = ((size_t)s.R * s.R + s.R) * sizeof(double);
+    float* pf = fp32 ? PinvF : nullptr;
     if (bytes <= 200 * 1024)
-        precond_kernel<double><<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, PinvF, nullptr, stats);
+        precond_kernel<<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, pf, nullptr, stats);
     else
-        precond_kernel<double><<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, Pinv, PinvF, scratch, stats);
+        precond_kernel<<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, Pinv, pf, scratch, stats);
 }
 
 size_t precond_smem_bytes(int R) {
