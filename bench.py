@@ -164,6 +164,32 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernel(which):
+    """A few launches of one kernel on the workload (for ncu captures): the
+    first mixed-path GN step (pcg: one persistent CP-CG launch per step) or
+    the bf16x3 all-mode MTTKRP (mttkrp)."""
+    import torch
+
+    from paper_1910_12331_gb300 import api, datagen
+
+    p = datagen.workload(WORKLOAD, seed=0)
+    dev = torch.device("cuda", 0)
+    X = torch.from_numpy(p["X"]).to(dev)
+    init = [torch.from_numpy(a.copy()).to(dev) for a in p["init"]]
+    h = api.Handle(dev)
+    if which == "mttkrp":
+        M = [torch.empty_like(a) for a in init]
+        for _ in range(3):
+            api.cp_mttkrp_all(h, X, init, M, prec="bf16x3")
+    else:
+        lam_hi, lam_lo = lam_thresholds(p["init"])
+        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, prec="bf16x3")
+        for _ in range(3):
+            api.cp_gn_step(h, X, [a.clone() for a in init], params, check=False)
+    torch.cuda.synchronize()
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,9 +197,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["pcg", "mttkrp"], default=None,
+                    help="profiling aid: only run a few launches of one kernel on the workload, print nothing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return run_kernel(args.kernel)
 
     import torch
 

@@ -24,7 +24,7 @@
 // modes.  Both GEMMs read the same shared-memory X chunk: GEMM-Y as a K-major
 // A operand, GEMM-Z as an MN-major B operand.
 //
-// Kernel: persistent, one CTA per SM, 16 warps; CTA g owns a contiguous range
+// Kernel: persistent, one CTA per SM, 12 warps; CTA g owns a contiguous range
 // of steps in (b, g, m) order (m fastest).
 //   warp 0      producer: the step's X chunk tiles (128 i x 64 k, both planes,
 //               32 KB each, stored pre-swizzled so that linear bulk copies land
@@ -33,13 +33,12 @@
 //               (2 x 16 KB by TMA, resident for the run).
 //   warp 1      TMEM allocator and GEMM-Y issuer (one thread).
 //   warp 2      GEMM-Z issuer (one thread).
-//   warps 3-6   B_Z builders: B_Z = split(a^(1)(block b) * w_m)^T, K-major,
-//               double-buffered.
-//   warps 8-15  epilogue (two warps per TMEM lane quadrant, 32 rank columns
-//               each): D_Y (double-buffered in TMEM) -> M^(1), c_m; D_Z at
-//               segment end.
-//   warp 7      idle.  Warp w runs on sub-partition w mod 4, so every
-//               sub-partition holds one builder and two epilogue warps.
+//   warp 3      idle.
+//   warps 4-11  workers, two per TMEM lane quadrant: build B_Z =
+//               split(a^(1)(block b) * w_m)^T (K-major, double-buffered) one
+//               step ahead, then drain D_Y (double-buffered in TMEM) into
+//               M^(1) and c_m, and D_Z at segment end.  One code path per
+//               sub-partition keeps the hot instruction footprint small.
 // Partials go to workspace in FP32 and a finalize kernel reduces them in a
 // fixed order into the FP64 outputs (no atomics, deterministic).
 // Every mbarrier wait is bounded: on expiry the CTA records CP_ERR_TIMEOUT,
@@ -57,8 +56,8 @@ namespace cpgn {
 
 namespace tc {
 
-constexpr int kThreads = 512;            // 16 warps
-constexpr int kEpi = 256;                // epilogue threads (two warps per TMEM lane quadrant)
+constexpr int kThreads = 384;            // 12 warps
+constexpr int kWork = 256;               // worker threads (two warps per TMEM lane quadrant)
 constexpr int kStages = 4;               // X chunk tiles in flight
 constexpr int kBI = 128;                 // rows of an i-block (M of GEMM-Y, K of GEMM-Z)
 constexpr int kKC = 64;                  // columns of a chunk
@@ -337,19 +336,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&C.drain[s]), 1);
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&C.bz_full[s]), 128);
+            mbar_init(smem_u32(&C.bz_full[s]), kWork);
             mbar_init(smem_u32(&C.bz_empty[s]), 1);
             mbar_init(smem_u32(&C.dy_full[s]), 1);
-            mbar_init(smem_u32(&C.dy_empty[s]), kEpi);
+            mbar_init(smem_u32(&C.dy_empty[s]), kWork);
         }
         for (int s = 0; s < kWRing; ++s) {
             mbar_init(smem_u32(&C.w_full[s]), 1);
-            mbar_init(smem_u32(&C.w_empty[s]), 128 + kEpi);  // every builder and epilogue thread
+            mbar_init(smem_u32(&C.w_empty[s]), kWork);
         }
         mbar_init(smem_u32(&C.by_full), 1);
         mbar_init(smem_u32(&C.by_empty), 1);
         mbar_init(smem_u32(&C.dz_full), 1);
-        mbar_init(smem_u32(&C.dz_empty), kEpi);
+        mbar_init(smem_u32(&C.dz_empty), kWork);
         *abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -527,89 +526,81 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_drain(smem_u32(&C.drain[1]), 0, p.status);
         }
         __syncwarp();
-    } else if (warp >= 3 && warp <= 6) {
-        // ------------------------------------------------------- B_Z builders
-        // (warps 3-6: one per sub-partition)
-        // thread: rows i0, i0 + 1 of the i-block, rank columns rh .. rh + 31.
-        // B_Z row 2r holds the hi part of column r, row 2r + 1 the lo part.
-        const int et = (warp - 3) * 32 + lane;  // 0..127
-        const int i0 = 2 * (et & 63), rh = 32 * (et >> 6);
+    } else if (warp >= 4) {
+        // ------------------------------------------------------------ workers
+        // Warps 4-11, two per TMEM lane quadrant.  Step t of the loop first
+        // builds B_Z of step t + 1, then drains D_Y of step t:
+        //   B_Z build: thread = rows i0, i0 + 1 of the i-block and 16 rank
+        //   columns; B_Z row 2r holds the hi part of column r, row 2r + 1 the lo part.
+        //   D_Y drain: thread = TMEM lane (row i) and 32 rank columns (warp half).
+        const int wk = warp - 4;
+        const int q = warp & 3;                  // TMEM lane quadrant of this warp
+        const int cb = 32 * (wk >> 2);           // first rank column of this warp's D_Y / D_Z share
+        const int row = q * 32 + lane;           // lane of D_Y (row i) and of D_Z (row rho)
+        const int et = wk * 32 + lane;           // 0..255
+        const int i0 = 2 * (et & 63), rq = 16 * (et >> 6);  // B_Z rows and first rank column
         auto grp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
             mbar_wait(bar, parity, abort_s, p.status);
-            named_sync(1, 128);
-            if (et == 0) C.dec[0] = *abort_s;
-            named_sync(1, 128);
-            return C.dec[0] == 0;
+            named_sync(2, kWork);
+            if (et == 0) C.dec[1] = *abort_s;
+            named_sync(2, kWork);
+            return C.dec[1] == 0;
         };
-        // byte address of element (row, i0) in buffer 0 is sub + (row & 7 term) + row * 128
+        // byte address of B_Z element (row, i0) in buffer 0 is rowbase[row & 7] + (row - 2 rq) * 128
         unsigned char* rowbase[8];
         {
             const int ii = i0 & 63;
-            unsigned char* sub = bz_gen0 + (i0 >> 6) * kOpSub + 2 * rh * 128;
+            unsigned char* sub = bz_gen0 + (i0 >> 6) * kOpSub + 2 * rq * 128;
 #pragma unroll
             for (int x = 0; x < 8; ++x) rowbase[x] = sub + ((((ii >> 3) ^ x) & 7) << 4) + (ii & 7) * 2;
         }
-        float a0[32], a1[32];
-        StepId sp = step_of(p, T0);
-        int pb = -1;
-        int64_t tt = 0;
-        for (int64_t t = T0; t < T1; ++t, ++tt, sp.next(p)) {
-            if (sp.b != pb) {
-                pb = sp.b;
-                const int64_t g0 = (int64_t)sp.b * kBI + i0;
+        float b0[16], b1[16];          // A^(1) rows i0, i0 + 1 (columns rq ..) of the block being built
+        float a1r[32], m1acc[32];      // A^(1) row `row` (columns cb ..) and the M^(1) partial
+        int bb = -1, pb = -1;
+        // B_Z of step `st` (relative index tb) into buffer tb & 1
+        auto build = [&](const StepId& st, int64_t tb) -> bool {
+            if (st.b != bb) {
+                bb = st.b;
+                const int64_t g0 = (int64_t)st.b * kBI + i0;
 #pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    a0[r] = g0 < p.s1 ? p.A1f[g0 * kRT + rh + r] : 0.0f;
-                    a1[r] = g0 + 1 < p.s1 ? p.A1f[(g0 + 1) * kRT + rh + r] : 0.0f;
+                for (int r = 0; r < 16; ++r) {
+                    b0[r] = g0 < p.s1 ? p.A1f[g0 * kRT + rq + r] : 0.0f;
+                    b1[r] = g0 + 1 < p.s1 ? p.A1f[(g0 + 1) * kRT + rq + r] : 0.0f;
                 }
             }
-            const int db = (int)(tt & 1);
-            const int ws = (int)(tt % kWRing);
-            if (!grp_wait(smem_u32(&C.bz_empty[db]), (uint32_t)(((tt >> 1) & 1) ^ 1))) break;
-            if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tt / kWRing) & 1))) break;
-            if (et == 0) TC_TRACE(3, (int)tt);
+            const int db = (int)(tb & 1), ws = (int)(tb % kWRing);
+            if (!grp_wait(smem_u32(&C.bz_empty[db]), (uint32_t)(((tb >> 1) & 1) ^ 1))) return false;
+            if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tb / kWRing) & 1))) return false;
+            if (et == 0) TC_TRACE(3, (int)tb);
             const uint32_t boff = db * kBZBytes;
-            const float4* wv = reinterpret_cast<const float4*>(&C.wring[ws][rh]);
+            const float4* wv = reinterpret_cast<const float4*>(&C.wring[ws][rq]);
 #pragma unroll
-            for (int r4 = 0; r4 < 32; r4 += 4) {
+            for (int r4 = 0; r4 < 16; r4 += 4) {
                 const float4 w4 = wv[r4 >> 2];
                 const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int r = r4 + u;
-                    const float p0 = a0[r] * w[u], p1 = a1[r] * w[u];
+                    const float p0 = b0[r] * w[u], p1 = b1[r] * w[u];
                     const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
                     const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - __low2float(hi), p1 - __high2float(hi));
                     *reinterpret_cast<__nv_bfloat162*>(rowbase[(2 * r) & 7] + boff + (2 * r) * 128) = hi;
                     *reinterpret_cast<__nv_bfloat162*>(rowbase[(2 * r + 1) & 7] + boff + (2 * r + 1) * 128) = lo;
                 }
             }
-            mbar_arrive(smem_u32(&C.w_empty[ws]));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&C.bz_full[db]));
-            if (et == 0) TC_TRACE(7, (int)tt);
-        }
-    } else if (warp >= 8) {
-        // ------------------------------------------------------------ epilogue
-        // Two warps per TMEM lane quadrant; warp half h takes rank columns
-        // 32h .. 32h + 31 of its 32 rows (and the same k columns of D_Z).
-        const int q = warp & 3;                // TMEM lane quadrant of this warp
-        const int cb = 32 * ((warp - 8) >> 2);  // first column of this warp
-        const int row = q * 32 + lane;         // lane of D_Y (row i) and of D_Z (row rho)
-        const int et = threadIdx.x - 256;      // 0..255
-        auto grp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
-            mbar_wait(bar, parity, abort_s, p.status);
-            named_sync(2, kEpi);
-            if (et == 0) C.dec[1] = *abort_s;
-            named_sync(2, kEpi);
-            return C.dec[1] == 0;
+            if (et == 0) TC_TRACE(7, (int)tb);
+            return true;
         };
-        float a1r[32], m1acc[32];
-        StepId sp = step_of(p, T0);
+        StepId sp = step_of(p, T0), nx = sp;
         SegTrack seg;
-        int done = 0, pb = -1;
+        int done = 0;
+        bool ok = T0 >= T1 || build(sp, 0);
         int64_t tt = 0;
-        for (int64_t t = T0; t < T1; ++t, ++tt, sp.next(p)) {
+        for (int64_t t = T0; t < T1 && ok; ++t, ++tt, sp.next(p)) {
+            nx.next(p);
+            if (t + 1 < T1 && !(ok = build(nx, tt + 1))) break;
             bool run_start, seg_start;
             seg.enter(t, T0, sp.m, run_start, seg_start);
             if (run_start) {
@@ -624,8 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int db = (int)(tt & 1);
             const int ws = (int)(tt % kWRing);
-            if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tt / kWRing) & 1))) break;
-            if (!grp_wait(smem_u32(&C.dy_full[db]), (uint32_t)((tt >> 1) & 1))) break;
+            if (!(ok = grp_wait(smem_u32(&C.dy_full[db]), (uint32_t)((tt >> 1) & 1)))) break;
             if (et == 0) TC_TRACE(4, (int)tt);
             tc_fence_after();
             const uint32_t ta = t_dy0 + db * 128 + cb + ((uint32_t)(q * 32) << 16);
@@ -656,11 +646,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive(smem_u32(&C.dy_empty[db]));
             mbar_arrive(smem_u32(&C.w_empty[ws]));
             if (p.N >= 3) {
-                named_sync(2, kEpi);
+                named_sync(2, kWork);
                 if (et < kRT)
                     p.P_c[(((int64_t)sp.b * p.ngr + sp.g) * p.mid + sp.m) * kRT + et] =
                         C.red[0][et] + C.red[1][et] + C.red[2][et] + C.red[3][et];
-                named_sync(2, kEpi);
+                named_sync(2, kWork);
             }
             if (et == 0) TC_TRACE(5, (int)tt);
             const bool rl = run_last(p, t, T1, sp.m);
@@ -674,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         *reinterpret_cast<float4*>(py + r) =
                             make_float4(m1acc[r], m1acc[r + 1], m1acc[r + 2], m1acc[r + 3]);
                 }
-                if (!grp_wait(smem_u32(&C.dz_full), (uint32_t)(seg.zs & 1))) break;
+                if (!(ok = grp_wait(smem_u32(&C.dz_full), (uint32_t)(seg.zs & 1)))) break;
                 tc_fence_after();
                 // D_Z[cc][rho][n]: rho = 2r + (lo part); n < 64: x_hi column k = n, else x_lo column n - 64
                 const int nc = (int)imin(kGroup, p.nch - sp.g * kGroup);
