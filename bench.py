@@ -164,6 +164,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def cp_loss_timing(dev, reps=5):
+    """Forward + backward of the CP loss ||X - [[A,B,C]]||^2 on the loss256
+    workload (256^3 FP32, R=32 N(0,1) factors): the library's autograd
+    Function (direct FP64 forward, fused all-mode MTTKRP backward) against
+    torch.einsum autograd of the same loss in FP64."""
+    import torch
+
+    from paper_1910_12331_gb300 import autograd, datagen
+
+    p = datagen.workload("loss256", seed=0)
+    X = torch.from_numpy(p["X"]).to(dev)
+    A0 = [torch.from_numpy(a.copy()).to(dev) for a in p["init"]]
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def ours(prec):
+        A = [a.clone().requires_grad_() for a in A0]
+        autograd.cp_loss(X, A, prec=prec).backward()
+
+    def einsum():
+        A = [a.clone().requires_grad_() for a in A0]
+        ((X.double() - torch.einsum("iz,jz,kz->ijk", *A)) ** 2).sum().backward()
+
+    return {"workload": "loss256: 256x256x256 FP32, R=32, N(0,1) factors", "unit": "ms (forward+backward)",
+            "ours_bf16x3_backward": timed(lambda: ours("bf16x3")), "ours_fp64_backward": timed(lambda: ours("fp64")),
+            "torch_einsum_fp64": timed(einsum)}
+
+
 def run_kernel(which):
     """A few launches of one kernel on the workload (for ncu captures): the
     first mixed-path GN step (pcg: one persistent CP-CG launch per step) or
@@ -315,6 +354,9 @@ def main():
     h2d = X_host.numel() * 4 + sum(a.numel() * 8 for a in init_host)
     d2h = sum(a.numel() * 8 for a in out)
 
+    # ---- CP loss autograd Function (256^3 FP32, R=32): forward + fused-MTTKRP backward vs an einsum baseline
+    loss_info = cp_loss_timing(dev)
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -364,6 +406,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "cp_loss": loss_info,
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": clk.summary(),
     }

@@ -223,6 +223,13 @@ cp_status cp_als_sweep(cp_handle h, const cp_desc* desc, const void* X, double* 
 cp_status cp_residual(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
                       double* rel_residual);
 
+/* The two FP64 sums behind cp_residual: *sq_err = ||X - [[A]]||_F^2 and
+ * *sq_x = ||X||_F^2 (host scalars; either may be NULL).  sq_err is the CP
+ * loss of Eq. (2.3) without its factor 1/2.  Synchronises.
+ * Errors: CP_ERR_ARG, CP_ERR_NOMEM, CP_ERR_CUDA. */
+cp_status cp_residual_sums(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
+                           double* sq_err, double* sq_x);
+
 /* ---------------------------------------------------------------------------
  * Matvec without device allocation.  The paper has no counterpart: this call
  * serves callers that cannot call cudaMalloc -- code running under a fixed,

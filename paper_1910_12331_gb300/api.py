@@ -25,7 +25,7 @@ PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3, "residual": CP_PREC_RESI
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
-           "cp_residual", "cp_gn_matvec_noalloc")
+           "cp_residual", "cp_residual_sums", "cp_gn_matvec_noalloc")
 
 
 class cp_desc(ctypes.Structure):
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = False):
                                   ctypes.POINTER(cp_solve_result)]
         L.cp_als_sweep.argtypes = [vp, pd, vp, vp, d, i, ctypes.POINTER(d)]
         L.cp_residual.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d)]
+        L.cp_residual_sums.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.cp_gn_matvec_noalloc.argtypes = [pd, vp, vp, d, vp, vp]
         for name in SYMBOLS:
             if name != "cp_status_string":
@@ -318,6 +319,17 @@ def cp_residual(h: Handle, X, A):
     r = ctypes.c_double()
     _check(load().cp_residual(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(r)), "cp_residual")
     return r.value
+
+
+def cp_residual_sums(h: Handle, X, A):
+    """(||X - [[A]]||_F^2, ||X||_F^2) in FP64."""
+    R = _factors(X, A)
+    h._bind_stream()
+    d = h.desc(X, R)
+    e, x = ctypes.c_double(), ctypes.c_double()
+    _check(load().cp_residual_sums(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(e),
+                                   ctypes.byref(x)), "cp_residual_sums")
+    return e.value, x.value
 
 
 def cp_gn_matvec_noalloc(A, W, lam, Q):

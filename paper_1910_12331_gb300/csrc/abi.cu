@@ -597,4 +597,22 @@ cp_status cp_residual(cp_handle h, const cp_desc* d, const void* X, const double
     return CP_OK;
 }
 
+cp_status cp_residual_sums(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* sq_err,
+                           double* sq_x) {
+    if (!h || !X) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    CP_TRY(grow(h->stats, sizeof(DevStats)));
+    if (!h->h_stats) CUDA_TRY(cudaMallocHost((void**)&h->h_stats, sizeof(DevStats)));
+    CUDA_TRY(cudaMemsetAsync(h->stats.p, 0, sizeof(DevStats), h->stream));
+    launch_residual_f64(s, d->x_dtype, X, ptrs_of(A, s.N), (DevStats*)h->stats.p, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CP_TRY(sync_stats(h));
+    if (sq_err) *sq_err = h->h_stats->res_num;
+    if (sq_x) *sq_x = h->h_stats->res_den;
+    return CP_OK;
+}
+
 }  // extern "C"
