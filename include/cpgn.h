@@ -231,6 +231,47 @@ cp_status cp_residual_sums(cp_handle h, const cp_desc* desc, const void* X, cons
                            double* sq_err, double* sq_x);
 
 /* ---------------------------------------------------------------------------
+ * Many small independent order-3 problems (Algorithm 1 with Algorithm 2 per
+ * problem) solved by one persistent kernel launch: each CTA takes problems
+ * from a work counter and runs the whole Gauss-Newton iteration of one problem
+ * in its shared memory (FP32 vectors, factors and Gram products; FP64 dot
+ * products, CG scalars, preconditioner elimination and factor master copy).
+ * A problem stops when its direct relative residual ||X - [[A]]|| / ||X|| <=
+ * target_residual (converged = 1), after max_iters GN iterations, or on an
+ * error (its status).  lambda follows the varying rule of Section 3.2 from
+ * lam (first iteration) with the problem's thresholds and mu. */
+#define CP_BATCH_MAX_SIDE 256
+#define CP_BATCH_MAX_RANK 32
+
+typedef struct {
+    int64_t dims[3];       /* s_1, s_2, s_3 (1 .. CP_BATCH_MAX_SIDE) */
+    int rank;              /* R (1 .. CP_BATCH_MAX_RANK) */
+    const float* X;        /* device, FP32, C-contiguous s_1 x s_2 x s_3 (caller-owned) */
+    double* A[3];          /* device, FP64 row-major s_n x R, in/out (caller-owned) */
+    double lam, lam_lo, lam_hi, mu;  /* regularisation of Section 3.2 */
+} cp_batch_problem;
+
+typedef struct {
+    int status;            /* cp_status of this problem (CP_OK, CP_ERR_NOT_SPD, CP_ERR_NONFINITE) */
+    int iters;             /* GN iterations performed */
+    int cg_iters_total;
+    int converged;         /* 1 if the residual target was met */
+    int cg_breakdowns;     /* CG solves ended early because the FP32 curvature <W, Q W> was not
+                              positive (the update found so far is applied) */
+    double rel_residual;   /* last residual evaluated (FP32 reconstruction, FP64 sums) */
+    double lam;            /* lambda of the last iteration */
+} cp_batch_result;
+
+/* problems and results are host arrays of nprob entries.  The shared memory a
+ * problem needs, 8 (R^2 + R + 96) + 4 (6 (s_1 + s_2 + s_3) R + 21 R^2) bytes,
+ * must not exceed 220 KB (CP_ERR_UNSUPPORTED).  Synchronises.
+ * Errors: CP_ERR_ARG (null pointers, sizes out of range, mu <= 1, lam < 0,
+ * lam_hi < lam_lo), CP_ERR_UNSUPPORTED, CP_ERR_NOMEM, CP_ERR_CUDA; per-problem
+ * device errors go to results[i].status. */
+cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
+                              int cg_max_iter, int max_iters, double target_residual, cp_batch_result* results);
+
+/* ---------------------------------------------------------------------------
  * Matvec without device allocation.  The paper has no counterpart: this call
  * serves callers that cannot call cudaMalloc -- code running under a fixed,
  * pre-reserved device-memory budget, inside an allocator or memory-pool

@@ -25,7 +25,7 @@ PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3, "residual": CP_PREC_RESI
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
-           "cp_residual", "cp_residual_sums", "cp_gn_matvec_noalloc")
+           "cp_residual", "cp_residual_sums", "cp_gn_solve_batched", "cp_gn_matvec_noalloc")
 
 
 class cp_desc(ctypes.Structure):
@@ -73,6 +73,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+class cp_batch_problem(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int64 * 3), ("rank", ctypes.c_int), ("X", ctypes.c_void_p),
+                ("A", ctypes.c_void_p * 3), ("lam", ctypes.c_double), ("lam_lo", ctypes.c_double),
+                ("lam_hi", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class cp_batch_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cg_iters_total", ctypes.c_int),
+                ("converged", ctypes.c_int), ("cg_breakdowns", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("lam", ctypes.c_double)]
+
+
 class CPError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -113,6 +125,8 @@ def load(build_if_missing: bool = False):
         L.cp_residual.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d)]
         L.cp_residual_sums.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.cp_gn_matvec_noalloc.argtypes = [pd, vp, vp, d, vp, vp]
+        L.cp_gn_solve_batched.argtypes = [vp, i, ctypes.POINTER(cp_batch_problem), d, i, i, d,
+                                          ctypes.POINTER(cp_batch_result)]
         for name in SYMBOLS:
             if name != "cp_status_string":
                 getattr(L, name).restype = ctypes.c_int
@@ -330,6 +344,32 @@ def cp_residual_sums(h: Handle, X, A):
     _check(load().cp_residual_sums(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(e),
                                    ctypes.byref(x)), "cp_residual_sums")
     return e.value, x.value
+
+
+def cp_gn_solve_batched(h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_iters=200, target_residual=1e-6):
+    """Solve many small order-3 problems in one persistent launch.  problems: list of
+    dicts with X (float32 CUDA, 3-D), A (three float64 CUDA (s_n, R) tensors, updated in
+    place), lam, lam_lo, lam_hi, mu.  Returns a list of result dicts."""
+    n = len(problems)
+    arr = (cp_batch_problem * max(n, 1))()
+    for k, q in enumerate(problems):
+        X, A = q["X"], q["A"]
+        if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 3 or not X.is_contiguous():
+            raise ValueError("batched: X must be a contiguous 3-D float32 CUDA tensor")
+        R = A[0].shape[1]
+        for m in range(3):
+            _check_factor(A[m], X.shape[m], R, f"A[{m}]")
+        arr[k].dims = (ctypes.c_int64 * 3)(*X.shape)
+        arr[k].rank = R
+        arr[k].X = X.data_ptr()
+        arr[k].A = (ctypes.c_void_p * 3)(*[a.data_ptr() for a in A])
+        arr[k].lam, arr[k].lam_lo, arr[k].lam_hi, arr[k].mu = q["lam"], q["lam_lo"], q["lam_hi"], q.get("mu", 2.0)
+    res = (cp_batch_result * max(n, 1))()
+    h._bind_stream()
+    _check(load().cp_gn_solve_batched(h.h, n, arr, eps_cg, cg_max_iter, max_iters, target_residual, res),
+           "cp_gn_solve_batched")
+    keys = ("status", "iters", "cg_iters_total", "converged", "cg_breakdowns", "rel_residual", "lam")
+    return [{k2: getattr(res[k], k2) for k2 in keys} for k in range(n)]
 
 
 def cp_gn_matvec_noalloc(A, W, lam, Q):

@@ -597,6 +597,17 @@ cp_status cp_residual(cp_handle h, const cp_desc* d, const void* X, const double
     return CP_OK;
 }
 
+cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
+                              int cg_max_iter, int max_iters, double target_residual, cp_batch_result* results) {
+    if (!h || nprob < 0 || (nprob > 0 && (!problems || !results)) || cg_max_iter < 0 || max_iters < 0 ||
+        !(eps_cg >= 0.0))
+        return CP_ERR_ARG;
+    if (nprob == 0) return CP_OK;
+    DeviceGuard g(h->device);
+    return run_batched(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters, target_residual,
+                       results);
+}
+
 cp_status cp_residual_sums(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* sq_err,
                            double* sq_x) {
     if (!h || !X) return CP_ERR_ARG;

@@ -88,4 +88,8 @@ void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const 
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,
                          cudaStream_t st);
 
+// ---- batched small problems (k_batched.cu) -----------------------------------------
+cp_status run_batched(int device, cudaStream_t stream, int nprob, const cp_batch_problem* problems, double eps_cg,
+                      int cg_max_iter, int max_iters, double target_residual, cp_batch_result* results);
+
 }  // namespace cpgn

@@ -72,8 +72,8 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "cpgn.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(cp_desc), sizeof(cp_gn_params), sizeof(cp_gn_stats),
-         sizeof(cp_solve_opts), sizeof(cp_solve_result));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(cp_desc), sizeof(cp_gn_params), sizeof(cp_gn_stats),
+         sizeof(cp_solve_opts), sizeof(cp_solve_result), sizeof(cp_batch_problem), sizeof(cp_batch_result));
   return 0;
 }
 """
@@ -83,5 +83,5 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
         sizes = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
     mine = [ctypes.sizeof(c) for c in (api.cp_desc, api.cp_gn_params, api.cp_gn_stats, api.cp_solve_opts,
-                                       api.cp_solve_result)]
+                                       api.cp_solve_result, api.cp_batch_problem, api.cp_batch_result)]
     assert sizes == mine
