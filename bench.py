@@ -44,7 +44,29 @@ CG_MAX = 250
 MU = 2.0
 # GN iterations the FP64 path needs on this workload and seed (measured on a
 # GB300, recorded in the design doc); scales the CPU oracle's per-iteration time.
-GN_ITERS_FP64 = None
+GN_ITERS_FP64 = 51
+
+# DRAM traffic of the dominant kernels from one ncu capture each (profiles/pcg_kernel_collinear400.md,
+# profiles/mttkrp_tc_collinear400.md).  It is reported only while the kernel source still has the
+# SHA-1 it had when the counters were taken.
+PROFILED = {
+    "pcg": {"src": "paper_1910_12331_gb300/csrc/k_pcg.cu", "sha1": None,
+            "dram_bytes": 937728, "cg_iters": None},
+    "mttkrp": {"src": "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu", "sha1": None,
+               "dram_bytes": 287462912 + 5816832},
+}
+
+
+def profiled(key):
+    """The profiled record of a kernel if its source is unchanged since the capture, else None."""
+    import hashlib
+
+    rec = PROFILED[key]
+    try:
+        digest = hashlib.sha1(open(os.path.join(ROOT, rec["src"]), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec if rec["sha1"] == digest else None
 
 
 def lam_thresholds(A):
@@ -267,7 +289,8 @@ def run_kernel(which):
         lam_hi, lam_lo = lam_thresholds(p["init"])
         params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, prec="bf16x3")
         for _ in range(3):
-            api.cp_gn_step(h, X, [a.clone() for a in init], params, check=False)
+            _, st = api.cp_gn_step(h, X, [a.clone() for a in init], params, check=False)
+        print("pcg launch: %d CG iterations" % st["cg_iters"], flush=True)
     torch.cuda.synchronize()
     h.close()
 
@@ -413,17 +436,21 @@ def main():
     mt_per_launch = mt_phase / max(gn, 1)
     if mt_phase >= pcg_phase:
         ach = mt_bytes / mt_per_launch / 1e9
+        rec = profiled("mttkrp")
         roof = {"kernel": "all-mode MTTKRP phase (bf16x3 tcgen05 + prep/finalize; FP64 when refining)",
                 "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": None}
+                "traffic": rec["dram_bytes"] if rec else None}
     else:
         cg_it = max(last["cg_iters_total"], 1)
         rows = sum(X.shape)
         state_bytes = 4.0 * rows * R * 12  # FP32 CG vectors read/written per iteration
         ach = state_bytes / (pcg_phase / cg_it) / 1e9
-        roof = {"kernel": "persistent CP-CG kernel (per CG iteration)", "bound": "hbm", "achieved": ach,
-                "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
-                "us_per_cg_iteration": pcg_phase / cg_it * 1e6}
+        rec = profiled("pcg")
+        traffic = rec["dram_bytes"] / rec["cg_iters"] if rec and rec["cg_iters"] else None
+        roof = {"kernel": "persistent CP-CG kernel pcg_kernel<float> (per CG iteration)", "bound": "hbm",
+                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic,
+                "us_per_cg_iteration": pcg_phase / cg_it * 1e6,
+                "note": "latency-bound (three grid barriers per iteration); state L2-resident"}
     cpu = None
     if not args.no_cpu_baseline:
         gn64 = res64["iters"] + 1

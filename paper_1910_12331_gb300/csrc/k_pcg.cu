@@ -37,61 +37,131 @@ __device__ __forceinline__ double fmadd(double a, double b, double c) { return _
 // round trip serves a whole gather (at most 256 blocks).
 constexpr int kGatherPerLane = 8;
 
-// sum of v[0..nb), warp 0, fixed order; broadcast to the block
-__device__ __forceinline__ double gather_sum(const double* v, int nb, double* bcast) {
-    if (threadIdx.x < 32) {
+// Error-free sum s + e = a + b (Knuth two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+// (h, l) += (xh, xl) in double-float
+__device__ __forceinline__ void df_add(float& h, float& l, float xh, float xl) {
+    float s, e;
+    two_sum(h, xh, s, e);
+    h = s;
+    l += xl + e;
+}
+
+// Block partials of the CG dot products, one 8-byte slot per block: FP64 for
+// FP64 vectors, a double-float (hi, lo) pair of FP32 values for FP32 vectors,
+// so that the cross-block sums of the FP32 path run on the FP32 pipes (on
+// GB300 a chain of FP64 additions costs more than the sums are worth).
+template <typename T>
+struct Slot;
+template <>
+struct Slot<double> {
+    static __device__ __forceinline__ void put(double* p, double h, double l) { *p = h + l; }
+    static __device__ __forceinline__ float as_float(const double* v, int c) { return (float)__ldcg(&v[c]); }
+    // sum of v[c] over lane's c in [lane, nb) step 32, fixed order; then over the warp
+    static __device__ __forceinline__ double warp_total(const double* v, int nb, int lane, int c0, int c1) {
         double x[kGatherPerLane];
 #pragma unroll
         for (int u = 0; u < kGatherPerLane; ++u) {
-            const int c = (int)threadIdx.x + 32 * u;
-            x[u] = c < nb ? __ldcg(&v[c]) : 0.0;
+            const int c = lane + 32 * u;
+            x[u] = (c < nb && c >= c0 && c < c1) ? __ldcg(&v[c]) : 0.0;
         }
         double acc = 0.0;
 #pragma unroll
         for (int u = 0; u < kGatherPerLane; ++u) acc += x[u];
-        acc = warp_sum(acc);
-        if (threadIdx.x == 0) *bcast = acc;
+        return warp_sum(acc);
+    }
+};
+template <>
+struct Slot<float> {
+    static __device__ __forceinline__ float as_float(const double* v, int c) {
+        const float2 x = __ldcg(reinterpret_cast<const float2*>(v) + c);
+        return x.x + x.y;
+    }
+    static __device__ __forceinline__ void put(double* p, double h, double l) {
+        const float fh = (float)(h + l);
+        *reinterpret_cast<float2*>(p) = make_float2(fh, (float)((h - (double)fh) + l));
+    }
+    static __device__ __forceinline__ double warp_total(const double* v, int nb, int lane, int c0, int c1) {
+        float2 x[kGatherPerLane];
+#pragma unroll
+        for (int u = 0; u < kGatherPerLane; ++u) {
+            const int c = lane + 32 * u;
+            x[u] = (c < nb && c >= c0 && c < c1) ? __ldcg(reinterpret_cast<const float2*>(v) + c) : make_float2(0.f, 0.f);
+        }
+        float h = 0.f, l = 0.f;
+#pragma unroll
+        for (int u = 0; u < kGatherPerLane; ++u) df_add(h, l, x[u].x, x[u].y);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+            df_add(h, l, oh, ol);
+        }
+        return (double)h + (double)l;
+    }
+};
+
+// s = sum of the block partials v[0..nb) (warp 0, fixed order) and q = numer / s,
+// both broadcast to the block.  One lane divides: a division in every thread
+// would load GB300's slow FP64 pipe with hundreds of divisions per block.
+template <typename T>
+__device__ __forceinline__ double gather_sum(const double* v, int nb, double* bcast, double numer, double& q) {
+    if (threadIdx.x < 32) {
+        const double acc = Slot<T>::warp_total(v, nb, (int)threadIdx.x, 0, nb);
+        if (threadIdx.x == 0) {
+            bcast[0] = acc;
+            bcast[1] = numer / acc;
+        }
     }
     __syncthreads();
-    const double r = *bcast;
+    const double r = bcast[0];
+    q = bcast[1];
     __syncthreads();
     return r;
 }
 
 // One pass over the <R,Z> and |R|^2 partials: rz = sum of all rz partials,
-// rsum = sum over modes of sqrt(sum of that mode's |R|^2 partials).
+// rsum = sum over modes of sqrt(sum of that mode's |R|^2 partials), and
+// ratio = rz / rz_old (beta), formed by one lane.  The per-mode norms only
+// feed the CG stop test: FP32 square roots.
+template <typename T>
 __device__ __forceinline__ void gather_rz_rn(const double* rzp, const double* rnp, int nb, const int* mode_blk0, int N,
-                                             double* bcast, double& rz, double& rsum) {
+                                             double* bcast, double rz_old, double& rz, double& rsum, double& ratio) {
     if (threadIdx.x < 32) {
-        double xz[kGatherPerLane], xn[kGatherPerLane];
+        const int lane = (int)threadIdx.x;
+        // the |R|^2 partials are loaded once, with the rz partials in flight
+        float xn[kGatherPerLane];
 #pragma unroll
         for (int u = 0; u < kGatherPerLane; ++u) {
-            const int c = (int)threadIdx.x + 32 * u;
-            xz[u] = c < nb ? __ldcg(&rzp[c]) : 0.0;
-            xn[u] = c < nb ? __ldcg(&rnp[c]) : 0.0;
+            const int c = lane + 32 * u;
+            xn[u] = c < nb ? Slot<T>::as_float(rnp, c) : 0.f;
         }
-        double az = 0.0;
-#pragma unroll
-        for (int u = 0; u < kGatherPerLane; ++u) az += xz[u];
-        az = warp_sum(az);
-        double tot = 0.0;
+        const double az = Slot<T>::warp_total(rzp, nb, lane, 0, nb);
+        float tot = 0.f;
         for (int m = 0; m < N; ++m) {
-            double am = 0.0;
+            float am = 0.f;
 #pragma unroll
             for (int u = 0; u < kGatherPerLane; ++u) {
-                const int c = (int)threadIdx.x + 32 * u;
+                const int c = lane + 32 * u;
                 if (c >= mode_blk0[m] && c < mode_blk0[m + 1]) am += xn[u];
             }
-            tot += sqrt(warp_sum(am));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) am += __shfl_xor_sync(0xffffffffu, am, o);
+            tot += sqrtf(fmaxf(am, 0.f));
         }
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             bcast[0] = az;
-            bcast[1] = tot;
+            bcast[1] = (double)tot;
+            bcast[2] = rz_old != 0.0 ? az / rz_old : 0.0;
         }
     }
     __syncthreads();
     rz = bcast[0];
     rsum = bcast[1];
+    ratio = bcast[2];
     __syncthreads();
 }
 
@@ -102,12 +172,6 @@ __device__ __forceinline__ void gather_rz_rn(const double* rzp, const double* rn
 // (GB300's FP64 pipe runs at 1/64 of FP32: a reduction in FP64 by every
 // thread would cost more than the whole row computation.)  FP64 vectors:
 // plain FP64 products and sums, the cross-warp step again in one warp.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float z = s - a;
-    e = (a - (s - z)) + (b - z);
-}
-
 template <typename T>
 struct DotAcc;
 template <>
@@ -142,11 +206,11 @@ struct DotAcc<double> {
     __device__ __forceinline__ double value() const { return v; }
 };
 
-// (sum x*y, sum u*w) over the block's rows; both results valid in every thread.
+// (sum x*y, sum u*w) over the block's rows, as (hi, lo) pairs valid in thread 0.
 // red: at least 2 * (blockDim.x / 32) + 2 doubles.
 template <typename T>
 __device__ __forceinline__ void dot2_rows(const T* x, const T* y, const T* u, const T* w, int len, double* red,
-                                          double& r0, double& r1) {
+                                          double& r0h, double& r0l, double& r1h, double& r1l) {
     DotAcc<T> a, c;
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
         a.add_prod(x[e], y[e]);
@@ -155,23 +219,41 @@ __device__ __forceinline__ void dot2_rows(const T* x, const T* y, const T* u, co
     a.warp_reduce();
     if (u) c.warp_reduce();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) {
-        red[warp] = a.value();
-        red[32 + warp] = u ? c.value() : 0.0;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        double s0 = lane < nw ? red[lane] : 0.0, s1 = lane < nw ? red[32 + lane] : 0.0;
-        s0 = warp_sum(s0);
-        s1 = warp_sum(s1);
+    if constexpr (sizeof(T) == 4) {
+        float2* r2 = reinterpret_cast<float2*>(red);
         if (lane == 0) {
-            red[64] = s0;
-            red[65] = s1;
+            r2[warp] = make_float2(a.h, a.l);
+            r2[32 + warp] = u ? make_float2(c.h, c.l) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float2 p = lane < nw ? r2[lane] : make_float2(0.f, 0.f), q = lane < nw ? r2[32 + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ph = __shfl_xor_sync(0xffffffffu, p.x, o), pl = __shfl_xor_sync(0xffffffffu, p.y, o);
+                const float qh = __shfl_xor_sync(0xffffffffu, q.x, o), ql = __shfl_xor_sync(0xffffffffu, q.y, o);
+                df_add(p.x, p.y, ph, pl);
+                df_add(q.x, q.y, qh, ql);
+            }
+            r0h = p.x;
+            r0l = p.y;
+            r1h = q.x;
+            r1l = q.y;
+        }
+    } else {
+        if (lane == 0) {
+            red[warp] = a.value();
+            red[32 + warp] = u ? c.value() : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double s0 = lane < nw ? red[lane] : 0.0, s1 = lane < nw ? red[32 + lane] : 0.0;
+            r0h = warp_sum(s0);
+            r1h = warp_sum(s1);
+            r0l = r1l = 0.0;
         }
     }
     __syncthreads();
-    r0 = red[64];
-    r1 = red[65];
 }
 
 
@@ -403,18 +485,22 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
     rows_mm<T>(sR, Pm, nullptr, nullptr, (T)0, sZ, rows, R, Rp);
     __syncthreads();
     for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = sZ[e];
-    double rz_p, rn_p;
-    dot2_rows(sR, sZ, sR, sR, lenp, red, rz_p, rn_p);
-    if (threadIdx.x == 0) { part_rz[b] = rz_p; part_rn[b] = rn_p; }
+    double rz_h, rz_l, rn_h, rn_l;
+    dot2_rows(sR, sZ, sR, sR, lenp, red, rz_h, rz_l, rn_h, rn_l);
+    if (threadIdx.x == 0) {
+        Slot<T>::put(part_rz + b, rz_h, rz_l);
+        Slot<T>::put(part_rn + b, rn_h, rn_l);
+    }
     y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
 
     int it = 0;
     double rsum = 0.0, rz = 0.0, beta = 0.0;
     bool ok = grid_sync(a.bar, status, nb, lim);
-    auto reduce_r = [&](double& rz_out, double& rsum_out) {
-        gather_rz_rn(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_out, rsum_out);
+    double ratio = 0.0;
+    auto reduce_r = [&](double rz_old, double& rz_out, double& rsum_out) {
+        gather_rz_rn<T>(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_old, rz_out, rsum_out, ratio);
     };
-    if (ok) reduce_r(rz, rsum);
+    if (ok) reduce_r(0.0, rz, rsum);
     if (stationary) {
         ok = false;
         if (b == 0 && threadIdx.x == 0) a.stats->stopped = 1;
@@ -433,14 +519,20 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
                 const int c0 = a.mode_blk0[pp], c1 = a.mode_blk0[pp + 1];
                 T acc = it == 0 ? (T)0 : be * a.Yfull[e];
                 int c = c0;
-                for (; c + 4 <= c1; c += 4) {
-                    T v[4];
+                for (; c + 16 <= c1; c += 16) {  // sixteen partials in flight per round
+                    T v[16];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
+                    for (int u = 0; u < 16; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) acc += v[u];
+                    for (int u = 0; u < 16; ++u) acc += v[u];
                 }
-                for (; c < c1; ++c) acc += ldcg(&a.Zpart[(size_t)c * RR + q]);
+                if (c < c1) {
+                    T v[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) v[u] = c + u < c1 ? ldcg(&a.Zpart[(size_t)(c + u) * RR + q]) : (T)0;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) acc += v[u];
+                }
                 a.Yfull[e] = acc;
             }
         }
@@ -473,16 +565,16 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         // ---- Q = lam W + W Gamma^(n,n) + A T^(n)^T, partial <W,Q>
         rows_mm<T>(sW, Gm, sA, Tt, (T)a.lam, sQ, rows, R, Rp);
         __syncthreads();
-        double wq_p, unused;
-        dot2_rows<T>(sW, sQ, nullptr, nullptr, lenp, red, wq_p, unused);
-        if (threadIdx.x == 0) part_wq[b] = wq_p;
+        double wq_h, wq_l, unused_h, unused_l;
+        dot2_rows<T>(sW, sQ, nullptr, nullptr, lenp, red, wq_h, wq_l, unused_h, unused_l);
+        if (threadIdx.x == 0) Slot<T>::put(part_wq + b, wq_h, wq_l);
         PCG_TRACE(2);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         PCG_TRACE(3);
-        const double wq = gather_sum(part_wq, (int)nb, bcast);
+        double alpha;
+        const double wq = gather_sum<T>(part_wq, (int)nb, bcast, rz, alpha);
         if (!isfinite(wq)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (!(wq > 0.0)) { set_status(status, CP_ERR_BREAKDOWN); break; }
-        const double alpha = rz / wq;
         const T al = (T)alpha;
         for (int e = threadIdx.x; e < lenp; e += blockDim.x) {
             sV[e] = fmadd(al, sW[e], sV[e]);
@@ -491,18 +583,21 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         __syncthreads();
         rows_mm<T>(sR, Pm, nullptr, nullptr, (T)0, sZ, rows, R, Rp);
         __syncthreads();
-        dot2_rows(sR, sZ, sR, sR, lenp, red, rz_p, rn_p);
-        if (threadIdx.x == 0) { part_rz[b] = rz_p; part_rn[b] = rn_p; }
+        dot2_rows(sR, sZ, sR, sR, lenp, red, rz_h, rz_l, rn_h, rn_l);
+        if (threadIdx.x == 0) {
+            Slot<T>::put(part_rz + b, rz_h, rz_l);
+            Slot<T>::put(part_rn + b, rn_h, rn_l);
+        }
         y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
         PCG_TRACE(4);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         PCG_TRACE(5);
         double rz_new;
-        reduce_r(rz_new, rsum);
+        reduce_r(rz, rz_new, rsum);
         ++it;
         if (!(rsum > tol)) break;
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
-        beta = rz_new / rz;
+        beta = ratio;  // rz_new / rz, formed by one lane
         rz = rz_new;
         const T be = (T)beta;
         for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = fmadd(be, sW[e], sZ[e]);
