@@ -210,6 +210,84 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_kernel(Shape s, const
     }
 }
 
+// The same elimination in double-float (hi + lo FP32 pairs, about 2^-44
+// relative: error-free products by fmaf, Dekker; error-free sums, Knuth) for
+// the mixed path, whose CG runs in FP32: GB300 runs FP32 at 64 times its FP64
+// rate, and the elimination's R^3 updates per mode dominate the FP64 version.
+// The pivot reciprocal and its SPD test are formed in FP64 by one thread.
+__device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+__device__ __forceinline__ float2 df_sub2(float2 a, float2 b) {  // a - b
+    const float s = a.x - b.x;
+    const float z = s - a.x;
+    const float e = (a.x - (s - z)) + (-b.x - z);
+    const float l = e + (a.y - b.y);
+    const float h = s + l;
+    return make_float2(h, l - (h - s));
+}
+
+__global__ void __launch_bounds__(kPrecondThreads) precond_df_kernel(Shape s, const double* Gam, double lam,
+                                                                     double* Pinv, float* PinvF, float2* scratch,
+                                                                     DevStats* stats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_bad;
+    __shared__ float2 s_inv;
+    const int R = s.R, n = blockIdx.x;
+    float2* B = scratch ? scratch + (int64_t)n * (R * R + R) : reinterpret_cast<float2*>(smem_raw);
+    float2* f = B + R * R;
+    const double* Gnn = Gam + ((int64_t)n * s.N + n) * R * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_bad = 0;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const double v = Gnn[e] + ((e / R) == (e % R) ? lam : 0.0);
+        const float h = (float)v;
+        B[e] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+    for (int j = 0; j < R; ++j) {
+        if (threadIdx.x == 0) {
+            const float2 pv = B[j * R + j];
+            double p = (double)pv.x + (double)pv.y;
+            if (!(p > 0.0)) {
+                s_bad = 1;
+                p = 1.0;
+            }
+            const double iv = 1.0 / p;
+            const float h = (float)iv;
+            s_inv = make_float2(h, (float)(iv - (double)h));
+        }
+        for (int i = threadIdx.x; i < R; i += blockDim.x) f[i] = B[i * R + j];
+        __syncthreads();
+        const float2 inv = s_inv;
+        for (int k = threadIdx.x; k < R; k += blockDim.x) B[j * R + k] = k == j ? inv : df_mul2(B[j * R + k], inv);
+        __syncthreads();
+        for (int i = warp; i < R; i += nw) {
+            if (i == j) continue;
+            const float2 fi = f[i];
+            for (int k = lane; k < R; k += 32) {
+                const float2 t = df_mul2(fi, k == j ? inv : B[j * R + k]);
+                B[i * R + k] = k == j ? make_float2(-t.x, -t.y) : df_sub2(B[i * R + k], t);
+            }
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
+        if (threadIdx.x == 0) set_status(&stats->status, CP_ERR_NOT_SPD);
+        return;
+    }
+    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
+        const float2 v = B[q];
+        if (Pinv) Pinv[(int64_t)n * R * R + q] = (double)v.x + (double)v.y;
+        if (PinvF) PinvF[(int64_t)n * R * R + q] = v.x + v.y;
+    }
+}
+
 void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv, float* PinvF, double* scratch,
                     DevStats* stats, cudaStream_t st, bool fp32) {
     static bool attr_set[64] = {};
@@ -217,13 +295,21 @@ void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv,
     cudaGetDevice(&dev);
     if (dev >= 64 || !attr_set[dev]) {
         cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(precond_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (dev < 64) attr_set[dev] = true;
     }
-    // The elimination always runs in FP64: the blocks Gamma^(n,n) + lam I of a
-    // collinear problem at small lam are too ill-conditioned for an FP32
-    // elimination.  The FP32 CG of the mixed path gets the FP64 inverse rounded once.
+    // The blocks Gamma^(n,n) + lam I of a collinear problem at small lam are
+    // too ill-conditioned for an FP32 elimination: FP64 for the plain path,
+    // double-float for the mixed path (whose FP32 CG gets the inverse rounded once).
     const size_t bytes = ((size_t)s.R * s.R + s.R) * sizeof(double);
-    float* pf = fp32 ? PinvF : nullptr;
+    if (fp32) {
+        if (bytes <= 200 * 1024)
+            precond_df_kernel<<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, PinvF, nullptr, stats);
+        else
+            precond_df_kernel<<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, Pinv, PinvF, (float2*)scratch, stats);
+        return;
+    }
+    float* pf = nullptr;
     if (bytes <= 200 * 1024)
         precond_kernel<<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, pf, nullptr, stats);
     else

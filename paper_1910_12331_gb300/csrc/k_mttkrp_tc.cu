@@ -56,8 +56,14 @@ namespace cpgn {
 
 namespace tc {
 
-constexpr int kThreads = 384;            // 12 warps
-constexpr int kWork = 256;               // worker threads (two warps per TMEM lane quadrant)
+#ifndef CPGN_TC_WQ
+#define CPGN_TC_WQ 2
+#endif
+constexpr int kWQ = CPGN_TC_WQ;          // worker warps per TMEM lane quadrant
+constexpr int kWork = 128 * kWQ;         // worker threads
+constexpr int kThreads = 128 + kWork;    // four role warps + the workers
+constexpr int kWCols = 64 / kWQ;         // rank columns of D_Y / D_Z per worker warp
+constexpr int kBRanks = 64 / (kWork / 64);  // B_Z rank columns per builder thread
 constexpr int kStages = 4;               // X chunk tiles in flight
 constexpr int kBI = 128;                 // rows of an i-block (M of GEMM-Y, K of GEMM-Z)
 constexpr int kKC = 64;                  // columns of a chunk
@@ -535,10 +541,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         //   D_Y drain: thread = TMEM lane (row i) and 32 rank columns (warp half).
         const int wk = warp - 4;
         const int q = warp & 3;                  // TMEM lane quadrant of this warp
-        const int cb = 32 * (wk >> 2);           // first rank column of this warp's D_Y / D_Z share
+        const int cb = kWCols * (wk >> 2);       // first rank column of this warp's D_Y / D_Z share
         const int row = q * 32 + lane;           // lane of D_Y (row i) and of D_Z (row rho)
-        const int et = wk * 32 + lane;           // 0..255
-        const int i0 = 2 * (et & 63), rq = 16 * (et >> 6);  // B_Z rows and first rank column
+        const int et = wk * 32 + lane;           // 0 .. kWork - 1
+        const int i0 = 2 * (et & 63), rq = kBRanks * (et >> 6);  // B_Z rows and first rank column
         auto grp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
             mbar_wait(bar, parity, abort_s, p.status);
             named_sync(2, kWork);
@@ -554,8 +560,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int x = 0; x < 8; ++x) rowbase[x] = sub + ((((ii >> 3) ^ x) & 7) << 4) + (ii & 7) * 2;
         }
-        float b0[16], b1[16];          // A^(1) rows i0, i0 + 1 (columns rq ..) of the block being built
-        float a1r[32], m1acc[32];      // A^(1) row `row` (columns cb ..) and the M^(1) partial
+        float b0[kBRanks], b1[kBRanks];  // A^(1) rows i0, i0 + 1 (columns rq ..) of the block being built
+        float a1r[kWCols], m1acc[kWCols];  // A^(1) row `row` (columns cb ..) and the M^(1) partial
         int bb = -1, pb = -1;
         // B_Z of step `st` (relative index tb) into buffer tb & 1
         auto build = [&](const StepId& st, int64_t tb) -> bool {
@@ -563,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bb = st.b;
                 const int64_t g0 = (int64_t)st.b * kBI + i0;
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
+                for (int r = 0; r < kBRanks; ++r) {
                     b0[r] = g0 < p.s1 ? p.A1f[g0 * kRT + rq + r] : 0.0f;
                     b1[r] = g0 + 1 < p.s1 ? p.A1f[(g0 + 1) * kRT + rq + r] : 0.0f;
                 }
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t boff = db * kBZBytes;
             const float4* wv = reinterpret_cast<const float4*>(&C.wring[ws][rq]);
 #pragma unroll
-            for (int r4 = 0; r4 < 16; r4 += 4) {
+            for (int r4 = 0; r4 < kBRanks; r4 += 4) {
                 const float4 w4 = wv[r4 >> 2];
                 const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
@@ -608,10 +614,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     pb = sp.b;
                     const int64_t gi = (int64_t)sp.b * kBI + row;
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) a1r[r] = gi < p.s1 ? p.A1f[gi * kRT + cb + r] : 0.0f;
+                    for (int r = 0; r < kWCols; ++r) a1r[r] = gi < p.s1 ? p.A1f[gi * kRT + cb + r] : 0.0f;
                 }
 #pragma unroll
-                for (int r = 0; r < 32; ++r) m1acc[r] = 0.0f;
+                for (int r = 0; r < kWCols; ++r) m1acc[r] = 0.0f;
             }
             const int db = (int)(tt & 1);
             const int ws = (int)(tt % kWRing);
@@ -620,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t ta = t_dy0 + db * 128 + cb + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-            for (int j = 0; j < 32; j += 16) {
+            for (int j = 0; j < kWCols; j += 16) {
                 uint32_t ra[16], rb[16];
                 tmem_ld16(ta + j, ra);
                 tmem_ld16(ta + 64 + j, rb);
@@ -660,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (rl && slot_ok) {
                     float* py = p.P_Y1 + (slot * kBI + row) * kRT + cb;
 #pragma unroll
-                    for (int r = 0; r < 32; r += 4)
+                    for (int r = 0; r < kWCols; r += 4)
                         *reinterpret_cast<float4*>(py + r) =
                             make_float4(m1acc[r], m1acc[r + 1], m1acc[r + 2], m1acc[r + 3]);
                 }
@@ -672,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float* pz = p.P_Z + ((slot * kGroup + cc) * kRT + (row >> 1)) * kKC + cb;
                     const uint32_t tz = t_dz0 + cc * 128 + cb + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 16) {
+                    for (int j = 0; j < kWCols; j += 16) {
                         uint32_t za[16], zb[16];
                         tmem_ld16(tz + j, za);
                         tmem_ld16(tz + 64 + j, zb);
@@ -805,7 +811,7 @@ __global__ void prep_kernel(Shape s, Ptrs<const double> A, int r0, int64_t pitch
 // output per thread.  Both list the slots of their i-block (chunk's group) in
 // increasing order, kFinList at a time (the slot records are staged in shared
 // memory by all threads, then compacted by one warp), and sum the listed
-// partials with eight independent loads in flight.  Middle modes: block = 8
+// partials with sixteen independent loads in flight.  Middle modes: block = 8
 // rows x 32 threads, summing the per-step column sums c_m times the other
 // middle factors.
 constexpr int kFinRows = 8;
@@ -852,12 +858,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
         double acc = 0.0;
         for (int e0 = 0; e0 < nslots; e0 += kFinList) {
             const int cnt = fin_list(p, e0, min(nslots, e0 + kFinList), 1, g, list, stage);
-            for (int j = 0; j < cnt; j += 8) {
-                float v[8];
+            for (int j = 0; j < cnt; j += 16) {
+                float v[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = j + u < cnt ? src[(int64_t)list[j + u] * sstride] : 0.0f;
+                for (int u = 0; u < 16; ++u) v[u] = j + u < cnt ? src[(int64_t)list[j + u] * sstride] : 0.0f;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc += v[u];
+                for (int u = 0; u < 16; ++u) acc += v[u];
             }
             __syncthreads();
         }
@@ -876,14 +882,14 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
             const int cnt = fin_list(p, e0, min(nslots, e0 + kFinList), 0, b, list, stage);
             if (i < sn) {
                 const float* src = p.P_Y1 + (i % kBI) * kRT + c0;
-                for (int j = 0; j < cnt; j += 8) {
-                    float2 v[8];
+                for (int j = 0; j < cnt; j += 16) {
+                    float2 v[16];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
+                    for (int u = 0; u < 16; ++u)
                         v[u] = j + u < cnt ? *reinterpret_cast<const float2*>(src + (int64_t)list[j + u] * kBI * kRT)
                                            : make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < 16; ++u) {
                         acc0 += v[u].x;
                         acc1 += v[u].y;
                     }
