@@ -50,10 +50,10 @@ GN_ITERS_FP64 = 51
 # profiles/mttkrp_tc_collinear400.md).  It is reported only while the kernel source still has the
 # SHA-1 it had when the counters were taken.
 PROFILED = {
-    "pcg": {"src": "paper_1910_12331_gb300/csrc/k_pcg.cu", "sha1": None,
-            "dram_bytes": 937728, "cg_iters": None},
-    "mttkrp": {"src": "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu", "sha1": None,
-               "dram_bytes": 287462912 + 5816832},
+    "pcg": {"src": "paper_1910_12331_gb300/csrc/k_pcg.cu", "sha1": "9ff0f02333ddf657166801babc0cf8515c760354",
+            "dram_bytes": 926720, "cg_iters": 4},
+    "mttkrp": {"src": "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu", "sha1": "e7d91b723a2d6ee06efe4ef33a27dcd357662807",
+               "dram_bytes": 287492352 + 5866496},
 }
 
 

@@ -177,11 +177,11 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         CP_TRY(grow(h->stats, sizeof(DevStats)));
         CP_TRY(tc_mttkrp_all(h->split, d, s, X, A, M, &((DevStats*)h->stats.p)->status, h->stream));
     } else if (prec == CP_PREC_RESIDUAL) {
-        // MTTKRP of the residual tensor E = X - [[A]] (double-float), as bf16 planes
+        // MTTKRP of the residual tensor E = X - [[A]] (extended precision), as bf16 planes
         CP_TRY(grow(h->stats, sizeof(DevStats)));
         CP_TRY(grow(h->resid_planes, (size_t)PlaneTiling::of(s).total() * 2));
         DevStats* ds = (DevStats*)h->stats.p;
-        CP_TRY(grow(h->Adf, (size_t)s.roff[s.N] * s.R * 2 * sizeof(float)));
+        CP_TRY(grow(h->Adf, resid_scratch_bytes(s)));
         launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, h->stream);
         CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
         h->launches += 2 + (s.R + 63) / 64 * 3;

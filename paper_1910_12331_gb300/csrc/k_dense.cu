@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_kernel(Shape s, const
 // relative: error-free products by fmaf, Dekker; error-free sums, Knuth) for
 // the mixed path, whose CG runs in FP32: GB300 runs FP32 at 64 times its FP64
 // rate, and the elimination's R^3 updates per mode dominate the FP64 version.
-// The pivot reciprocal and its SPD test are formed in FP64 by one thread.
+// The pivot reciprocal (double-float Newton step) and its SPD test are formed
+// by one thread, without FP64 instructions.
 __device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
     const float p = a.x * b.x;
     float e = fmaf(a.x, b.x, -p);
@@ -252,15 +253,19 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_df_kernel(Shape s, co
     __syncthreads();
     for (int j = 0; j < R; ++j) {
         if (threadIdx.x == 0) {
-            const float2 pv = B[j * R + j];
-            double p = (double)pv.x + (double)pv.y;
-            if (!(p > 0.0)) {
+            // 1/p in double-float: FP32 reciprocal, then one Newton step with an
+            // error-free residual r = 1 - p h (no FP64 instruction on this serial path)
+            float2 pv = B[j * R + j];
+            if (!(pv.x > 0.f)) {
                 s_bad = 1;
-                p = 1.0;
+                pv = make_float2(1.f, 0.f);
             }
-            const double iv = 1.0 / p;
-            const float h = (float)iv;
-            s_inv = make_float2(h, (float)(iv - (double)h));
+            const float h = 1.0f / pv.x;
+            const float2 ph = df_mul2(pv, make_float2(h, 0.f));
+            const float r = (1.0f - ph.x) - ph.y;
+            const float c = h * r;
+            const float ih = h + c;
+            s_inv = make_float2(ih, c - (ih - h));
         }
         for (int i = threadIdx.x; i < R; i += blockDim.x) f[i] = B[i * R + j];
         __syncthreads();

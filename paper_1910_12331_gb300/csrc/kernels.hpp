@@ -80,9 +80,11 @@ void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, 
                        Ptrs<double> Q, double* Y, cudaStream_t st);
 
 // ---- residual tensor in double-float, as bf16 planes in PlaneTiling layout (k_resid.cu)
-// Adf_scratch: (sum_n s_n) * R float2 (double-float copy of the factors).
+// scratch: resid_scratch_bytes(s) bytes (double-float copy of the factors and
+// block maxima of the first and last factor).
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                        void* Adf_scratch, DevStats* stats, cudaStream_t st);
+                        void* scratch, DevStats* stats, cudaStream_t st);
+size_t resid_scratch_bytes(const Shape& s);
 
 // ---- residual (k_residual.cu) ------------------------------------------------------
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,
