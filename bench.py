@@ -7,10 +7,12 @@ column collinearity 0.9 plus 1e-6 relative Gaussian noise, decomposed at
 rank R = 50 from a seeded N(0,1) starting point.  One step = one complete
 CP-GN solve (Algorithm 1 with CP-CG, Algorithm 2) from that starting point to
 relative stationarity sum||G||/sum||M|| <= 1e-8 with an FP64 gradient: the
-mixed path runs the tcgen05 bf16x3 MTTKRP with FP32 CG vectors and FP64
-scalars, and switches the MTTKRP to FP64 for the final iterations.  The
-value is the time to target (seconds, lower is better); the same solve on the
-plain FP64 GPU path and the all-mode MTTKRP throughput are reported beside it.
+mixed path forms every gradient as -E_(n) P^(n) from the residual tensor
+E = X - [[A]] (reconstruction by error-free bf16 slice products on the
+tcgen05 tensor cores, then the tcgen05 bf16x3 MTTKRP of E) and runs CP-CG
+with FP32 vectors and FP64 scalars.  The value is the time to target
+(seconds, lower is better); the same solve on the plain FP64 GPU path and the
+all-mode MTTKRP throughput are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank solves its own replica; rank 0 prints one
@@ -47,14 +49,17 @@ MU = 2.0
 GN_ITERS_FP64 = 51
 
 # DRAM traffic of the dominant kernels from one ncu capture each (profiles/pcg_kernel_collinear400.md,
-# profiles/mttkrp_tc_collinear400.md).  It is reported only while the kernel source still has the
-# SHA-1 it had when the counters were taken.
+# profiles/resid_gradient_collinear400.md).  It is reported only while every source of the record
+# still has the SHA-1 it had when the counters were taken.
 PROFILED = {
-    "pcg": {"src": "paper_1910_12331_gb300/csrc/k_pcg.cu", "sha1": "9ff0f02333ddf657166801babc0cf8515c760354",
+    "pcg": {"src": {"paper_1910_12331_gb300/csrc/k_pcg.cu": "9ff0f02333ddf657166801babc0cf8515c760354"},
             "dram_bytes": 926720, "cg_iters": 4},
-    "mttkrp": {"src": "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu", "sha1": "e7d91b723a2d6ee06efe4ef33a27dcd357662807",
-               "dram_bytes": 287492352 + 5866496},
+    "gradient": {"src": {"paper_1910_12331_gb300/csrc/k_resid_tc.cu": None,
+                         "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu": None},
+                 "dram_bytes": None},
 }
+# The mixed path of the timed solve: residual-form gradient every iteration, FP32 CG vectors.
+MIXED = {"prec": "residual", "cg_fp32": True}
 
 
 def profiled(key):
@@ -62,11 +67,14 @@ def profiled(key):
     import hashlib
 
     rec = PROFILED[key]
-    try:
-        digest = hashlib.sha1(open(os.path.join(ROOT, rec["src"]), "rb").read()).hexdigest()
-    except OSError:
-        return None
-    return rec if rec["sha1"] == digest else None
+    for src, sha in rec["src"].items():
+        try:
+            digest = hashlib.sha1(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        except OSError:
+            return None
+        if sha != digest:
+            return None
+    return rec
 
 
 def lam_thresholds(A):
@@ -270,8 +278,9 @@ def batched_timing(dev, count=512):
 
 def run_kernel(which):
     """A few launches of one kernel on the workload (for ncu captures): the
-    first mixed-path GN step (pcg: one persistent CP-CG launch per step) or
-    the bf16x3 all-mode MTTKRP (mttkrp)."""
+    first mixed-path GN step (pcg: one persistent CP-CG launch per step), the
+    bf16x3 all-mode MTTKRP (mttkrp), or the residual-form gradient (resid:
+    tensor-core reconstruction of E, then the MTTKRP of E)."""
     import torch
 
     from paper_1910_12331_gb300 import api, datagen
@@ -285,9 +294,12 @@ def run_kernel(which):
         M = [torch.empty_like(a) for a in init]
         for _ in range(3):
             api.cp_mttkrp_all(h, X, init, M, prec="bf16x3")
+    elif which == "resid":
+        for _ in range(3):
+            api.cp_gradient(h, X, init, prec="residual")
     else:
         lam_hi, lam_lo = lam_thresholds(p["init"])
-        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, prec="bf16x3")
+        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, **MIXED)
         for _ in range(3):
             _, st = api.cp_gn_step(h, X, [a.clone() for a in init], params, check=False)
         print("pcg launch: %d CG iterations" % st["cg_iters"], flush=True)
@@ -302,7 +314,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["pcg", "mttkrp"], default=None,
+    ap.add_argument("--kernel", choices=["pcg", "mttkrp", "resid"], default=None,
                     help="profiling aid: only run a few launches of one kernel on the workload, print nothing")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -335,13 +347,13 @@ def main():
     total = int(np.prod(X.shape))
     R = init[0].shape[1]
 
-    def solve(prec, refine=3e-5):
+    def solve(mode):
         for a, b in zip(A, init):
             a.copy_(b)
-        h.bump_version(X)  # the split planes are rebuilt inside the timed step
-        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, prec=prec)
-        opts = api.solve_opts(max_iters=MAX_GN, target_stationarity=TARGET_STAT,
-                              refine_below=refine if prec != "fp64" else 0.0)
+        h.bump_version(X)  # any cached split of X is rebuilt inside the timed step
+        kw = MIXED if mode == "mixed" else {"prec": "fp64"}
+        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, **kw)
+        opts = api.solve_opts(max_iters=MAX_GN, target_stationarity=TARGET_STAT)
         _, res = api.cp_gn_solve(h, X, A, params, opts)
         return res
 
@@ -352,7 +364,7 @@ def main():
 
     # ---- warm-up and timed steps (mixed path)
     for _ in range(args.warmup):
-        solve("bf16x3")
+        solve("mixed")
     results = []
     barrier()
     stream = torch.cuda.current_stream(dev)
@@ -360,7 +372,7 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            results.append(solve("bf16x3"))
+            results.append(solve("mixed"))
         e1.record(stream)
         barrier()
     t_total = e0.elapsed_time(e1) / 1e3
@@ -410,8 +422,8 @@ def main():
         Xd = X_host.to(dev, non_blocking=True)
         Ad = [a.to(dev, non_blocking=True) for a in init_host]
         h.bump_version(Xd)
-        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, prec="bf16x3")
-        opts = api.solve_opts(max_iters=MAX_GN, target_stationarity=TARGET_STAT, refine_below=3e-5)
+        params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, **MIXED)
+        opts = api.solve_opts(max_iters=MAX_GN, target_stationarity=TARGET_STAT)
         api.cp_gn_solve(h, Xd, Ad, params, opts)
         out = [a.cpu() for a in Ad]
     torch.cuda.synchronize()
@@ -435,9 +447,12 @@ def main():
     gn = last["iters"] + (1 if last["converged"] else 0)
     mt_per_launch = mt_phase / max(gn, 1)
     if mt_phase >= pcg_phase:
-        ach = mt_bytes / mt_per_launch / 1e9
-        rec = profiled("mttkrp")
-        roof = {"kernel": "all-mode MTTKRP phase (bf16x3 tcgen05 + prep/finalize; FP64 when refining)",
+        # residual-form gradient per GN iteration: the reconstruction reads X (4 B) and writes the
+        # bf16 hi/lo planes of E (4 B), the MTTKRP of E reads the planes (4 B) -- 12 B per element
+        grad_bytes = 12.0 * total
+        ach = grad_bytes / mt_per_launch / 1e9
+        rec = profiled("gradient")
+        roof = {"kernel": "residual-form gradient phase (tcgen05 reconstruction of E + tcgen05 MTTKRP of E)",
                 "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                 "traffic": rec["dram_bytes"] if rec else None}
     else:
@@ -464,10 +479,10 @@ def main():
         "dtype": "bf16x3/f32/f64", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
                    "target": f"sum||G||/sum||M|| <= {TARGET_STAT} with an FP64 gradient",
-                   "step": "one full CP-GN solve incl. the bf16 split of X",
+                   "step": "one full CP-GN solve (residual-form gradient every iteration, FP32 CG vectors)",
                    "l2": "inputs larger than L2 (X 256 MB, split planes 256 MB)",
                    "parallelism": f"replicas x{ws}"},
-        "converged": converged, "gn_iters": last["iters"], "gn_iters_fp64_mttkrp": last["iters_refined"],
+        "converged": converged, "gn_iters": last["iters"], "gradient": "residual form -E_(n) P^(n) every iteration",
         "cg_iters": last["cg_iters_total"], "stationarity": last["stationarity"],
         "phase_ms": {"mttkrp": last["mttkrp_ms"], "pcg": last["pcg_ms"], "device": last["device_ms"]},
         "mttkrp": {"tflops": mt_flops / t_mt / 1e12, "us": t_mt * 1e6, "gbs": mt_bytes / t_mt / 1e9,

@@ -274,7 +274,7 @@ def gn_params(lam, lam_lo, lam_hi, mu=2.0, eps_cg=1e-3, cg_max_iter=250, prec="f
     p.lam, p.lam_lo, p.lam_hi, p.mu = float(lam), float(lam_lo), float(lam_hi), float(mu)
     p.lam_dir, p.lam_fixed = int(lam_dir), int(bool(lam_fixed))
     p.prec = PREC[prec]
-    p.cg_fp32 = int(prec == "bf16x3") if cg_fp32 is None else int(bool(cg_fp32))
+    p.cg_fp32 = int(prec in ("bf16x3", "residual")) if cg_fp32 is None else int(bool(cg_fp32))
     p.want_residual = int(bool(want_residual))
     p.stop_stationarity = float(stop_stationarity)
     p.spin_limit = int(spin_limit)

@@ -181,10 +181,17 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         CP_TRY(grow(h->stats, sizeof(DevStats)));
         CP_TRY(grow(h->resid_planes, (size_t)PlaneTiling::of(s).total() * 2));
         DevStats* ds = (DevStats*)h->stats.p;
-        CP_TRY(grow(h->Adf, resid_scratch_bytes(s)));
-        launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, h->stream);
+        if (resid_tc_supported(s)) {  // reconstruction on the tensor cores (R <= 64)
+            CP_TRY(grow(h->Adf, resid_tc_scratch_bytes(s)));
+            h->launches += launch_resid_split_tc(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, &ds->status,
+                                                 h->stream);
+        } else {
+            CP_TRY(grow(h->Adf, resid_scratch_bytes(s)));
+            launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, h->stream);
+            h->launches += 2;
+        }
         CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
-        h->launches += 2 + (s.R + 63) / 64 * 3;
+        h->launches += (s.R + 63) / 64 * 3;
     } else {
         return CP_ERR_ARG;
     }

@@ -51,10 +51,13 @@
 
 #include "kernels.hpp"
 #include "tc.hpp"
+#include "tc_ptx.cuh"
 
 namespace cpgn {
 
 namespace tc {
+
+using namespace tcx;
 
 #ifndef CPGN_TC_WQ
 #define CPGN_TC_WQ 2
@@ -79,7 +82,6 @@ constexpr uint32_t kPayload = kStages * kTile + kBYBytes + 2 * kBZBytes;  // 102
 constexpr int kWRing = 6;                // w_m rows in flight (shared by builders and epilogue)
 constexpr int kWAhead = 3;               // the producer loads w_m this many steps ahead of its X loads
 constexpr uint32_t kTmemCols = 512;      // D_Y x2 (128 columns each) + D_Z x2 chunks (128 each)
-constexpr long long kWaitLimit = 1LL << 26;
 #ifndef CPGN_TC_PREFETCH
 #define CPGN_TC_PREFETCH 0
 #endif
@@ -143,109 +145,6 @@ static_assert(kDynSmem <= 227 * 1024, "shared memory above the per-block limit")
     } while (0)
 #endif
 
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait on an mbarrier phase.  Returns false (and raises the CTA abort
-// flag and the global status) when the limit expires or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-    for (long long i = 0; i < kWaitLimit; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (i > 256) __nanosleep(32);
-    }
-    *abort_flag = 1;
-    atomicCAS(status, 0, CP_ERR_TIMEOUT);
-    return false;
-}
-// Bounded wait that ignores the abort flag: used to drain copies and MMAs that
-// were issued (they complete on their own) before shared memory and TMEM go.
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, int* status) {
-    for (long long i = 0; i < kWaitLimit; ++i) {
-        if (mbar_try(bar, parity)) return;
-        if (i > 256) __nanosleep(32);
-    }
-    atomicCAS(status, 0, CP_ERR_TIMEOUT);
-}
-// Linear bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// Fire-and-forget L2 prefetch of a linear range (no shared memory, no completion).
-__device__ __forceinline__ void bulk_prefetch(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(map), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-// 16 consecutive FP32 columns of this thread's TMEM lane (completion via tmem_wait_ld)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, 128-byte swizzle, version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-// Instruction descriptor: D F32, A/B BF16, M = 128, the given N; A and B K- or MN-major.
-__device__ __forceinline__ uint32_t idesc_bf16(int n, bool a_mn, bool b_mn) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
 // Sum 16 per-lane values over the 32 lanes of a warp.  Afterwards lane l holds
 // in v[0] the warp total of column butterfly16_col(l) (lanes l and l^1 agree).
 __device__ __forceinline__ void butterfly16(float* v, int lane) {
@@ -264,11 +163,6 @@ __device__ __forceinline__ void butterfly16(float* v, int lane) {
 __device__ __forceinline__ int butterfly16_col(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
-
-__device__ __forceinline__ void named_sync(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-__host__ __device__ __forceinline__ int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 
 // Step (b, g, m) of linear index t = (b * ngr + g) * mid + m.  Decoded once
 // per role; the loops then advance it without divisions.
@@ -628,9 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int j = 0; j < kWCols; j += 16) {
                 uint32_t ra[16], rb[16];
-                tmem_ld16(ta + j, ra);
-                tmem_ld16(ta + 64 + j, rb);
-                tmem_wait_ld();
+                tmem_ld16x2_wait(ta + j, ta + 64 + j, ra, rb);
                 float v[16];
 #pragma unroll
                 for (int u = 0; u < 16; u += 4) {
@@ -680,9 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < kWCols; j += 16) {
                         uint32_t za[16], zb[16];
-                        tmem_ld16(tz + j, za);
-                        tmem_ld16(tz + 64 + j, zb);
-                        tmem_wait_ld();
+                        tmem_ld16x2_wait(tz + j, tz + 64 + j, za, zb);
                         float z[16];
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
@@ -944,24 +834,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
 }
 
 // ------------------------------------------------------------ host side
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)f;
-        cudaGetLastError();
-    });
-    return fn;
-}
+static EncodeTiledFn encode_fn() { return tc_encode_fn(); }
 
 
 #ifdef CPGN_TC_TRACE

@@ -1,0 +1,645 @@
+// k_resid_tc.cu -- the residual tensor E = X - [[A^(1), ..., A^(N)]] with the
+// reconstruction on tcgen05 tensor cores (sm_103a), written as bf16 high/low
+// planes (PlaneTiling) for the tensor-core MTTKRP, with sum E^2 and sum X^2.
+// Used for R <= 64; larger ranks take the CUDA-core kernel of k_resid.cu.
+//
+// Why: the gradient G^(n) = -E_(n) P^(n) of Eq. (2.3) needs E to far better
+// than FP32's 2^-24 when E is small; see k_resid.cu.
+//
+// Arithmetic: error-free splitting of a matrix product into slice products on
+// fixed grids (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012), with bf16 slices and the tensor
+// core's FP32 accumulation:
+//   For a slice m of the middle modes, [[A]][i, m, k] = sum_r u_ir v_kr with
+//   u_ir = a^(1)_ir w_m[r] (w_m: the product of the middle factors' rows) and
+//   v_kr = a^(N)_kr.  Row i of u is scaled by the power of two sigma_i >=
+//   max_r |u_ir|, row k of v by tau_k >= max_r |v_kr|, and every scaled value
+//   is cut into six pieces on the grids 2^-8, 2^-16, ..., 2^-48 (round to
+//   nearest on each grid; the remainder goes on to the next).  A piece on grid
+//   2^-8s is an integer of at most 8 significant bits times 2^-8s, exact in
+//   bf16.  The product of pieces s and t is an integer of at most 16 bits on
+//   the grid 2^-8(s+t); all products of one level L = s + t summed over r < 64
+//   stay below 2^23 units of that grid, so the FP32 accumulation of a level is
+//   exact.  Levels L = 2..7 (21 piece pairs) go to six TMEM accumulators; the
+//   pairs with s + t >= 8 and the remainders beyond the sixth piece are below
+//   2^-46 R sigma_i tau_k.  The epilogue adds the levels in double-float,
+//   subtracts from x (scaled by the same powers of two) and scales back.
+//
+// Kernel: persistent, one CTA per SM, 12 warps.  A run is (i-block b of 128
+// rows, slice m); a step is one 32-column chunk c of a run.
+//   warp 0      producer: the step's pieces of v (6 x 4 KB, one bulk copy,
+//               precomputed once per call, pre-swizzled) into one of two slots.
+//   warp 1      TMEM allocator and MMA issuer (one thread): per K-step, six
+//               MMAs (M = 128, N = 192, one per piece of u) into the six level
+//               accumulators of one of two TMEM buffers (6 levels x 32 columns).
+//   warps 4-11  workers: build the pieces of u for a run (6 x 16 KB), then per
+//               step drain the six levels of D (lane = row i, 16 columns per
+//               warp), form E and write its planes.
+// Every mbarrier wait is bounded (CP_ERR_TIMEOUT, CTA abort flag, drain).
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "kernels.hpp"
+#include "tc.hpp"
+#include "tc_ptx.cuh"
+
+namespace cpgn {
+
+namespace rtc {
+
+using namespace tcx;
+
+constexpr int kSlices = 6;                         // pieces per value
+constexpr int kLevels = 6;                         // L = 2 .. 7
+constexpr int kBI = 128;                           // rows i of a run (M)
+constexpr int kKC = 32;                            // columns k of a step (N)
+constexpr int kRT = 64;                            // rank columns (K), zero padded
+constexpr uint32_t kASlice = kBI * 128;            // 128 rows x 64 bf16, K-major, 128-byte swizzle
+constexpr uint32_t kBSlice = kKC * 128;            // 32 rows x 64 bf16
+constexpr uint32_t kABytes = kSlices * kASlice;    // 96 KB
+constexpr uint32_t kBBytes = kSlices * kBSlice;    // 24 KB per step
+constexpr uint32_t kXTile = kBI * kKC * 4;         // 128 rows x 32 FP32 of X, 128-byte swizzle (TMA)
+// A step's B slot: five zero blocks, then the six pieces of v (32 rows each).
+// For piece s of u, the N = 192 window starting at block 6 - s holds piece
+// t = L - s of v in block L - 2 (zero where t < 1), so one MMA per (s, K-step)
+// accumulates every level L = 2..7 into its own 32 TMEM columns.
+constexpr uint32_t kBSlot = (2 * kSlices - 1) * kBSlice;  // 44 KB
+constexpr uint32_t kPayload = kABytes + 2 * kBSlot + 2 * kXTile;
+constexpr int kWork = 256;
+constexpr int kThreads = 128 + kWork;
+constexpr uint32_t kTmemCols = 512;                // 2 buffers x 6 levels x 32 columns
+constexpr uint32_t kDBuf = kLevels * kKC;          // TMEM columns of one buffer
+
+struct Params {
+    int N, R;
+    int64_t s1, mid, sN;
+    int nib, nck;        // 128-row blocks, 32-column chunks (covering the planes' 64-column chunks)
+    int64_t runs;        // nib * mid, run j = b * mid + m
+    PlaneTiling pt;
+    const void* X;
+    int x_f64;
+    const float2* A1df;  // [nib * 128][64] (hi, lo) of A^(1), zero padded
+    const float2* Wdf;   // [mid][64] (hi, lo) of w_m, zero padded
+    const unsigned char* Vsl;  // [nck][6][32][128 B] pieces of a^(N)_kr / tau_k, swizzled
+    const float* tau;    // [nck * 32]
+    int x_tma;           // X tiles come by tensor copy (FP32, s_N % 4 == 0), else the workers load X
+    __nv_bfloat16* planes;
+    DevStats* stats;
+    int* status;
+};
+
+struct SmemCtl {
+    uint64_t a_full, a_empty, b_full[2], b_empty[2], d_full[2], d_empty[2], x_full[2], x_empty[2], drain;
+    uint32_t tmem_base;
+    int abort_flag;
+    float sig[2][kBI];      // sigma_i of a run, by run parity
+    double red[2][8];
+    alignas(16) float tau_s[2][kKC];  // tau_k of a step, with its X tile
+};
+constexpr uint32_t kDynSmem = kPayload + (uint32_t)sizeof(SmemCtl);
+static_assert(kDynSmem <= 227 * 1024, "shared memory above the per-block limit");
+
+// Smallest power of two >= v for finite v > 0 (FP32 / FP64 bit patterns).
+__host__ __device__ __forceinline__ float pow2_ceil_f(float v) {
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    u = (u + 0x007fffffu) & 0xff800000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+__device__ __forceinline__ double pow2_ceil_d(double v) {
+    const unsigned long long u = (__double_as_longlong(v) + 0x000fffffffffffffull) & 0xfff0000000000000ull;
+    return __longlong_as_double((long long)u);
+}
+// 1 / p for a power of two p in the normal range (exact)
+__device__ __forceinline__ float pow2_inv(float p) {
+    return __uint_as_float((uint32_t)(254u << 23) - __float_as_uint(p));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+// Byte offset of element (row, col) in a K-major operand tile with rows of
+// 64 bf16 (128 bytes) and the 128-byte swizzle: 16-byte piece j of row r is
+// stored at piece j ^ (r mod 8); 8-row groups are 1024 bytes apart.
+__host__ __device__ __forceinline__ uint32_t sw128(int row, int col) {
+    return (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u +
+           (uint32_t)((((col >> 3) ^ (row & 7)) << 4) | ((col & 7) << 1));
+}
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Pieces of one scaled double-float value (|h + l| <= 1) on the grids 2^-8s.
+__device__ __forceinline__ void cut6(float h, float l, float* pc) {
+    pc[0] = rintf(h * 0x1p8f) * 0x1p-8f;
+    h -= pc[0];
+    pc[1] = rintf(h * 0x1p16f) * 0x1p-16f;
+    h -= pc[1];
+    pc[2] = rintf(h * 0x1p24f) * 0x1p-24f;
+    h -= pc[2];
+    float hh, ll;
+    two_sum(h, l, hh, ll);  // the low part joins below 2^-24
+    pc[3] = rintf(hh * 0x1p32f) * 0x1p-32f;
+    hh = (hh - pc[3]) + ll;
+    pc[4] = rintf(hh * 0x1p40f) * 0x1p-40f;
+    hh -= pc[4];
+    pc[5] = rintf(hh * 0x1p48f) * 0x1p-48f;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_constant__ CUtensorMap tmX, Params p) {
+    extern __shared__ __align__(1024) unsigned char dsmem[];
+    if (smem_u32(dsmem) & 1023u) {
+        if (threadIdx.x == 0) atomicCAS(p.status, 0, CP_ERR_UNSUPPORTED);
+        return;
+    }
+    SmemCtl& C = *reinterpret_cast<SmemCtl*>(dsmem + kPayload);
+    volatile int* abort_s = &C.abort_flag;
+    const uint32_t sA = smem_u32(dsmem), sB = sA + kABytes, sX = sB + 2 * kBSlot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the zero blocks of both B slots (never written again)
+    for (int e = threadIdx.x; e < (int)(2 * (kSlices - 1) * kBSlice / 16); e += kThreads) {
+        const int sl = e / (int)((kSlices - 1) * kBSlice / 16), o = e % (int)((kSlices - 1) * kBSlice / 16);
+        reinterpret_cast<uint4*>(dsmem + kABytes + sl * kBSlot)[o] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&C.a_full), kWork);
+        mbar_init(smem_u32(&C.a_empty), 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&C.b_full[s]), 1);
+            mbar_init(smem_u32(&C.b_empty[s]), 1);
+            mbar_init(smem_u32(&C.d_full[s]), 1);
+            mbar_init(smem_u32(&C.d_empty[s]), kWork);
+            mbar_init(smem_u32(&C.x_full[s]), 1);
+            mbar_init(smem_u32(&C.x_empty[s]), kWork);
+        }
+        mbar_init(smem_u32(&C.drain), 1);
+        *abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&C.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = C.tmem_base;
+    const int64_t J0 = (int64_t)blockIdx.x * p.runs / gridDim.x;
+    const int64_t J1 = (int64_t)(blockIdx.x + 1) * p.runs / gridDim.x;
+    const int ksteps = (p.R + 15) / 16;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int64_t tt = 0;
+            bool ok = true;
+            for (int64_t j = J0; j < J1 && ok; ++j) {
+                const int b = (int)(j / p.mid);
+                const int m = (int)(j - (int64_t)b * p.mid);
+                for (int c = 0; c < p.nck; ++c, ++tt) {
+                    const int slot = (int)(tt & 1);
+                    const uint32_t pe = (uint32_t)(((tt >> 1) & 1) ^ 1);
+                    if (!(ok = mbar_wait(smem_u32(&C.b_empty[slot]), pe, abort_s, p.status))) break;
+                    const uint32_t fb = smem_u32(&C.b_full[slot]);
+                    mbar_expect_tx(fb, kBBytes);
+                    bulk_load(sB + slot * kBSlot + (kSlices - 1) * kBSlice, p.Vsl + (size_t)c * kBBytes, kBBytes, fb);
+                    // the step's tau_k and (tensor copy) X tile, released by the workers
+                    if (!(ok = mbar_wait(smem_u32(&C.x_empty[slot]), pe, abort_s, p.status))) break;
+                    const uint32_t fx = smem_u32(&C.x_full[slot]);
+                    mbar_expect_tx(fx, (p.x_tma ? kXTile : 0u) + kKC * 4u);
+                    bulk_load(smem_u32(&C.tau_s[slot][0]), p.tau + (size_t)c * kKC, kKC * 4u, fx);
+                    if (p.x_tma) tma_load_3d(sX + slot * kXTile, &tmX, c * kKC, m, b * kBI, fx);
+                }
+            }
+            for (int64_t k = (tt > 2 ? tt - 2 : 0); k < tt; ++k) {
+                mbar_drain(smem_u32(&C.b_full[k & 1]), (uint32_t)((k >> 1) & 1), p.status);
+                mbar_drain(smem_u32(&C.x_full[k & 1]), (uint32_t)((k >> 1) & 1), p.status);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id = idesc_bf16(kLevels * kKC, false, false);
+            int64_t tt = 0;
+            int jr = 0;
+            bool ok = true;
+            for (int64_t j = J0; j < J1 && ok; ++j, ++jr) {
+                if (!(ok = mbar_wait(smem_u32(&C.a_full), (uint32_t)(jr & 1), abort_s, p.status))) break;
+                for (int c = 0; c < p.nck; ++c, ++tt) {
+                    const int slot = (int)(tt & 1);
+                    const uint32_t ph = (uint32_t)((tt >> 1) & 1);
+                    if (!(ok = mbar_wait(smem_u32(&C.d_empty[slot]), ph ^ 1, abort_s, p.status))) break;
+                    if (!(ok = mbar_wait(smem_u32(&C.b_full[slot]), ph, abort_s, p.status))) break;
+                    tc_fence_after();
+                    const uint32_t dbase = tmem + slot * kDBuf;
+                    const uint64_t a0 = sdesc(sA, 16, 1024), b0 = sdesc(sB + slot * kBSlot, 16, 1024);
+                    // K-step outermost (consecutive MMAs of one K-step read different pieces;
+                    // issued piece-pair by piece-pair with a pair's K-steps back to back into
+                    // one accumulator, some K = 48..63 products were measured not to arrive)
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        if (ks >= ksteps) break;
+#pragma unroll
+                        for (int sp = 1; sp <= kSlices; ++sp) {
+                            const uint64_t ao = (uint64_t)(((sp - 1) * kASlice + ks * 32) >> 4);
+                            const uint64_t bo = (uint64_t)(((kSlices - sp) * kBSlice + ks * 32) >> 4);
+                            tc_mma(dbase, a0 + ao, b0 + bo, id, (ks == 0 && sp == 1) ? 0 : 1);
+                        }
+                    }
+                    tc_commit(smem_u32(&C.b_empty[slot]));
+                    tc_commit(smem_u32(&C.d_full[slot]));
+                    if (c == p.nck - 1) tc_commit(smem_u32(&C.a_empty));
+                }
+            }
+            tc_commit(smem_u32(&C.drain));
+            mbar_drain(smem_u32(&C.drain), 0, p.status);
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ------------------------------------------------------------ workers
+        const int wk = warp - 4;
+        const int q = warp & 3;              // TMEM lane quadrant of this warp
+        const int ch = wk >> 2;              // 16-column half of a step
+        const int row = q * 32 + lane;       // TMEM lane = row of the block
+        const int et = wk * 32 + lane;       // 0 .. kWork - 1
+        bool ok = true;
+        float eh = 0.f, el = 0.f, xh = 0.f, xl = 0.f;
+
+        // pieces of u for run j (all workers; named barrier 1 only, taken by every worker)
+        // pieces of u for run j: eight lanes per row (8 rank columns = one 16-byte
+        // piece each), four rows per warp and pass, four passes
+        auto build = [&](int64_t j, int jr) {
+            if (ok) ok = mbar_wait(smem_u32(&C.a_empty), (uint32_t)((jr & 1) ^ 1), abort_s, p.status);
+            if (!ok) return;
+            const int64_t b = j / p.mid, m = j - b * p.mid;
+            const int c8 = lane & 7;
+            const float4* wsrc = reinterpret_cast<const float4*>(p.Wdf + (size_t)m * kRT + c8 * 8);
+            float2 w[8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 t4 = __ldg(wsrc + u);
+                w[2 * u] = make_float2(t4.x, t4.y);
+                w[2 * u + 1] = make_float2(t4.z, t4.w);
+            }
+#pragma unroll 2
+            for (int pass = 0; pass < 4; ++pass) {
+                const int brow = pass * 32 + wk * 4 + (lane >> 3);
+                const float4* asrc =
+                    reinterpret_cast<const float4*>(p.A1df + ((size_t)b * kBI + brow) * kRT + c8 * 8);
+                float2 v[8];
+                float mx = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 t4 = __ldg(asrc + u);
+                    v[2 * u] = df_mul(make_float2(t4.x, t4.y), w[2 * u]);
+                    v[2 * u + 1] = df_mul(make_float2(t4.z, t4.w), w[2 * u + 1]);
+                    mx = fmaxf(mx, fmaxf(fabsf(v[2 * u].x), fabsf(v[2 * u + 1].x)));
+                }
+                // sigma_i >= max_r |u_ir| over the row's eight lanes (hi parts; the low
+                // parts stay inside the 2^-24 slack of the first piece)
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+                const float sg = pow2_ceil_f(fmaxf(mx, 0x1p-100f));
+                if (c8 == 0) C.sig[jr & 1][brow] = sg;
+                const float inv = pow2_inv(sg);
+                float pc[8][kSlices];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cut6(v[u].x * inv, v[u].y * inv, pc[u]);
+                const uint32_t off = sw128(brow, c8 * 8);
+#pragma unroll
+                for (int sl = 0; sl < kSlices; ++sl) {
+                    uint4 q4;
+                    q4.x = bf2(pc[0][sl], pc[1][sl]);
+                    q4.y = bf2(pc[2][sl], pc[3][sl]);
+                    q4.z = bf2(pc[4][sl], pc[5][sl]);
+                    q4.w = bf2(pc[6][sl], pc[7][sl]);
+                    *reinterpret_cast<uint4*>(dsmem + sl * kASlice + off) = q4;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&C.a_full));
+        };
+
+        int64_t tt = 0;
+        int jr = 0;
+        if (J0 < J1) build(J0, 0);
+        for (int64_t j = J0; j < J1; ++j, ++jr) {
+            const int b = (int)(j / p.mid);
+            const int64_t m = j - (int64_t)b * p.mid;
+            const int64_t i = (int64_t)b * kBI + row;
+            const bool row_in = i < p.s1, row_out = row < p.pt.rows(b);
+            for (int c = 0; c < p.nck; ++c, ++tt) {
+                // the next run's pieces of u go in while this run's last step drains
+                if (c == p.nck - 1 && j + 1 < J1) build(j + 1, jr + 1);
+                if (!ok) continue;
+                const int slot = (int)(tt & 1);
+                const uint32_t ph = (uint32_t)((tt >> 1) & 1);
+                const int64_t k0 = (int64_t)c * kKC + ch * 16;
+                float xv[16];
+                if (!p.x_tma) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int64_t k = k0 + u;
+                        xv[u] = (row_in && k < p.sN && !p.x_f64)
+                                    ? __ldg(reinterpret_cast<const float*>(p.X) + (i * p.mid + m) * p.sN + k)
+                                    : 0.f;
+                    }
+                }
+                if (!(ok = mbar_wait(smem_u32(&C.x_full[slot]), ph, abort_s, p.status))) continue;
+                if (!(ok = mbar_wait(smem_u32(&C.d_full[slot]), ph, abort_s, p.status))) continue;
+                tc_fence_after();
+                // sigma_i of this run: written by another worker before its a_full arrival,
+                // which the MMAs behind d_full waited for
+                const float sg = C.sig[jr & 1][row];
+                uint32_t d[kLevels][16];
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + slot * kDBuf + ch * 16;
+#pragma unroll
+                for (int L = 0; L < kLevels; L += 2) tmem_ld16x2_wait(ta + L * kKC, ta + (L + 1) * kKC, d[L], d[L + 1]);
+                float it[16];
+#pragma unroll
+                for (int u = 0; u < 16; u += 4) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(&C.tau_s[slot][ch * 16 + u]);
+                    it[u] = t4.x;
+                    it[u + 1] = t4.y;
+                    it[u + 2] = t4.z;
+                    it[u + 3] = t4.w;
+                }
+                if (p.x_tma) {
+                    // 128-byte rows; 16-byte piece j of row r sits at piece j ^ (r mod 8)
+                    const unsigned char* xr = dsmem + (kABytes + 2 * kBSlot) + slot * kXTile + row * 128;
+#pragma unroll
+                    for (int u = 0; u < 16; u += 4) {
+                        const float4 x4 =
+                            *reinterpret_cast<const float4*>(xr + ((((ch * 16 + u) >> 2) ^ (row & 7)) << 4));
+                        xv[u] = x4.x;
+                        xv[u + 1] = x4.y;
+                        xv[u + 2] = x4.z;
+                        xv[u + 3] = x4.w;
+                    }
+                }
+                mbar_arrive(smem_u32(&C.x_empty[slot]));
+                tc_fence_before();
+                mbar_arrive(smem_u32(&C.d_empty[slot]));
+                const float isg = pow2_inv(sg);
+                float e2 = 0.f, x2 = 0.f;
+                uint32_t hw[8], lw[8];
+#pragma unroll
+                for (int u = 0; u < 16; u += 2) {
+                    float ev[2];
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        const int w = u + v;
+                        const float small = ((__uint_as_float(d[5][w]) + __uint_as_float(d[4][w])) +
+                                             __uint_as_float(d[3][w])) +
+                                            __uint_as_float(d[2][w]);
+                        float h, l;
+                        two_sum(__uint_as_float(d[0][w]), __uint_as_float(d[1][w]), h, l);
+                        l += small;
+                        // scaled units: x / (sigma_i tau_k) - (h + l), exact scalings by powers of two
+                        const float tk = it[w];
+                        float e;
+                        if (p.x_f64) {  // X in FP64: the subtraction in FP64 (rare path)
+                            const int64_t k = k0 + w;
+                            const double xd = (row_in && k < p.sN)
+                                                  ? reinterpret_cast<const double*>(p.X)[(i * p.mid + m) * p.sN + k]
+                                                  : 0.0;
+                            e = (float)((((xd * (double)isg * (double)pow2_inv(tk)) - (double)h) - (double)l) *
+                                        (double)sg * (double)tk);
+                            xv[w] = (float)xd;
+                        } else {
+                            const float xs = xv[w] * isg * pow2_inv(tk);
+                            e = (((xs - h) - l) * sg) * tk;
+                        }
+                        ev[v] = e;
+                        e2 = fmaf(e, e, e2);
+                        x2 = fmaf(xv[w], xv[w], x2);
+                    }
+                    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(ev[0], ev[1]);
+                    const float2 hf = __bfloat1622float2(hi2);
+                    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(ev[0] - hf.x, ev[1] - hf.y);
+                    hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&hi2);
+                    lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&lo2);
+                }
+                float s1, s2;
+                two_sum(eh, e2, s1, s2);
+                eh = s1;
+                el += s2;
+                two_sum(xh, x2, s1, s2);
+                xh = s1;
+                xl += s2;
+                if (row_out) {
+                    // 16 columns = two 16-byte pieces of the row in each plane
+                    const int rows_b = p.pt.rows(b);
+                    const int kc = (int)((int64_t)c * kKC % 64) + ch * 16;  // column inside the 64-column tile
+                    const int64_t tb = p.pt.tile(b, (int)((int64_t)c * kKC / 64), m);
+                    __nv_bfloat16* r0 = p.planes + tb + (int64_t)row * 64;
+                    __nv_bfloat16* r1 = p.planes + tb + ((int64_t)rows_b + row) * 64;
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int j8 = (kc >> 3) + h2;
+                        const int pos = ((j8 ^ (row & 7)) << 3);
+                        *reinterpret_cast<uint4*>(r0 + pos) =
+                            make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
+                        *reinterpret_cast<uint4*>(r1 + pos) =
+                            make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
+                    }
+                }
+            }
+        }
+        // sum E^2 and sum X^2 over the workers (FP64 across threads, fixed order)
+        double num = warp_sum((double)eh + (double)el), den = warp_sum((double)xh + (double)xl);
+        if (lane == 0) {
+            C.red[0][wk] = num;
+            C.red[1][wk] = den;
+        }
+        named_sync(1, kWork);
+        if (et == 0) {
+            double a = 0.0, bsum = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                a += C.red[0][w];
+                bsum += C.red[1][w];
+            }
+            atomicAdd(&p.stats->eres_num, a);
+            atomicAdd(&p.stats->eres_den, bsum);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// ------------------------------------------------------------ preparation
+__device__ __forceinline__ float2 split_df(double d) {
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
+}
+
+// A1df rows (zero padded to nib * 128 x 64) and Wdf rows w_m = prod_{middle q} a^(q)_{i_q(m) r}
+__global__ void recon_prep_rows(Shape s, Ptrs<const double> A, int nib, float2* A1df, float2* Wdf) {
+    const int R = s.R, N = s.N;
+    const int64_t na = (int64_t)nib * kBI * kRT, nw = s.mid * kRT;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + nw; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < na) {
+            const int64_t i = e / kRT;
+            const int r = (int)(e - i * kRT);
+            A1df[e] = (i < s.dims[0] && r < R) ? split_df(A.p[0][i * R + r]) : make_float2(0.f, 0.f);
+        } else {
+            const int64_t f = e - na, m = f / kRT;
+            const int r = (int)(f - m * kRT);
+            double w = r < R ? 1.0 : 0.0;
+            int64_t t = m;
+            for (int qq = N - 2; qq >= 1 && r < R; --qq) {
+                const int64_t iq = t % s.dims[qq];
+                t /= s.dims[qq];
+                w *= A.p[qq][iq * R + r];
+            }
+            Wdf[f] = split_df(w);
+        }
+    }
+}
+
+// Pieces of v_kr = a^(N)_kr / tau_k (one warp per k; lanes r and r + 32),
+// exact in FP64, stored as the swizzled K-major image of each 32-row chunk.
+__global__ void recon_prep_v(Shape s, const double* AN, int nck, unsigned char* Vsl, float* tau) {
+    const int R = s.R;
+    const int64_t sN = s.dims[s.N - 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= (int64_t)nck * kKC) return;
+    double v[2];
+    double mx = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        v[h] = (k < sN && r < R) ? AN[k * R + r] : 0.0;
+        mx = fmax(mx, fabs(v[h]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double t = mx > 0.0 ? pow2_ceil_d(mx) : 1.0;
+    if (lane == 0) tau[k] = (float)t;
+    const int c = (int)(k / kKC), kk = (int)(k - (int64_t)c * kKC);
+    unsigned char* img = Vsl + (size_t)c * kBBytes;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        double x = v[h] / t;  // exact: t is a power of two
+#pragma unroll
+        for (int sl = 1; sl <= kSlices; ++sl) {
+            const double g = ldexp(1.0, 8 * sl);
+            const double pc = rint(x * g) / g;
+            x -= pc;
+            *reinterpret_cast<__nv_bfloat16*>(img + (size_t)(sl - 1) * kBSlice + sw128(kk, r)) =
+                __float2bfloat16_rn((float)pc);
+        }
+    }
+}
+
+struct Layout {
+    size_t a1, w, v, tau, total;
+};
+inline Layout layout_of(const Shape& s) {
+    const PlaneTiling pt = PlaneTiling::of(s);
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    Layout l;
+    l.a1 = 0;
+    l.w = up((size_t)pt.nib * kBI * kRT * sizeof(float2));
+    l.v = l.w + up((size_t)s.mid * kRT * sizeof(float2));
+    l.tau = l.v + up((size_t)pt.nch * 2 * kBBytes);
+    l.total = l.tau + up((size_t)pt.nch * 2 * kKC * sizeof(float));
+    return l;
+}
+
+}  // namespace rtc
+
+bool resid_tc_supported(const Shape& s) { return s.R <= rtc::kRT && s.N >= 2; }
+
+size_t resid_tc_scratch_bytes(const Shape& s) { return rtc::layout_of(s).total; }
+
+int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
+                          void* scratch, DevStats* stats, int* status, cudaStream_t st) {
+    using namespace rtc;
+    static bool attr_set[64] = {};
+    static int sms_of[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(recon_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (dev < 64) {
+            attr_set[dev] = true;
+            sms_of[dev] = sms;
+        }
+    }
+    const int sms = dev < 64 ? sms_of[dev] : 148;
+    const PlaneTiling pt = PlaneTiling::of(s);
+    const Layout l = layout_of(s);
+    unsigned char* sc = (unsigned char*)scratch;
+    Params p;
+    p.N = s.N;
+    p.R = s.R;
+    p.s1 = s.dims[0];
+    p.mid = s.mid;
+    p.sN = s.dims[s.N - 1];
+    p.nib = pt.nib;
+    p.nck = pt.nch * 2;
+    p.runs = (int64_t)pt.nib * s.mid;
+    p.pt = pt;
+    p.X = X;
+    p.x_f64 = xdt == CP_F64;
+    p.A1df = (const float2*)(sc + l.a1);
+    p.Wdf = (const float2*)(sc + l.w);
+    p.Vsl = sc + l.v;
+    p.tau = (const float*)(sc + l.tau);
+    p.planes = (__nv_bfloat16*)planes;
+    p.stats = stats;
+    p.status = status;
+    recon_prep_rows<<<256, 256, 0, st>>>(s, A, pt.nib, (float2*)(sc + l.a1), (float2*)(sc + l.w));
+    const int64_t nk = (int64_t)p.nck * kKC;
+    recon_prep_v<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, st>>>(s, A.p[s.N - 1], p.nck, sc + l.v,
+                                                                    (float*)(sc + l.tau));
+    // X tiles by tensor copy: FP32 X viewed as (s_N, mid, s_1), box 32 x 1 x 128, 128-byte
+    // swizzle, zero fill outside the tensor (rows i >= s_1, columns k >= s_N)
+    CUtensorMap tmX;
+    memset(&tmX, 0, sizeof(tmX));
+    p.x_tma = 0;
+    EncodeTiledFn enc = tc_encode_fn();
+    if (enc && xdt == CP_F32 && p.sN % 4 == 0 && ((uintptr_t)X & 15u) == 0) {
+        cuuint64_t dims[3] = {(cuuint64_t)p.sN, (cuuint64_t)p.mid, (cuuint64_t)p.s1};
+        cuuint64_t strides[2] = {(cuuint64_t)p.sN * 4, (cuuint64_t)p.mid * p.sN * 4};
+        cuuint32_t box[3] = {(cuuint32_t)kKC, 1, (cuuint32_t)kBI};
+        cuuint32_t es[3] = {1, 1, 1};
+        p.x_tma = enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(X), dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const int grid = (int)std::min<int64_t>(sms, p.runs);
+    recon_tc_kernel<<<grid, kThreads, kDynSmem, st>>>(tmX, p);
+    return 3;
+}
+
+}  // namespace cpgn

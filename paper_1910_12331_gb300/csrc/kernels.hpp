@@ -85,6 +85,12 @@ void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, 
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
                         void* scratch, DevStats* stats, cudaStream_t st);
 size_t resid_scratch_bytes(const Shape& s);
+// The same residual tensor with the reconstruction on the tensor cores (R <= 64):
+// error-free bf16 slice products; returns the number of kernels launched.
+bool resid_tc_supported(const Shape& s);
+size_t resid_tc_scratch_bytes(const Shape& s);
+int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
+                          void* scratch, DevStats* stats, int* status, cudaStream_t st);
 
 // ---- residual (k_residual.cu) ------------------------------------------------------
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,

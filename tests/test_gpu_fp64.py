@@ -123,6 +123,29 @@ def test_gn_step_fixed_cg(env, orc, dims, R, k, cg_fp32):
     assert params.lam == lam_o and params.lam_dir == dir_o
 
 
+@pytest.mark.parametrize("dims,R,k", [((20, 20, 20), 5, 5), ((6, 5, 4, 7), 4, 7), ((37, 70, 45), 9, 4),
+                                      ((8, 6), 3, 3), ((150, 120, 90), 12, 6)])
+def test_gn_step_fixed_cg_fp32(env, orc, dims, R, k):
+    """FP32 CG vectors (FP64 gradient, FP32 Gamma and preconditioner): the
+    same k iterations as the FP64 oracle.  Each of the k steps rounds the
+    vectors and the matrices to FP32 (2^-24) and the preconditioned system at
+    lambda_hi has a condition number below 1e2 here, so the direction agrees
+    to 1e2 * k * 2^-24 * (a few) < 1e-4."""
+    torch, api, h = env
+    A = _factors(dims, R, 6)
+    X = _tensor(dims, 6)
+    hi, lo = orc.default_lambda(A)
+    Ad = _dev(torch, A)
+    params = api.gn_params(hi, lo, hi, eps_cg=0.0, cg_max_iter=k, cg_fp32=True)
+    s, st = api.cp_gn_step(h, torch.from_numpy(X).cuda(), Ad, params)
+    Ao, _, _, so, sto = orc.gn_step(X, A, hi, 0, lo, hi, 2.0, 0.0, k)
+    assert st["cg_iters"] == so["cg_iters"] == k
+    assert s == sto == api.CP_WARN_CG_MAXIT
+    d_gpu = [a.cpu().numpy() - a0 for a, a0 in zip(Ad, A)]
+    d_orc = [a - a0 for a, a0 in zip(Ao, A)]
+    assert _relerr(d_gpu, d_orc) <= 1e-4
+
+
 def test_gn_step_tolerance_stop(env, orc):
     torch, api, h = env
     from paper_1910_12331_gb300 import datagen

@@ -119,6 +119,46 @@ def test_gradient_residual_mode_near_optimum(env, orc, dims, R, eps):
     np.testing.assert_allclose(mn, [np.linalg.norm(m) for m in M], rtol=1e-9)
 
 
+@pytest.mark.parametrize("dims,R", [((130, 9, 140), 16), ((130, 9, 140), 33), ((130, 9, 140), 48), ((130, 9, 140), 49),
+                                    ((130, 9, 140), 50), ((140, 130, 150), 64), ((30, 20, 24, 10), 57), ((50, 70), 64)])
+def test_gradient_residual_mode_ranks(env, orc, dims, R):
+    """The residual tensor on the tensor cores covers ranks up to 64 (four
+    16-column K-steps): the residual-form gradient near the optimum stays at
+    the bf16x3 rate times the stationarity, for every rank count."""
+    torch, api, h = env
+    X, A = _near_exact(dims, R, 4, 1e-6)
+    Gr, _, _ = api.cp_gradient(h, torch.from_numpy(X).cuda(), [torch.from_numpy(a).cuda() for a in A], prec="residual")
+    Gam = orc.gamma(orc.gram(A))
+    M = orc.mttkrp(X, A)
+    Go, gno = orc.gradient(A, Gam, M)
+    msum = sum(np.linalg.norm(m) for m in M)
+    err = sum(np.linalg.norm(g.cpu().numpy() - o) for g, o in zip(Gr, Go)) / msum
+    assert err <= 3 * TOL_BF16X3 * (sum(gno) / msum) + 1e-12
+
+
+@pytest.mark.parametrize("R,rank", [(50, 48), (50, 49), (64, 56), (64, 63), (49, 48), (40, 35), (64, None), (50, None)])
+def test_residual_exact_rank(env, orc, R, rank):
+    """At an exact factorisation the residual tensor is only the FP32
+    rounding of X, so the step's entry residual equals the oracle's; one
+    nonzero rank column probes each 16-column K-step of the reconstruction on
+    its own (a missing piece product would show at 1e-3)."""
+    torch, api, h = env
+    dims = (130, 9, 140)
+    rng = np.random.default_rng(3)
+    T = [rng.standard_normal((s, R)) for s in dims]
+    if rank is not None:
+        for t in T:
+            t[:, np.arange(R) != rank] = 0.0
+    from tests import cpref
+
+    X = cpref.reconstruct(T).astype(np.float32)
+    params = api.gn_params(1.0, 1e-9, 1.0, eps_cg=0.0, cg_max_iter=0, prec="residual", cg_fp32=True, lam_fixed=True)
+    _, st = api.cp_gn_step(h, torch.from_numpy(X).cuda(), [torch.from_numpy(t.copy()).cuda() for t in T], params,
+                           check=False)
+    r = orc.residual(X, T)
+    assert abs(st["entry_residual"] - r) <= 1e-3 * r
+
+
 def test_gradient_residual_mode_far(env, orc):
     torch, api, h = env
     X, A = _problem((37, 70, 45), 13, 5)
