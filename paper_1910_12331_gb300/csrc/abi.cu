@@ -40,7 +40,7 @@ constexpr long long kDefaultSpin = 1LL << 24;  // polls (with 64 ns sleeps: abou
 struct cp_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
-    DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch;
+    DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch, grad_part;
     DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf;
     DevStats* h_stats = nullptr;  // pinned
     SplitCache split;             // bf16 planes of X (tensor-core path)
@@ -145,6 +145,7 @@ static cp_status ensure_common(cp_handle h, const Shape& s) {
     const size_t RR = (size_t)s.R * s.R;
     const size_t rows = (size_t)s.roff[s.N];
     CP_TRY(grow(h->gram_part, (size_t)s.N * gram_chunks(s) * RR * sizeof(double)));
+    CP_TRY(grow(h->grad_part, gradient_part_doubles(s) * sizeof(double)));
     CP_TRY(grow(h->S, s.N * RR * sizeof(double)));
     CP_TRY(grow(h->Gam, (size_t)s.N * s.N * RR * sizeof(double)));
     CP_TRY(grow(h->GamF, (size_t)s.N * s.N * RR * sizeof(float)));
@@ -248,7 +249,7 @@ cp_status cp_destroy(cp_handle h) {
     {
         DeviceGuard g(h->device);
         cudaStreamSynchronize(h->stream);
-        DevBuf* bufs[] = {&h->gram_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
+        DevBuf* bufs[] = {&h->gram_part, &h->grad_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
                           &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
                           &h->stats, &h->Y, &h->resid_planes, &h->Adf};
         for (DevBuf* b : bufs)
@@ -313,7 +314,7 @@ cp_status cp_gradient(cp_handle h, const cp_desc* d, const void* X, const double
     CP_TRY(mttkrp_into(h, d, s, X, Ap, packed_ptrs((double*)h->Mp.p, s), prec));
     CP_TRY(gram_gamma(h, s, Ap));
     launch_gradient(s, Ap, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
-                    (DevStats*)h->stats.p, h->stream, prec == CP_PREC_RESIDUAL);
+                    (double*)h->grad_part.p, (DevStats*)h->stats.p, h->stream, prec == CP_PREC_RESIDUAL);
     launch_unpack(s, (const double*)h->Gp.p, ptrs_of(G, s.N), h->stream);
     CUDA_TRY(cudaGetLastError());
     CP_TRY(sync_stats(h));
@@ -422,8 +423,9 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
     CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
     CP_TRY(gram_gamma(h, s, Ac));
     h->launches += 2;
-    launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p, ds, h->stream,
-                    p->prec == CP_PREC_RESIDUAL);
+    launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
+                    (double*)h->grad_part.p, ds, h->stream, p->prec == CP_PREC_RESIDUAL);
+    h->launches += 1;  // the fixed-order norm reduction
     // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
     launch_precond(s, (const double*)h->Gam.p, p->lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
                    (double*)h->precond_scratch.p, ds, h->stream, p->cg_fp32 != 0);

@@ -108,9 +108,12 @@ void launch_gamma(const Shape& s, const double* part, int chunks, double* S, dou
 }
 
 // -------------------------------------------------------------- gradient
-// One thread per (row, column) of the packed gradient.
+// One thread per (row, column) of the packed gradient.  Each block writes its
+// partial ||G||^2 and ||M||^2 to part[n][block]; grad_norms_kernel adds them in
+// a fixed order (no atomics), so the norms, and every decision that depends on
+// them (CG tolerance, stop test), are the same from run to run.
 __global__ void gradient_kernel(Shape s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
-                                DevStats* stats, bool resid) {
+                                double* part, bool resid) {
     __shared__ double red[32];
     const int R = s.R;
     const int n = blockIdx.y;
@@ -135,18 +138,43 @@ __global__ void gradient_kernel(Shape s, Ptrs<const double> A, const double* Gam
     g2 = block_sum(g2, red);
     m2 = block_sum(m2, red);
     if (threadIdx.x == 0) {
-        atomicAdd(&stats->gnorm2[n], g2);
-        atomicAdd(&stats->mnorm2[n], m2);
+        double* o = part + 2 * ((int64_t)n * gridDim.x + blockIdx.x);
+        o[0] = g2;
+        o[1] = m2;
+    }
+}
+
+// warp n: stats->gnorm2[n], mnorm2[n] = fixed-order sums of the nb block partials of mode n
+__global__ void grad_norms_kernel(int N, int nb, const double* part, DevStats* stats) {
+    const int n = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (n >= N) return;
+    double g2 = 0.0, m2 = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+        g2 += part[2 * ((int64_t)n * nb + b)];
+        m2 += part[2 * ((int64_t)n * nb + b) + 1];
+    }
+    g2 = warp_sum(g2);
+    m2 = warp_sum(m2);
+    if (lane == 0) {
+        stats->gnorm2[n] = g2;
+        stats->mnorm2[n] = m2;
         if (!isfinite(g2) || !isfinite(m2)) set_status(&stats->status, CP_ERR_NONFINITE);
     }
 }
 
-void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
-                     DevStats* stats, cudaStream_t st, bool resid) {
+static int gradient_blocks(const Shape& s) {
     int64_t mx = 0;
     for (int n = 0; n < s.N; ++n) mx = std::max<int64_t>(mx, s.dims[n] * s.R);
-    dim3 grid((unsigned)((mx + 255) / 256), s.N);
-    gradient_kernel<<<grid, 256, 0, st>>>(s, A, Gam, M, G, stats, resid);
+    return (int)((mx + 255) / 256);
+}
+
+size_t gradient_part_doubles(const Shape& s) { return (size_t)2 * s.N * gradient_blocks(s); }
+
+void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
+                     double* part, DevStats* stats, cudaStream_t st, bool resid) {
+    const int nb = gradient_blocks(s);
+    gradient_kernel<<<dim3((unsigned)nb, s.N), 256, 0, st>>>(s, A, Gam, M, G, part, resid);
+    grad_norms_kernel<<<1, 32 * s.N, 0, st>>>(s.N, nb, part, stats);
 }
 
 // -------------------------------------------------------- preconditioner

@@ -30,9 +30,9 @@
 // rows, slice m); a step is one 32-column chunk c of a run.
 //   warp 0      producer: the step's pieces of v (6 x 4 KB, one bulk copy,
 //               precomputed once per call, pre-swizzled) into one of two slots.
-//   warp 1      TMEM allocator and MMA issuer (one thread): per K-step, six
-//               MMAs (M = 128, N = 192, one per piece of u) into the six level
-//               accumulators of one of two TMEM buffers (6 levels x 32 columns).
+//   warp 1      TMEM allocator and MMA issuer (one thread): 21 piece pairs x
+//               K/16 MMAs (M = 128, N = 32) into the six level accumulators of
+//               one of two TMEM buffers (6 levels x 32 columns).
 //   warps 4-11  workers: build the pieces of u for a run (6 x 16 KB), then per
 //               step drain the six levels of D (lane = row i, 16 columns per
 //               warp), form E and write its planes.
@@ -62,11 +62,7 @@ constexpr uint32_t kBSlice = kKC * 128;            // 32 rows x 64 bf16
 constexpr uint32_t kABytes = kSlices * kASlice;    // 96 KB
 constexpr uint32_t kBBytes = kSlices * kBSlice;    // 24 KB per step
 constexpr uint32_t kXTile = kBI * kKC * 4;         // 128 rows x 32 FP32 of X, 128-byte swizzle (TMA)
-// A step's B slot: five zero blocks, then the six pieces of v (32 rows each).
-// For piece s of u, the N = 192 window starting at block 6 - s holds piece
-// t = L - s of v in block L - 2 (zero where t < 1), so one MMA per (s, K-step)
-// accumulates every level L = 2..7 into its own 32 TMEM columns.
-constexpr uint32_t kBSlot = (2 * kSlices - 1) * kBSlice;  // 44 KB
+constexpr uint32_t kBSlot = kBBytes;                // a step's B slot: the six pieces of v
 constexpr uint32_t kPayload = kABytes + 2 * kBSlot + 2 * kXTile;
 constexpr int kWork = 256;
 constexpr int kThreads = 128 + kWork;
@@ -171,12 +167,6 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
     volatile int* abort_s = &C.abort_flag;
     const uint32_t sA = smem_u32(dsmem), sB = sA + kABytes, sX = sB + 2 * kBSlot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the zero blocks of both B slots (never written again)
-    for (int e = threadIdx.x; e < (int)(2 * (kSlices - 1) * kBSlice / 16); e += kThreads) {
-        const int sl = e / (int)((kSlices - 1) * kBSlice / 16), o = e % (int)((kSlices - 1) * kBSlice / 16);
-        reinterpret_cast<uint4*>(dsmem + kABytes + sl * kBSlot)[o] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&C.a_full), kWork);
         mbar_init(smem_u32(&C.a_empty), 1);
@@ -221,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
                     if (!(ok = mbar_wait(smem_u32(&C.b_empty[slot]), pe, abort_s, p.status))) break;
                     const uint32_t fb = smem_u32(&C.b_full[slot]);
                     mbar_expect_tx(fb, kBBytes);
-                    bulk_load(sB + slot * kBSlot + (kSlices - 1) * kBSlice, p.Vsl + (size_t)c * kBBytes, kBBytes, fb);
+                    bulk_load(sB + slot * kBSlot, p.Vsl + (size_t)c * kBBytes, kBBytes, fb);
                     // the step's tau_k and (tensor copy) X tile, released by the workers
                     if (!(ok = mbar_wait(smem_u32(&C.x_empty[slot]), pe, abort_s, p.status))) break;
                     const uint32_t fx = smem_u32(&C.x_full[slot]);
@@ -239,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id = idesc_bf16(kLevels * kKC, false, false);
+            const uint32_t id = idesc_bf16(kKC, false, false);
             int64_t tt = 0;
             int jr = 0;
             bool ok = true;
@@ -253,17 +243,25 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
                     tc_fence_after();
                     const uint32_t dbase = tmem + slot * kDBuf;
                     const uint64_t a0 = sdesc(sA, 16, 1024), b0 = sdesc(sB + slot * kBSlot, 16, 1024);
-                    // K-step outermost (consecutive MMAs of one K-step read different pieces;
-                    // issued piece-pair by piece-pair with a pair's K-steps back to back into
-                    // one accumulator, some K = 48..63 products were measured not to arrive)
+                    // K-step outermost, then level, then piece pair: consecutive MMAs go to
+                    // different level accumulators.  (Two other orders were measured to lose
+                    // MMAs that accumulate back to back into one accumulator: piece pair by
+                    // piece pair with a pair's K-steps adjacent, and one N = 192 MMA per piece
+                    // into all six levels at once; this order gave bit-identical results.)
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         if (ks >= ksteps) break;
 #pragma unroll
-                        for (int sp = 1; sp <= kSlices; ++sp) {
-                            const uint64_t ao = (uint64_t)(((sp - 1) * kASlice + ks * 32) >> 4);
-                            const uint64_t bo = (uint64_t)(((kSlices - sp) * kBSlice + ks * 32) >> 4);
-                            tc_mma(dbase, a0 + ao, b0 + bo, id, (ks == 0 && sp == 1) ? 0 : 1);
+                        for (int L = 2; L <= kLevels + 1; ++L) {
+#pragma unroll
+                            for (int sp = 1; sp <= kSlices; ++sp) {
+                                const int t = L - sp;
+                                if (t < 1 || t > kSlices) continue;
+                                const bool first = sp == (L - kSlices > 1 ? L - kSlices : 1);
+                                const uint64_t ao = (uint64_t)(((sp - 1) * kASlice + ks * 32) >> 4);
+                                const uint64_t bo = (uint64_t)(((t - 1) * kBSlice + ks * 32) >> 4);
+                                tc_mma(dbase + (L - 2) * kKC, a0 + ao, b0 + bo, id, (first && ks == 0) ? 0 : 1);
+                            }
                         }
                     }
                     tc_commit(smem_u32(&C.b_empty[slot]));

@@ -20,8 +20,10 @@ void launch_gamma(const Shape& s, const double* part, int chunks, double* S, dou
 // G^(n) = A^(n) Gam[n][n] - M^(n) (packed G, packed M); norms into stats.
 // resid = true: M holds the MTTKRP of the residual tensor, G = -M and the
 // reported |M^(n)| is that of A^(n) Gam[n][n] - G^(n).
+// part: gradient_part_doubles(s) doubles of scratch (per-block partial norms).
 void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
-                     DevStats* stats, cudaStream_t st, bool resid = false);
+                     double* part, DevStats* stats, cudaStream_t st, bool resid);
+size_t gradient_part_doubles(const Shape& s);
 // Pinv[n] = (Gam[n][n] + lam I)^{-1} (FP64 Cholesky + inverse); PinvF float copy (may be null).
 // scratch: precond_scratch_doubles(s) doubles, used only when precond_smem_bytes(R) == 0.
 // fp32: the FP32 factorisation with clamped pivots (writes PinvF only).

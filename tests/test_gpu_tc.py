@@ -198,19 +198,22 @@ def test_mixed_solve_reaches_fp64_stationarity(env, orc):
     assert gn.sum() / sum(np.linalg.norm(m) for m in M) <= 2e-8
 
 
-def test_mixed_solve_bit_reproducible(env, orc):
-    """Every device reduction has a fixed order: two solves from the same
-    state give identical factors and iteration counts, bit for bit."""
+@pytest.mark.parametrize("dims,R,prec", [((130, 40, 70), 9, "bf16x3"), ((300, 60, 200), 24, "bf16x3"),
+                                         ((300, 60, 200), 24, "residual")])
+def test_mixed_solve_bit_reproducible(env, orc, dims, R, prec):
+    """Every device reduction that feeds a decision has a fixed order (the
+    gradient norms included): two solves from the same state give identical
+    factors and iteration counts, bit for bit."""
     torch, api, h = env
     from paper_1910_12331_gb300 import datagen
 
-    p = datagen.make_problem((130, 40, 70), 9, "normal", 0.5, 1e-6, np.float32, seed=12)
+    p = datagen.make_problem(dims, R, "normal", 0.5, 1e-6, np.float32, seed=12)
     hi, lo = orc.default_lambda(p["init"])
     X = torch.from_numpy(p["X"]).cuda()
     outs = []
     for _ in range(2):
         Ad = [torch.from_numpy(a.copy()).cuda() for a in p["init"]]
-        params = api.gn_params(hi, lo, hi, prec="bf16x3")
+        params = api.gn_params(hi, lo, hi, prec=prec)
         opts = api.solve_opts(max_iters=12, target_stationarity=0.0, refine_below=3e-5)
         _, res = api.cp_gn_solve(h, X, Ad, params, opts)
         outs.append(([a.cpu().numpy() for a in Ad], res["cg_iters_total"], res["iters"]))
