@@ -159,6 +159,25 @@ def test_residual_exact_rank(env, orc, R, rank):
     assert abs(st["entry_residual"] - r) <= 1e-3 * r
 
 
+def test_residual_gradient_call_to_call_identical(env):
+    """The residual tensor on the tensor cores is deterministic: repeated
+    calls on one input (many CTAs, many runs per CTA, R = 50) are bit-identical."""
+    torch, api, h = env
+    rng = np.random.default_rng(21)
+    dims, R = (384, 96, 320), 50
+    A = [torch.from_numpy(rng.standard_normal((s, R))).cuda() for s in dims]
+    X = torch.from_numpy(rng.standard_normal(dims).astype(np.float32)).cuda()
+    ref = None
+    for _ in range(8):
+        G, _, _ = api.cp_gradient(h, X, A, prec="residual")
+        g = [x.cpu().numpy() for x in G]
+        if ref is None:
+            ref = g
+        else:
+            for a, b in zip(g, ref):
+                assert np.array_equal(a, b)
+
+
 def test_gradient_residual_mode_far(env, orc):
     torch, api, h = env
     X, A = _problem((37, 70, 45), 13, 5)
