@@ -77,31 +77,32 @@ __device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int* p, un
 // monotonic arrival counter (zeroed before the launch): the k-th barrier is
 // complete when the counter reaches k * nblocks.  Thread 0 of each block
 // publishes the block's writes (fence + release add) and polls with acquire
-// loads.  Every wait is bounded by `limit` polls: on expiry the barrier
-// records CP_ERR_TIMEOUT, raises the abort flag and returns false, and so do
-// all later barriers of the launch, so that every block leaves the kernel.
+// loads; the abort flag is read every 32nd poll, so that a poll costs one L2
+// round trip.  Every wait is bounded by `limit` polls: on expiry the barrier
+// records CP_ERR_TIMEOUT, raises the abort flag and returns false; a block
+// waiting in any barrier sees the flag within 32 polls and returns false too,
+// so that every block leaves the kernel.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, unsigned int nblocks, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (ld_volatile_s32(&bar->abort)) {
-            ok = 0;
-        } else {
-            __threadfence();
-            const unsigned int old = atom_add_release_u32(&bar->count, 1u);
-            const unsigned int target = (old / nblocks + 1u) * nblocks;
-            long long polls = 0;
-            while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
-                if (ld_volatile_s32(&bar->abort)) { ok = 0; break; }
-                if (++polls > limit) {
-                    set_status(status, CP_ERR_TIMEOUT);
-                    atomicExch(&bar->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                if (polls > 256) __nanosleep(32);
+        __threadfence();
+        const unsigned int old = atom_add_release_u32(&bar->count, 1u);
+        const unsigned int target = (old / nblocks + 1u) * nblocks;
+        long long polls = 0;
+        while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
+            if (++polls > limit) {
+                set_status(status, CP_ERR_TIMEOUT);
+                atomicExch(&bar->abort, 1);
+                ok = 0;
+                break;
             }
+            if ((polls & 31) == 0 && ld_volatile_s32(&bar->abort)) {
+                ok = 0;
+                break;
+            }
+            if (polls > 256) __nanosleep(32);
         }
         s_ok = ok;
     }
