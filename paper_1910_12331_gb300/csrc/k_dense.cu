@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_kernel(Shape s, const
     __shared__ T s_inv;
     const int R = s.R, n = blockIdx.x;
     const bool in_smem = scratch == nullptr;
-    T* B = in_smem ? reinterpret_cast<T*>(smem_raw) : scratch + (int64_t)n * (R * R + R);
+    T* B = in_smem ? reinterpret_cast<T*>(smem_raw) : scratch + (int64_t)n * (R * R + 2 * R);
     T* f = B + R * R;  // column j of the previous step
     const double* Gnn = Gam + ((int64_t)n * s.N + n) * R * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -266,10 +266,11 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_df_kernel(Shape s, co
                                                                      DevStats* stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_bad;
-    __shared__ float2 s_inv;
     const int R = s.R, n = blockIdx.x;
-    float2* B = scratch ? scratch + (int64_t)n * (R * R + R) : reinterpret_cast<float2*>(smem_raw);
+    // B (R x R), then f (column j before step j) and prow (pivot row j scaled by 1/p)
+    float2* B = scratch ? scratch + (int64_t)n * (R * R + 2 * R) : reinterpret_cast<float2*>(smem_raw);
     float2* f = B + R * R;
+    float2* prow = f + R;
     const double* Gnn = Gam + ((int64_t)n * s.N + n) * R * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) s_bad = 0;
@@ -279,33 +280,38 @@ __global__ void __launch_bounds__(kPrecondThreads) precond_df_kernel(Shape s, co
         B[e] = make_float2(h, (float)(v - (double)h));
     }
     __syncthreads();
+    // two block barriers per pivot: (1) snapshot column j and the scaled pivot row,
+    // (2) update every row from the snapshots
     for (int j = 0; j < R; ++j) {
-        if (threadIdx.x == 0) {
-            // 1/p in double-float: FP32 reciprocal, then one Newton step with an
-            // error-free residual r = 1 - p h (no FP64 instruction on this serial path)
-            float2 pv = B[j * R + j];
-            if (!(pv.x > 0.f)) {
-                s_bad = 1;
-                pv = make_float2(1.f, 0.f);
-            }
-            const float h = 1.0f / pv.x;
-            const float2 ph = df_mul2(pv, make_float2(h, 0.f));
-            const float r = (1.0f - ph.x) - ph.y;
-            const float c = h * r;
-            const float ih = h + c;
-            s_inv = make_float2(ih, c - (ih - h));
+        // 1/p in double-float, formed by every thread: FP32 reciprocal, then one Newton
+        // step with an error-free residual r = 1 - p h (no FP64 instruction)
+        float2 pv = B[j * R + j];
+        if (!(pv.x > 0.f)) {
+            if (threadIdx.x == 0) s_bad = 1;
+            pv = make_float2(1.f, 0.f);
         }
-        for (int i = threadIdx.x; i < R; i += blockDim.x) f[i] = B[i * R + j];
+        const float hr = 1.0f / pv.x;
+        const float2 ph = df_mul2(pv, make_float2(hr, 0.f));
+        const float rr = (1.0f - ph.x) - ph.y;
+        const float cr = hr * rr;
+        const float ih = hr + cr;
+        const float2 inv = make_float2(ih, cr - (ih - hr));
+        for (int i = threadIdx.x; i < R; i += blockDim.x) {
+            f[i] = B[i * R + j];
+            prow[i] = i == j ? inv : df_mul2(B[j * R + i], inv);
+        }
         __syncthreads();
-        const float2 inv = s_inv;
-        for (int k = threadIdx.x; k < R; k += blockDim.x) B[j * R + k] = k == j ? inv : df_mul2(B[j * R + k], inv);
-        __syncthreads();
+        // rows i != j: B[i][k] -= f_i B'[j][k] (k != j), B[i][j] = -f_i / p; row j: B'[j][k]
         for (int i = warp; i < R; i += nw) {
-            if (i == j) continue;
             const float2 fi = f[i];
             for (int k = lane; k < R; k += 32) {
-                const float2 t = df_mul2(fi, k == j ? inv : B[j * R + k]);
-                B[i * R + k] = k == j ? make_float2(-t.x, -t.y) : df_sub2(B[i * R + k], t);
+                const float2 pk = prow[k];
+                if (i == j) {
+                    B[j * R + k] = pk;
+                } else {
+                    const float2 t = df_mul2(fi, pk);
+                    B[i * R + k] = k == j ? make_float2(-t.x, -t.y) : df_sub2(B[i * R + k], t);
+                }
             }
         }
         __syncthreads();
@@ -334,27 +340,29 @@ void launch_precond(const Shape& s, const double* Gam, double lam, double* Pinv,
     // The blocks Gamma^(n,n) + lam I of a collinear problem at small lam are
     // too ill-conditioned for an FP32 elimination: FP64 for the plain path,
     // double-float for the mixed path (whose FP32 CG gets the inverse rounded once).
-    const size_t bytes = ((size_t)s.R * s.R + s.R) * sizeof(double);
+    // shared memory (or the global scratch when it does not fit): R x R + 2 R eight-byte words
+    // (the FP64 kernel uses R x R + R of them)
+    const size_t bytes = precond_smem_bytes(s.R);
     if (fp32) {
-        if (bytes <= 200 * 1024)
+        if (bytes)
             precond_df_kernel<<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, PinvF, nullptr, stats);
         else
             precond_df_kernel<<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, Pinv, PinvF, (float2*)scratch, stats);
         return;
     }
     float* pf = nullptr;
-    if (bytes <= 200 * 1024)
+    if (bytes)
         precond_kernel<<<s.N, kPrecondThreads, bytes, st>>>(s, Gam, lam, Pinv, pf, nullptr, stats);
     else
         precond_kernel<<<s.N, kPrecondThreads, 0, st>>>(s, Gam, lam, Pinv, pf, scratch, stats);
 }
 
 size_t precond_smem_bytes(int R) {
-    const size_t bytes = ((size_t)R * R + R) * sizeof(double);
+    const size_t bytes = ((size_t)R * R + 2 * (size_t)R) * sizeof(double);
     return bytes <= 200 * 1024 ? bytes : 0;
 }
 
-size_t precond_scratch_doubles(const Shape& s) { return (size_t)s.N * ((size_t)s.R * s.R + s.R); }
+size_t precond_scratch_doubles(const Shape& s) { return (size_t)s.N * ((size_t)s.R * s.R + 2 * (size_t)s.R); }
 
 // ------------------------------------------------------- pack / update
 template <typename T>
