@@ -130,6 +130,16 @@ class ClockSampler:
         for line in self._proc.stdout:
             self.samples.append([x.strip() for x in line.split(",")])
 
+    def wait_first(self, timeout_s=5.0):
+        """Block until nvidia-smi has produced its first sample (its start-up
+        then lies outside any region timed afterwards)."""
+        t0 = time.time()
+        while self._proc and not self.samples and time.time() - t0 < timeout_s:
+            time.sleep(0.01)
+
+    def mark(self):
+        return len(self.samples)
+
     def __exit__(self, *exc):
         if self._proc:
             self._proc.terminate()
@@ -138,19 +148,22 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self._proc.kill()
 
-    def summary(self):
-        if not self.samples:
+    def summary(self, i0=0, i1=None):
+        """Clock median and throttle reasons over samples [i0, i1] (the timed region
+        and the sample taken right after it)."""
+        sel = self.samples[i0:(None if i1 is None else i1 + 1)] or self.samples[-1:]
+        if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        sm = [float(s[0]) for s in sel if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in sel if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for s in self.samples:
+        for s in sel:
             for k, nm in enumerate(names):
                 if len(s) > 4 + k and s[4 + k].lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+                "reasons": sorted(reasons), "samples": len(sel)}
 
 
 def cpu_oracle_sample(p, lam_hi, lam_lo, gn_iters, n_steps=1):
@@ -239,7 +252,9 @@ def batched_timing(dev, count=512):
     """The batched workload: 512 independent order-3 FP32 problems, sides
     uniform in 16..96, ranks uniform in 4..24, N(0,1) factors plus 1e-8
     relative noise, each solved to r <= 1e-6 (or 200 GN iterations) by one
-    persistent kernel launch."""
+    persistent kernel launch.  A plan is created once (the autotuner picks
+    the block size on a scratch copy of the factors); the timed call is one
+    plan launch captured in a CUDA graph and replayed, plus the result copy."""
     import torch
 
     from paper_1910_12331_gb300 import api, datagen
@@ -248,24 +263,31 @@ def batched_timing(dev, count=512):
     Xs = [torch.from_numpy(p["X"]).to(dev) for p in probs]
     h = api.Handle(dev)
     stream = torch.cuda.current_stream(dev)
-
-    def batch():
-        out = []
-        for p, X in zip(probs, Xs):
-            hi, lo = lam_thresholds(p["init"])
-            out.append(dict(X=X, A=[torch.from_numpy(a.copy()).to(dev) for a in p["init"]], lam=hi, lam_lo=lo,
-                            lam_hi=hi, mu=MU))
-        return out
-
-    api.cp_gn_solve_batched(h, batch()[:16], EPS_CG, CG_MAX, 200, 1e-6)  # warm-up
-    b = batch()
+    b = []
+    for p, X in zip(probs, Xs):
+        hi, lo = lam_thresholds(p["init"])
+        b.append(dict(X=X, A=[torch.from_numpy(a.copy()).to(dev) for a in p["init"]], lam=hi, lam_lo=lo,
+                      lam_hi=hi, mu=MU))
+    init = [[a.clone() for a in q["A"]] for q in b]
+    t0 = time.perf_counter()
+    plan = api.BatchPlan(h, b, EPS_CG, CG_MAX, 200, 1e-6, autotune=True)
+    tune_s = time.perf_counter() - t0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.launch()
+    for q, a0 in zip(b, init):
+        for a, c in zip(q["A"], a0):
+            a.copy_(c)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res = api.cp_gn_solve_batched(h, b, EPS_CG, CG_MAX, 200, 1e-6)
+    g.replay()
+    res = plan.results()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    threads = plan.threads
+    plan.close()
     h.close()
     conv = sum(r["converged"] for r in res)
     return {"workload": f"{count} order-3 FP32 problems, sides U{{16..96}}, ranks U{{4..24}}, N(0,1) factors, "
@@ -275,7 +297,8 @@ def batched_timing(dev, count=512):
             "cg_iters_mean": float(np.mean([r["cg_iters_total"] for r in res])),
             "cg_breakdowns": sum(r["cg_breakdowns"] for r in res),
             "status_counts": {str(k): sum(1 for r in res if r["status"] == k) for k in sorted({r["status"] for r in res})},
-            "launches": 1}
+            "launches": 1, "graph": "one captured plan launch, replayed", "threads_per_cta": threads,
+            "autotune_s": tune_s}
 
 
 def run_kernel(which):
@@ -364,19 +387,23 @@ def main():
         if pg:
             pg.barrier()
 
-    # ---- warm-up and timed steps (mixed path)
-    for _ in range(args.warmup):
-        solve("mixed")
-    results = []
-    barrier()
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- warm-up and timed steps (mixed path); the clock sampler starts before the
+    # warm-up so that nvidia-smi's start-up does not fall into the timed region
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        for _ in range(args.warmup):
+            solve("mixed")
+        results = []
+        barrier()
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        i0 = clk.mark()
         e0.record(stream)
         for _ in range(args.steps):
             results.append(solve("mixed"))
         e1.record(stream)
         barrier()
+        i1 = clk.mark()
     t_total = e0.elapsed_time(e1) / 1e3
     t_step = t_total / args.steps
     if pg:
@@ -497,7 +524,7 @@ def main():
         "cp_loss": loss_info,
         "batched": batch_info,
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
-        "clocks": clk.summary(),
+        "clocks": clk.summary(i0, i1),
     }
     print(json.dumps(line), flush=True)
     if pg:

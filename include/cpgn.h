@@ -271,6 +271,33 @@ typedef struct {
 cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
                               int cg_max_iter, int max_iters, double target_residual, cp_batch_result* results);
 
+/* The same batched solve as a reusable plan: cp_batch_plan_create checks the
+ * problems (same rules and errors as cp_gn_solve_batched), copies their
+ * descriptors to the device, allocates the results and, if `autotune` is
+ * nonzero, times the kernel's block sizes (128, 256 and 384 threads) on a
+ * device copy of the factors of at most 64 of the problems -- the caller's
+ * factors are not modified -- and keeps the fastest (otherwise 256).
+ * Synchronises.  The plan keeps the device pointers of the problems: X and A
+ * must stay allocated while the plan is used.
+ *
+ * cp_batch_plan_launch enqueues one solve of every problem from its current
+ * factors (A in/out, as cp_gn_solve_batched) on the handle's stream: a reset of
+ * the plan's work counter and one kernel launch, with no allocation and no
+ * synchronisation, so it may be captured into a CUDA graph and replayed.
+ * Launches of one plan must not overlap on the GPU (they share the counter
+ * and the results).  cp_batch_plan_results copies the results of the last
+ * completed launch to `results` (host, nprob entries); synchronises.
+ * cp_batch_plan_threads returns the block size in use.  Errors: CP_ERR_ARG,
+ * CP_ERR_UNSUPPORTED, CP_ERR_NOMEM, CP_ERR_CUDA. */
+typedef struct cp_batch_plan_s* cp_batch_plan;
+cp_status cp_batch_plan_create(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
+                               int cg_max_iter, int max_iters, double target_residual, int autotune,
+                               cp_batch_plan* plan);
+cp_status cp_batch_plan_launch(cp_handle h, cp_batch_plan plan);
+cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result* results);
+cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads);
+cp_status cp_batch_plan_destroy(cp_batch_plan plan);
+
 /* ---------------------------------------------------------------------------
  * Matvec without device allocation.  The paper has no counterpart: this call
  * serves callers that cannot call cudaMalloc -- code running under a fixed,

@@ -25,7 +25,9 @@ PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3, "residual": CP_PREC_RESI
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
-           "cp_residual", "cp_residual_sums", "cp_gn_solve_batched", "cp_gn_matvec_noalloc")
+           "cp_residual", "cp_residual_sums", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
+           "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads",
+           "cp_batch_plan_destroy")
 
 
 class cp_desc(ctypes.Structure):
@@ -127,6 +129,12 @@ def load(build_if_missing: bool = False):
         L.cp_gn_matvec_noalloc.argtypes = [pd, vp, vp, d, vp, vp]
         L.cp_gn_solve_batched.argtypes = [vp, i, ctypes.POINTER(cp_batch_problem), d, i, i, d,
                                           ctypes.POINTER(cp_batch_result)]
+        L.cp_batch_plan_create.argtypes = [vp, i, ctypes.POINTER(cp_batch_problem), d, i, i, d, i,
+                                           ctypes.POINTER(vp)]
+        L.cp_batch_plan_launch.argtypes = [vp, vp]
+        L.cp_batch_plan_results.argtypes = [vp, vp, ctypes.POINTER(cp_batch_result)]
+        L.cp_batch_plan_threads.argtypes = [vp, ctypes.POINTER(i)]
+        L.cp_batch_plan_destroy.argtypes = [vp]
         for name in SYMBOLS:
             if name != "cp_status_string":
                 getattr(L, name).restype = ctypes.c_int
@@ -346,10 +354,7 @@ def cp_residual_sums(h: Handle, X, A):
     return e.value, x.value
 
 
-def cp_gn_solve_batched(h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_iters=200, target_residual=1e-6):
-    """Solve many small order-3 problems in one persistent launch.  problems: list of
-    dicts with X (float32 CUDA, 3-D), A (three float64 CUDA (s_n, R) tensors, updated in
-    place), lam, lam_lo, lam_hi, mu.  Returns a list of result dicts."""
+def _batch_array(problems):
     n = len(problems)
     arr = (cp_batch_problem * max(n, 1))()
     for k, q in enumerate(problems):
@@ -364,12 +369,68 @@ def cp_gn_solve_batched(h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_i
         arr[k].X = X.data_ptr()
         arr[k].A = (ctypes.c_void_p * 3)(*[a.data_ptr() for a in A])
         arr[k].lam, arr[k].lam_lo, arr[k].lam_hi, arr[k].mu = q["lam"], q["lam_lo"], q["lam_hi"], q.get("mu", 2.0)
+    return arr
+
+
+_BATCH_KEYS = ("status", "iters", "cg_iters_total", "converged", "cg_breakdowns", "rel_residual", "lam")
+
+
+def cp_gn_solve_batched(h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_iters=200, target_residual=1e-6):
+    """Solve many small order-3 problems in one persistent launch.  problems: list of
+    dicts with X (float32 CUDA, 3-D), A (three float64 CUDA (s_n, R) tensors, updated in
+    place), lam, lam_lo, lam_hi, mu.  Returns a list of result dicts."""
+    n = len(problems)
+    arr = _batch_array(problems)
     res = (cp_batch_result * max(n, 1))()
     h._bind_stream()
     _check(load().cp_gn_solve_batched(h.h, n, arr, eps_cg, cg_max_iter, max_iters, target_residual, res),
            "cp_gn_solve_batched")
-    keys = ("status", "iters", "cg_iters_total", "converged", "cg_breakdowns", "rel_residual", "lam")
-    return [{k2: getattr(res[k], k2) for k2 in keys} for k in range(n)]
+    return [{k2: getattr(res[k], k2) for k2 in _BATCH_KEYS} for k in range(n)]
+
+
+class BatchPlan:
+    """A reusable batched solve (cp_batch_plan_*): created once (with the
+    autotuner's choice of block size), then launched -- asynchronously, on the
+    handle's stream, capturable into a CUDA graph -- and read back."""
+
+    def __init__(self, h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_iters=200, target_residual=1e-6,
+                 autotune=True):
+        self.h, self.n = h, len(problems)
+        self._keep = problems  # the plan holds their device pointers
+        arr = _batch_array(problems)
+        p = ctypes.c_void_p()
+        h._bind_stream()
+        _check(load().cp_batch_plan_create(h.h, self.n, arr, eps_cg, cg_max_iter, max_iters, target_residual,
+                                           int(bool(autotune)), ctypes.byref(p)), "cp_batch_plan_create")
+        self.p = p
+
+    @property
+    def threads(self):
+        t = ctypes.c_int()
+        _check(load().cp_batch_plan_threads(self.p, ctypes.byref(t)), "cp_batch_plan_threads")
+        return t.value
+
+    def launch(self):
+        """Enqueue one solve of every problem on torch's current stream (no synchronisation)."""
+        self.h._bind_stream()
+        _check(load().cp_batch_plan_launch(self.h.h, self.p), "cp_batch_plan_launch")
+
+    def results(self):
+        res = (cp_batch_result * self.n)()
+        self.h._bind_stream()
+        _check(load().cp_batch_plan_results(self.h.h, self.p, res), "cp_batch_plan_results")
+        return [{k2: getattr(res[k], k2) for k2 in _BATCH_KEYS} for k in range(self.n)]
+
+    def close(self):
+        if self.p:
+            load().cp_batch_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cp_gn_matvec_noalloc(A, W, lam, Q):

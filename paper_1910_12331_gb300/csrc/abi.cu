@@ -617,6 +617,55 @@ cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* pr
                        results);
 }
 
+}  // extern "C"
+
+struct cp_batch_plan_s {
+    int device;
+    int nprob;
+    cpgn::BatchPlan* p;
+};
+
+extern "C" {
+
+cp_status cp_batch_plan_create(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
+                               int cg_max_iter, int max_iters, double target_residual, int autotune,
+                               cp_batch_plan* plan) {
+    if (!h || !plan || nprob < 1 || !problems || cg_max_iter < 0 || max_iters < 0 || !(eps_cg >= 0.0))
+        return CP_ERR_ARG;
+    *plan = nullptr;
+    DeviceGuard g(h->device);
+    BatchPlan* p = nullptr;
+    CP_TRY(batch_plan_create(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters, target_residual,
+                             autotune, &p));
+    *plan = new cp_batch_plan_s{h->device, nprob, p};
+    return CP_OK;
+}
+
+cp_status cp_batch_plan_launch(cp_handle h, cp_batch_plan plan) {
+    if (!h || !plan || plan->device != h->device) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    return batch_plan_launch(plan->p, h->stream);
+}
+
+cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result* results) {
+    if (!h || !plan || !results || plan->device != h->device) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    return batch_plan_results(plan->p, h->stream, results);
+}
+
+cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads) {
+    if (!plan || !threads) return CP_ERR_ARG;
+    *threads = batch_plan_threads(plan->p);
+    return CP_OK;
+}
+
+cp_status cp_batch_plan_destroy(cp_batch_plan plan) {
+    if (!plan) return CP_ERR_ARG;
+    batch_plan_destroy(plan->p);
+    delete plan;
+    return CP_OK;
+}
+
 cp_status cp_residual_sums(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* sq_err,
                            double* sq_x) {
     if (!h || !X) return CP_ERR_ARG;

@@ -101,5 +101,13 @@ void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const
 // ---- batched small problems (k_batched.cu) -----------------------------------------
 cp_status run_batched(int device, cudaStream_t stream, int nprob, const cp_batch_problem* problems, double eps_cg,
                       int cg_max_iter, int max_iters, double target_residual, cp_batch_result* results);
+struct BatchPlan;
+cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp_batch_problem* problems,
+                            double eps_cg, int cg_max_iter, int max_iters, double target_residual, int autotune,
+                            BatchPlan** out);
+cp_status batch_plan_launch(BatchPlan* pl, cudaStream_t stream);
+cp_status batch_plan_results(BatchPlan* pl, cudaStream_t stream, cp_batch_result* results);
+int batch_plan_threads(const BatchPlan* pl);
+void batch_plan_destroy(BatchPlan* pl);
 
 }  // namespace cpgn

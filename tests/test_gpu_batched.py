@@ -91,3 +91,93 @@ def test_argument_checks(env, orc):
     with pytest.raises(api.CPError):  # shared memory above the per-block limit
         api.cp_gn_solve_batched(h, [q])
     assert api.cp_gn_solve_batched(h, []) == []
+
+
+def _batch(torch, orc, count, seed0):
+    rng = np.random.default_rng(seed0)
+    probs = []
+    for k in range(count):
+        dims = tuple(int(x) for x in rng.integers(16, 49, size=3))
+        R = int(rng.integers(4, 13))
+        _, q = _prob(torch, orc, dims, R, seed0 + k)
+        probs.append(q)
+    return probs
+
+
+def _snapshot(probs):
+    return [[a.clone() for a in q["A"]] for q in probs]
+
+
+def _restore(probs, snap):
+    for q, s in zip(probs, snap):
+        for a, b in zip(q["A"], s):
+            a.copy_(b)
+
+
+def test_plan_matches_one_shot(env, orc):
+    """A plan (block size 256, no autotuning) launches the same kernel as the
+    one-shot call: identical factors and results, bit for bit."""
+    torch, api, h = env
+    probs = _batch(torch, orc, 12, 500)
+    snap = _snapshot(probs)
+    r1 = api.cp_gn_solve_batched(h, probs, eps_cg=1e-3, cg_max_iter=100, max_iters=30, target_residual=1e-6)
+    a1 = _snapshot(probs)
+    _restore(probs, snap)
+    plan = api.BatchPlan(h, probs, eps_cg=1e-3, cg_max_iter=100, max_iters=30, target_residual=1e-6, autotune=False)
+    assert plan.threads == 256
+    plan.launch()
+    r2 = plan.results()
+    plan.close()
+    assert r1 == r2
+    for x, y in zip(a1, _snapshot(probs)):
+        for a, b in zip(x, y):
+            assert torch.equal(a, b)
+
+
+def test_plan_graph_replay(env, orc):
+    """A plan launch captured in a CUDA graph and replayed from the same
+    factors gives the same factors and results as a direct launch."""
+    torch, api, h = env
+    probs = _batch(torch, orc, 10, 600)
+    snap = _snapshot(probs)
+    plan = api.BatchPlan(h, probs, eps_cg=1e-3, cg_max_iter=100, max_iters=30, target_residual=1e-6, autotune=False)
+    plan.launch()
+    r_direct = plan.results()
+    a_direct = _snapshot(probs)
+    _restore(probs, snap)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.launch()
+    _restore(probs, snap)  # capture does not run the kernel; start the replay from the initial factors
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    r_graph = plan.results()
+    plan.close()
+    assert r_graph == r_direct
+    for x, y in zip(a_direct, _snapshot(probs)):
+        for a, b in zip(x, y):
+            assert torch.equal(a, b)
+
+
+def test_plan_autotune(env, orc):
+    """The autotuner times the block sizes on a scratch copy of the factors:
+    the caller's factors are untouched by plan creation, the pick is one of
+    the variants, and the tuned plan solves the batch."""
+    torch, api, h = env
+    probs = _batch(torch, orc, 16, 700)
+    snap = _snapshot(probs)
+    plan = api.BatchPlan(h, probs, eps_cg=1e-3, cg_max_iter=250, max_iters=200, target_residual=1e-6, autotune=True)
+    for x, y in zip(snap, _snapshot(probs)):
+        for a, b in zip(x, y):
+            assert torch.equal(a, b)
+    assert plan.threads in (128, 256, 384)
+    plan.launch()
+    res = plan.results()
+    plan.close()
+    assert sum(r["converged"] for r in res) >= 14
+    for q, r in zip(probs, res):
+        if r["converged"]:
+            rr = orc.residual(q["X"].cpu().numpy(), [a.cpu().numpy() for a in q["A"]])
+            assert rr <= 1.2e-6
