@@ -544,11 +544,12 @@ __global__ void recon_prep_v(Shape s, const double* AN, int nck, unsigned char* 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int r = lane + 32 * h;
-        double x = v[h] / t;  // exact: t is a power of two
+        // exact scalings by powers of two: multiplications by their exact reciprocals
+        double x = v[h] * __longlong_as_double((2046LL << 52) - __double_as_longlong(t));  // 1 / t, t = 2^k
 #pragma unroll
         for (int sl = 1; sl <= kSlices; ++sl) {
-            const double g = ldexp(1.0, 8 * sl);
-            const double pc = rint(x * g) / g;
+            const double g = ldexp(1.0, 8 * sl), gi = ldexp(1.0, -8 * sl);
+            const double pc = rint(x * g) * gi;
             x -= pc;
             *reinterpret_cast<__nv_bfloat16*>(img + (size_t)(sl - 1) * kBSlice + sw128(kk, r)) =
                 __float2bfloat16_rn((float)pc);
