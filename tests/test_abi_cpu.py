@@ -61,6 +61,27 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.cp_create(None, 0) == 1
 
 
+def test_batch_plan_arguments_rejected_without_gpu(lib):
+    """The plan entry points check their arguments before any CUDA call."""
+    vp = ctypes.c_void_p
+    lib.cp_batch_plan_create.restype = ctypes.c_int
+    lib.cp_batch_plan_create.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
+    out = vp()
+    assert lib.cp_batch_plan_create(None, 4, None, 1e-3, 10, 10, 1e-6, 0, ctypes.byref(out)) == 1
+    assert out.value is None
+    for name in ("cp_batch_plan_launch", "cp_batch_plan_results"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        assert f(None, None, None) == 1 if name == "cp_batch_plan_results" else f(None, None) == 1
+    lib.cp_batch_plan_threads.restype = ctypes.c_int
+    lib.cp_batch_plan_threads.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    t = ctypes.c_int(-1)
+    assert lib.cp_batch_plan_threads(None, ctypes.byref(t)) == 1 and t.value == -1
+    lib.cp_batch_plan_destroy.restype = ctypes.c_int
+    assert lib.cp_batch_plan_destroy(None) == 1
+
+
 def test_struct_layouts_match_header():
     """The ctypes mirrors of the header structs have the C sizes (checked with gcc)."""
     import subprocess
