@@ -56,7 +56,7 @@ PROFILED = {
                     "paper_1910_12331_gb300/csrc/common.cuh": "a5a6709e4bcc944414b3ddce82e9908cfe47e373"},
             "dram_bytes": 927744 + 8192, "cg_iters": 4},
     # recon_tc_kernel (258194688 B read + 237863424 B written) + mttkrp_tc_kernel (287438592 + 5595904)
-    "gradient": {"src": {"paper_1910_12331_gb300/csrc/k_resid_tc.cu": "4808cd243c3806ef0267938b8fae65b678458f1e",
+    "gradient": {"src": {"paper_1910_12331_gb300/csrc/k_resid_tc.cu": "dcfadb974a14b7ccaed7e02f71dc37c219b22be8",
                          "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu": "6a6404b2f6d34a94965684bfdb3e7d5295a65bc0"},
                  "dram_bytes": 258194688 + 237863424 + 287438592 + 5595904},
 }

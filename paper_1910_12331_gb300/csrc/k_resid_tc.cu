@@ -23,8 +23,10 @@
 //   stay below 2^23 units of that grid, so the FP32 accumulation of a level is
 //   exact.  Levels L = 2..7 (21 piece pairs) go to six TMEM accumulators; the
 //   pairs with s + t >= 8 and the remainders beyond the sixth piece are below
-//   2^-46 R sigma_i tau_k.  The epilogue adds the levels in double-float,
-//   subtracts from x (scaled by the same powers of two) and scales back.
+//   2^-46 R sigma_i tau_k.  The epilogue adds the levels in double-float (the
+//   FP32 additions of the small levels, |D_4| <~ 2^-16 R, round at most
+//   2^-40 R sigma_i tau_k), subtracts from x (scaled by the same powers of
+//   two) and scales back: error below 2^-39 R sigma_i tau_k in all.
 //
 // Kernel: persistent, one CTA per SM, 12 warps.  A run is (i-block b of 128
 // rows, slice m); a step is one 32-column chunk c of a run.

@@ -167,6 +167,19 @@ def test_gradient_is_jacobian_transpose_residual(orc, dims, R):
     np.testing.assert_allclose(gn, [np.linalg.norm(g) for g in cpref.unpack(ref, dims, R)], rtol=1e-12)
 
 
+@pytest.mark.parametrize("dims,R", [((9, 7, 8), 4), ((5, 4, 6, 3), 3), ((10, 12), 5)])
+def test_gradient_residual_form(orc, dims, R):
+    """Eq. (2.3)'s gradient in residual form: A^(n) Gamma^(n,n) - M^(n) equals
+    -MTTKRP(X - [[A]])^(n), because [[A]]_(n) P^(n) = A^(n) Gamma^(n,n)."""
+    A = _rand_factors(dims, R, 17)
+    X = _rand_tensor(dims, 17)
+    G, _ = orc.gradient(A, orc.gamma(orc.gram(A)), orc.mttkrp(X, A))
+    E = X - cpref.reconstruct(A)
+    ME = orc.mttkrp(E, A)
+    for g, me in zip(G, ME):
+        np.testing.assert_allclose(g, -me, rtol=1e-11, atol=1e-11 * np.abs(me).max())
+
+
 def test_gradient_finite_differences(orc):
     dims, R = (6, 5, 7), 3
     A = _rand_factors(dims, R, 8)
