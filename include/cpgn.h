@@ -61,13 +61,18 @@ typedef enum { CP_F32 = 0, CP_F64 = 1 } cp_dtype;
  *                  gradient, preconditioner, dot products, norms, alpha/beta
  *                  and the residual stay FP64. */
 /*  CP_PREC_RESIDUAL (gradient only: cp_gradient, cp_gn_step, cp_gn_solve)
- *                  G^(n) = -E_(n) P^(n) with E = X - [[A]] the residual tensor,
- *                  formed in double-float arithmetic (about 2^-44 relative),
- *                  split into bf16 planes and contracted by the bf16x3
- *                  tensor-core MTTKRP; M^(n) = A^(n) Gamma^(n,n) - G^(n).  This
- *                  is the same gradient as Algorithm 1's A Gamma - M, but its
- *                  error scales with |E| instead of |M|: the refinement used
- *                  by the mixed path once the bf16x3 gradient stalls. */
+ *                  G^(n) = -E_(n) P^(n) with E = X - [[A]] the residual tensor
+ *                  (Eq. (2.3) in residual form), split into bf16 planes and
+ *                  contracted by the bf16x3 tensor-core MTTKRP;
+ *                  M^(n) = A^(n) Gamma^(n,n) - G^(n).  E is reconstructed on
+ *                  the tensor cores by error-free bf16 slice products for
+ *                  R <= 64 (error below 2^-39 R sigma_i tau_k, sigma_i and
+ *                  tau_k the powers of two above the row maxima of the two
+ *                  product operands), else on the CUDA cores in extended FP32
+ *                  arithmetic.  The same gradient as Algorithm 1's A Gamma - M,
+ *                  but its error scales with |E| instead of |M|.  Used by the
+ *                  mixed path (with cg_fp32 = 1) on every iteration, or after
+ *                  the bf16x3 gradient stalls (cp_solve_opts.refine_below). */
 typedef enum { CP_PREC_FP64 = 0, CP_PREC_BF16X3 = 1, CP_PREC_RESIDUAL = 2 } cp_precision;
 
 typedef struct cp_handle_s* cp_handle;
