@@ -103,6 +103,18 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(value, pg, device):
+    """The largest value over the ranks of the process group (the job's time is
+    the slowest replica's), or the value itself without a group."""
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """Samples nvidia-smi SM clocks and throttle reasons while running."""
 
@@ -406,10 +418,7 @@ def main():
         i1 = clk.mark()
     t_total = e0.elapsed_time(e1) / 1e3
     t_step = t_total / args.steps
-    if pg:
-        tt = torch.tensor([t_step], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(t_step, pg, dev)
     last = results[-1]
     converged = all(r["converged"] for r in results)
 
