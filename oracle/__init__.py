@@ -17,10 +17,13 @@ Parity status of each routine (pins live in ``tests/test_oracle_pins.py``):
                         closed form, zero gradient at an exact decomposition,
                         Strassen and classical matmul-tensor decompositions)
   gradient              pinned (explicit Jacobian J^T r, finite differences)
-  precond_inv           pinned ((Gamma + lam I) P_inv = I)
-  matvec                pinned (explicit Jacobian (J^T J + lam I) v, null
-                        directions of the scaling indeterminacy)
-  pcg                   pinned (dense solve of the explicit normal equations)
+  precond_inv           pinned ((Gamma + lam D) P_inv = I, D = I or diag(Gamma))
+  matvec                pinned (explicit Jacobian (J^T J + lam D) v with
+                        D = I or diag(J^T J), null directions of the scaling
+                        indeterminacy)
+  pcg                   pinned (dense solve of the explicit normal equations,
+                        both dampings; with diag(J^T J) the step commutes with
+                        the column rescaling of the CP model)
   lambda_next           pinned (hand-derived sequence, golden fixture)
   gn_step               pinned (exact recovery of exact-rank tensors)
   residual              pinned (numpy reconstruction, zero at exact factors)
@@ -45,6 +48,8 @@ _lib = None
 
 MAXN = 8
 OK, ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, WARN_CG_MAXIT = 0, 1, 5, 7, 9
+# damping of the CG system (Section 3.2): lam I or lam diag(J^T J)
+REG_IDENTITY, REG_DIAG = 0, 1
 
 
 class _Desc(ctypes.Structure):
@@ -75,17 +80,17 @@ def _load():
             lib.orc_mttkrp_dt.argtypes = [d, dp, dp, dp]
             lib.orc_mttkrp_row.argtypes = [d, dp, dp, ctypes.c_int, ctypes.c_int64, dp]
             lib.orc_gradient.argtypes = [d, dp, dp, dp, dp, dp]
-            lib.orc_precond_inv.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp]
+            lib.orc_precond_inv.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, dp]
             lib.orc_precond_inv.restype = ctypes.c_int
-            lib.orc_matvec.argtypes = [d, dp, dp, dp, ctypes.c_double, dp]
-            lib.orc_pcg.argtypes = [d, dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+            lib.orc_matvec.argtypes = [d, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp]
+            lib.orc_pcg.argtypes = [d, dp, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, dp, P(ctypes.c_int), dp]
             lib.orc_pcg.restype = ctypes.c_int
             lib.orc_lambda_next.argtypes = [dp, P(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double]
             lib.orc_gn_step.argtypes = [d, dp, dp, dp, P(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_int, dp]
+                                        ctypes.c_int, ctypes.c_int, dp]
             lib.orc_gn_step.restype = ctypes.c_int
             lib.orc_residual.argtypes = [d, dp, dp]
             lib.orc_residual.restype = ctypes.c_double
@@ -171,28 +176,29 @@ def gradient(A, Gam, M):
     return _unpack(Gbuf, dims, R), gn[:len(dims)].copy()
 
 
-def precond_inv(Gnn, lam):
+def precond_inv(Gnn, lam, reg: int = REG_IDENTITY):
     R = Gnn.shape[0]
     P = np.zeros((R, R))
-    st = _load().orc_precond_inv(R, _ptr(np.ascontiguousarray(Gnn, dtype=np.float64)), float(lam), _ptr(P))
+    st = _load().orc_precond_inv(R, _ptr(np.ascontiguousarray(Gnn, dtype=np.float64)), float(lam), int(reg),
+                                 _ptr(P))
     return P, st
 
 
-def matvec(A, Gam, W, lam):
+def matvec(A, Gam, W, lam, reg: int = REG_IDENTITY):
     dims, R = [a.shape[0] for a in A], A[0].shape[1]
     Q = np.zeros(sum(dims) * R)
     _load().orc_matvec(ctypes.byref(_desc(dims, R)), _ptr(_pack(A)), _ptr(np.ascontiguousarray(Gam)),
-                       _ptr(_pack(W)), float(lam), _ptr(Q))
+                       _ptr(_pack(W)), float(lam), int(reg), _ptr(Q))
     return _unpack(Q, dims, R)
 
 
-def pcg(A, Gam, G, lam, eps_cg, maxit, beta_kind: int = 0):
+def pcg(A, Gam, G, lam, eps_cg, maxit, beta_kind: int = 0, reg: int = REG_IDENTITY):
     dims, R = [a.shape[0] for a in A], A[0].shape[1]
     V = np.zeros(sum(dims) * R)
     it = ctypes.c_int(0)
     rn = np.zeros(1)
     st = _load().orc_pcg(ctypes.byref(_desc(dims, R)), _ptr(_pack(A)), _ptr(np.ascontiguousarray(Gam)),
-                         _ptr(_pack(G)), float(lam), float(eps_cg), int(maxit), int(beta_kind), _ptr(V),
+                         _ptr(_pack(G)), float(lam), int(reg), float(eps_cg), int(maxit), int(beta_kind), _ptr(V),
                          ctypes.byref(it), _ptr(rn))
     return _unpack(V, dims, R), it.value, float(rn[0]), st
 
@@ -204,7 +210,8 @@ def lambda_next(lam, direction, lo, hi, mu):
     return float(l[0]), dr.value
 
 
-def gn_step(X, A, lam, direction, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind=0, use_dt=False):
+def gn_step(X, A, lam, direction, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind=0, use_dt=False,
+            reg=REG_IDENTITY):
     """One CP-GN iteration (Algorithm 1).  Returns (A_new, lam, dir, stats, status);
     stats = dict(grad_norm_sum, update_norm_sum, lam_used, cg_iters, cg_rnorm, m_norm_sum)."""
     X = _x64(X)
@@ -215,7 +222,7 @@ def gn_step(X, A, lam, direction, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind=0
     stats = np.zeros(6)
     st = _load().orc_gn_step(ctypes.byref(_desc(dims, R)), _ptr(X), _ptr(Abuf), _ptr(l), ctypes.byref(dr),
                              float(lam_lo), float(lam_hi), float(mu), float(eps_cg), int(maxit),
-                             int(beta_kind), int(bool(use_dt)), _ptr(stats))
+                             int(beta_kind), int(bool(use_dt)), int(reg), _ptr(stats))
     keys = ("grad_norm_sum", "update_norm_sum", "lam_used", "cg_iters", "cg_rnorm", "m_norm_sum")
     s = dict(zip(keys, stats.tolist()))
     s["cg_iters"] = int(s["cg_iters"])

@@ -29,6 +29,8 @@
 #define ORC_MAXN 8
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_NOT_SPD = 5, ORC_ERR_BREAKDOWN = 7, ORC_WARN_CG_MAXIT = 9 };
+/* damping of the CG system (Section 3.2) */
+enum { ORC_REG_IDENTITY = 0, ORC_REG_DIAG = 1 };
 
 typedef struct {
     int N;                   /* tensor order */
@@ -283,15 +285,24 @@ void orc_gradient(const orc_desc* d, const double* A, const double* Gam, const d
 
 /* ----------------------------------------------------------- preconditioner */
 
-/* P_inv = (Gamma^(n,n) + lam I)^{-1}  (Algorithm 2, first loop; Section 3.3):
- * Cholesky factorisation B = L L^T, then the explicit inverse by forward and
- * back substitution against the identity.  Returns ORC_ERR_NOT_SPD on a
- * non-positive pivot. */
-int orc_precond_inv(int R, const double* Gnn, double lam, double* Pinv) {
+/* Damping of the normal equations (Section 3.2).  reg = ORC_REG_IDENTITY:
+ * J^T J + lam I.  reg = ORC_REG_DIAG: J^T J + lam diag(J^T J); the diagonal
+ * of the block (n,n) = Gamma^(n,n) (x) I of Eq. (3.2) holds Gamma^(n,n)_{rr}
+ * at every row of column r, so the damping of entry (i, r) of mode n is
+ * lam * Gamma^(n,n)_{rr}. */
+static double damping(int reg, const double* Gnn, int R, int r) {
+    return reg == ORC_REG_DIAG ? Gnn[r * R + r] : 1.0;
+}
+
+/* P_inv = (Gamma^(n,n) + lam D)^{-1}  (Algorithm 2, first loop; Section 3.3),
+ * D = I or diag(Gamma^(n,n)) by reg: Cholesky factorisation B = L L^T, then
+ * the explicit inverse by forward and back substitution against the identity.
+ * Returns ORC_ERR_NOT_SPD on a non-positive pivot. */
+int orc_precond_inv(int R, const double* Gnn, double lam, int reg, double* Pinv) {
     double* L = (double*)calloc((size_t)R * R, sizeof(double));
     double* Y = (double*)calloc((size_t)R * R, sizeof(double));
     for (int j = 0; j < R; ++j) {
-        double diag = Gnn[j * R + j] + lam;
+        double diag = Gnn[j * R + j] + lam * damping(reg, Gnn, R, j);
         for (int k = 0; k < j; ++k) diag -= L[j * R + k] * L[j * R + k];
         if (!(diag > 0.0)) { free(L); free(Y); return ORC_ERR_NOT_SPD; }
         const double ljj = sqrt(diag);
@@ -321,14 +332,15 @@ int orc_precond_inv(int R, const double* Gnn, double lam, double* Pinv) {
 
 /* ------------------------------------------------------------------ matvec */
 
-/* Q^(n) = lam W^(n) + sum_p MatVec(A^(n), A^(p), Gamma^(n,p), W^(p))
- * (Algorithm 2, matvec line; Eq. (3.4)):
+/* Q^(n) = lam D W^(n) + sum_p MatVec(A^(n), A^(p), Gamma^(n,p), W^(p))
+ * (Algorithm 2, matvec line; Eq. (3.4)), D the damping chosen by reg
+ * (entry (k, r) of the damping term: lam * damping(reg, Gamma^(n,n), R, r) * w^(n)_{kr}):
  *   p = n : sum_z Gamma^(n,n)_{rz} w^(n)_{kz}
  *   p != n: sum_{l,z} a^(n)_{kz} a^(p)_{lr} Gamma^(n,p)_{rz} w^(p)_{lz}
  * The off-diagonal 4-index sum is evaluated in the order that gives the
  * O(N^2 s R^2) cost the paper states after Eq. (3.4): first
  * Y^(p)_{rz} = sum_l a^(p)_{lr} w^(p)_{lz}, then sum_z a^(n)_{kz} Gamma^(n,p)_{rz} Y^(p)_{rz}. */
-void orc_matvec(const orc_desc* d, const double* A, const double* Gam, const double* W, double lam,
+void orc_matvec(const orc_desc* d, const double* A, const double* Gam, const double* W, double lam, int reg,
                 double* Q) {
     const int N = d->N, R = d->R;
     double* Y = (double*)malloc(sizeof(double) * (size_t)N * R * R);
@@ -346,9 +358,10 @@ void orc_matvec(const orc_desc* d, const double* A, const double* Gam, const dou
         const double* An = A + factor_offset(d, n);
         const double* Wn = W + factor_offset(d, n);
         double* Qn = Q + factor_offset(d, n);
+        const double* Gnn = Gam + ((int64_t)n * N + n) * R * R;
         for (int64_t k = 0; k < d->dims[n]; ++k)
             for (int r = 0; r < R; ++r) {
-                double acc = lam * Wn[k * R + r];
+                double acc = lam * damping(reg, Gnn, R, r) * Wn[k * R + r];
                 for (int p = 0; p < N; ++p) {
                     const double* Gnp = Gam + ((int64_t)n * N + p) * R * R;
                     if (p == n) {
@@ -400,13 +413,13 @@ static void apply_precond(const orc_desc* d, const double* Pinv, const double* R
 }
 
 /* CP-CG, Algorithm 2: block-Jacobi (Kronecker) preconditioned CG on
- * (J^T J + lam I) V = -G.
+ * (J^T J + lam D) V = -G, D = I or diag(J^T J) by reg.
  * beta_kind = 0: standard PCG, beta = <R,Z>_new / <R,Z>_old.
  * beta_kind = 1: the ratio as printed in Algorithm 2, <R,Z>_new / <W,Q>.
  * Stop test at the loop head: sum_n ||R^(n)||_F <= eps_cg sum_n ||G^(n)||_F, or
  * maxit iterations.  Returns ORC_OK, ORC_WARN_CG_MAXIT, ORC_ERR_NOT_SPD or
  * ORC_ERR_BREAKDOWN (<W,Q> <= 0). */
-int orc_pcg(const orc_desc* d, const double* A, const double* Gam, const double* G, double lam,
+int orc_pcg(const orc_desc* d, const double* A, const double* Gam, const double* G, double lam, int reg,
             double eps_cg, int maxit, int beta_kind, double* V, int* iters_out, double* rnorm_out) {
     const int N = d->N, R = d->R;
     const int64_t len = factor_total(d);
@@ -417,7 +430,7 @@ int orc_pcg(const orc_desc* d, const double* A, const double* Gam, const double*
     double* Q = (double*)malloc(sizeof(double) * len);
     int status = ORC_OK;
     for (int n = 0; n < N; ++n) {
-        status = orc_precond_inv(R, Gam + ((int64_t)n * N + n) * R * R, lam, Pinv + (int64_t)n * R * R);
+        status = orc_precond_inv(R, Gam + ((int64_t)n * N + n) * R * R, lam, reg, Pinv + (int64_t)n * R * R);
         if (status != ORC_OK) goto done;
     }
     for (int64_t i = 0; i < len; ++i) { V[i] = 0.0; Rv[i] = -G[i]; }
@@ -429,7 +442,7 @@ int orc_pcg(const orc_desc* d, const double* A, const double* Gam, const double*
     double rsum = fro_sum(d, Rv);
     while (rsum > eps_cg * gsum) {
         if (it >= maxit) { status = ORC_WARN_CG_MAXIT; break; }
-        orc_matvec(d, A, Gam, W, lam, Q);
+        orc_matvec(d, A, Gam, W, lam, reg, Q);
         const double wq = dot_all(len, W, Q);
         if (!(wq > 0.0)) { status = ORC_ERR_BREAKDOWN; break; }
         const double alpha = rz / wq;
@@ -475,9 +488,10 @@ void orc_lambda_next(double* lam, int* dir, double lo, double hi, double mu) {
  * stats[0] = sum_n ||G^(n)||_F at the entry point, stats[1] = sum_n ||V^(n)||_F,
  * stats[2] = lambda used, stats[3] = CG iterations, stats[4] = final CG
  * residual sum, stats[5] = sum_n ||M^(n)||_F.
- * use_dt selects the dimension-tree MTTKRP (1) or the definition (0). */
+ * use_dt selects the dimension-tree MTTKRP (1) or the definition (0); reg the
+ * damping of the CG system (ORC_REG_IDENTITY or ORC_REG_DIAG). */
 int orc_gn_step(const orc_desc* d, const double* X, double* A, double* lam, int* dir, double lam_lo,
-                double lam_hi, double mu, double eps_cg, int maxit, int beta_kind, int use_dt,
+                double lam_hi, double mu, double eps_cg, int maxit, int beta_kind, int use_dt, int reg,
                 double* stats) {
     const int N = d->N, R = d->R;
     const int64_t len = factor_total(d);
@@ -496,7 +510,7 @@ int orc_gn_step(const orc_desc* d, const double* X, double* A, double* lam, int*
     int iters = 0;
     double rnorm = 0.0;
     const double lam_used = *lam;
-    int status = orc_pcg(d, A, Gam, G, lam_used, eps_cg, maxit, beta_kind, V, &iters, &rnorm);
+    int status = orc_pcg(d, A, Gam, G, lam_used, reg, eps_cg, maxit, beta_kind, V, &iters, &rnorm);
     if (status == ORC_OK || status == ORC_WARN_CG_MAXIT) {
         for (int64_t i = 0; i < len; ++i) A[i] += V[i];
         orc_lambda_next(lam, dir, lam_lo, lam_hi, mu);
@@ -567,7 +581,7 @@ int orc_als_sweep(const orc_desc* d, const double* X, double* A, double lam) {
         double* Mn = (double*)malloc(sizeof(double) * sn * R);
 #pragma omp parallel for
         for (int64_t i = 0; i < sn; ++i) orc_mttkrp_row(d, X, A, n, i, Mn + i * R);
-        status = orc_precond_inv(R, Gam + ((int64_t)n * N + n) * R * R, lam, Pinv);
+        status = orc_precond_inv(R, Gam + ((int64_t)n * N + n) * R * R, lam, ORC_REG_IDENTITY, Pinv);
         if (status == ORC_OK) {
             double* An = A + factor_offset(d, n);
             for (int64_t i = 0; i < sn; ++i)

@@ -327,6 +327,84 @@ def test_pcg_printed_beta_differs(orc):
     assert max(np.abs(a - b).max() for a, b in zip(Vs, Vp)) > 1e-6
 
 
+# ------------------------------------------------- diagonal damping (Section 3.2)
+
+def _diag_damping(J):
+    return np.diag(np.diag(J.T @ J))
+
+
+@pytest.mark.parametrize("dims,R", [((6, 5, 7), 3), ((4, 3, 5, 2), 3), ((5, 6), 2)])
+def test_matvec_diag_damping_explicit_jacobian(orc, dims, R):
+    """Q = (J^T J + lam diag(J^T J)) w with J formed explicitly (Eq. (3.1))."""
+    A = _rand_factors(dims, R, 41)
+    W = _rand_factors(dims, R, 42)
+    Gam = orc.gamma(orc.gram(A))
+    J = cpref.jacobian(A)
+    w = cpref.pack(W)
+    lam = 0.37
+    ref = J.T @ (J @ w) + lam * (_diag_damping(J) @ w)
+    got = cpref.pack(orc.matvec(A, Gam, W, lam, orc.REG_DIAG))
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # the two dampings differ exactly by lam (diag(J^T J) - I) w
+    ident = cpref.pack(orc.matvec(A, Gam, W, lam, orc.REG_IDENTITY))
+    np.testing.assert_allclose(got - ident, lam * (_diag_damping(J) - np.eye(len(w))) @ w, rtol=1e-10,
+                               atol=1e-12 * np.abs(ref).max())
+
+
+def test_precond_diag_damping(orc):
+    A = _rand_factors((9, 8, 7), 5, 43)
+    Gam = orc.gamma(orc.gram(A))
+    B = Gam[1, 1]
+    for lam in (0.0, 1e-3, 10.0):
+        P, st = orc.precond_inv(B, lam, orc.REG_DIAG)
+        assert st == orc.OK
+        np.testing.assert_allclose((B + lam * np.diag(np.diag(B))) @ P, np.eye(5), atol=1e-12)
+    # an indefinite matrix stays rejected
+    _, st = orc.precond_inv(np.array([[1.0, 2.0], [2.0, 1.0]]), 0.5, orc.REG_DIAG)
+    assert st == orc.ERR_NOT_SPD
+
+
+@pytest.mark.parametrize("dims,R,lam", [((5, 4, 6), 3, 1e-2), ((4, 3, 3, 2), 2, 0.5)])
+def test_pcg_diag_damping_solves_normal_equations(orc, dims, R, lam):
+    A = _rand_factors(dims, R, 44)
+    X = _rand_tensor(dims, 44)
+    Gam = orc.gamma(orc.gram(A))
+    G, _ = orc.gradient(A, Gam, orc.mttkrp(X, A))
+    V, _, _, st = orc.pcg(A, Gam, G, lam, 1e-13, 10000, 0, orc.REG_DIAG)
+    assert st == orc.OK
+    J = cpref.jacobian(A)
+    ref = np.linalg.solve(J.T @ J + lam * _diag_damping(J), -cpref.pack(G))
+    np.testing.assert_allclose(cpref.pack(V), ref, rtol=1e-8, atol=1e-9 * np.abs(ref).max())
+
+
+def test_gn_step_diag_damping_commutes_with_column_scaling(orc):
+    """The CP model is unchanged by A^(1) c, A^(2) / c (column scaling, Section
+    3.2).  The map is linear in the unknowns, J(phi(A)) = J(A) S^-1, so the
+    system damped by diag(J^T J), its block-Jacobi preconditioner and every CG
+    iterate transform covariantly: a GN step from the rescaled point is the
+    rescaled GN step.  Damping by lam I breaks this."""
+    dims, R = (7, 6, 5), 3
+    A = _rand_factors(dims, R, 45)
+    X = _rand_tensor(dims, 45)
+    c = np.array([3.0, 0.7, 1.9])
+    Ac = [A[0] * c, A[1] / c, A[2].copy()]
+    np.testing.assert_allclose(cpref.reconstruct(Ac), cpref.reconstruct(A), rtol=1e-12, atol=1e-12)
+
+    def step(F, reg):
+        out, _, _, _, st = orc.gn_step(X, F, 0.05, 0, 1e-3, 1.0, 2.0, 0.0, 6, reg=reg)
+        assert st == orc.WARN_CG_MAXIT
+        return out
+
+    new = step(A, orc.REG_DIAG)
+    newc = step(Ac, orc.REG_DIAG)
+    for got, ref in zip(newc, [new[0] * c, new[1] / c, new[2]]):
+        np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-10 * np.abs(ref).max())
+    new = step(A, orc.REG_IDENTITY)
+    newc = step(Ac, orc.REG_IDENTITY)
+    dev = max(np.abs(g - r).max() / np.abs(r).max() for g, r in zip(newc, [new[0] * c, new[1] / c, new[2]]))
+    assert dev > 1e-4
+
+
 # ------------------------------------------------------------------ lambda rule
 
 def test_lambda_schedule_golden(orc):
