@@ -85,6 +85,16 @@ typedef struct {
     uint64_t x_version;            /* bump when the contents of X change (split cache key) */
 } cp_desc;
 
+/* Damping of the Gauss-Newton system (Section 3.2).  CP_REG_IDENTITY solves
+ * (J^T J + lam I) v = -g, the Levenberg-Marquardt form the paper uses with its
+ * varying lam.  CP_REG_DIAG solves (J^T J + lam diag(J^T J)) v = -g, the
+ * scale-invariant alternative the same section discusses: the diagonal of the
+ * block (n,n) = Gamma^(n,n) (x) I of J^T J (Eq. (3.2)), so entry (i, r) of mode
+ * n is damped by lam * Gamma^(n,n)_{rr}, in the matvec and in the
+ * preconditioner (Gamma^(n,n) + lam diag(Gamma^(n,n)))^{-1}; lam is then
+ * dimensionless. */
+typedef enum { CP_REG_IDENTITY = 0, CP_REG_DIAG = 1 } cp_reg;
+
 /* Parameters of one Gauss-Newton step (Algorithm 1) and its CG solve
  * (Algorithm 2).  lam / lam_dir are in/out: cp_gn_step uses lam for this
  * step and then advances it by the varying rule of Section 3.2. */
@@ -97,6 +107,8 @@ typedef struct {
     double mu;            /* factor mu > 1 of the varying rule */
     int lam_dir;          /* 0: decreasing, 1: increasing (in/out) */
     int lam_fixed;        /* 1: keep lam constant (constant regularisation) */
+    int reg;              /* cp_reg: damping lam I (0, default) or lam diag(J^T J) (1); other
+                             values are CP_ERR_ARG */
     cp_precision prec;    /* MTTKRP arithmetic */
     int cg_fp32;          /* 1: CG vectors and the matvec in FP32 (dot products, norms, alpha,
                              beta stay FP64); 0: FP64 */

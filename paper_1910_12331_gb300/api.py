@@ -22,6 +22,8 @@ CP_ERR_NOT_SPD, CP_ERR_NONFINITE, CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT, CP_WARN_CG_M
 CP_F32, CP_F64 = 0, 1
 CP_PREC_FP64, CP_PREC_BF16X3, CP_PREC_RESIDUAL = 0, 1, 2
 PREC = {"fp64": CP_PREC_FP64, "bf16x3": CP_PREC_BF16X3, "residual": CP_PREC_RESIDUAL}
+CP_REG_IDENTITY, CP_REG_DIAG = 0, 1
+REG = {"identity": CP_REG_IDENTITY, "diag": CP_REG_DIAG}
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
@@ -38,7 +40,7 @@ class cp_desc(ctypes.Structure):
 class cp_gn_params(ctypes.Structure):
     _fields_ = [("eps_cg", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("lam", ctypes.c_double),
                 ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double), ("mu", ctypes.c_double),
-                ("lam_dir", ctypes.c_int), ("lam_fixed", ctypes.c_int), ("prec", ctypes.c_int),
+                ("lam_dir", ctypes.c_int), ("lam_fixed", ctypes.c_int), ("reg", ctypes.c_int), ("prec", ctypes.c_int),
                 ("cg_fp32", ctypes.c_int), ("want_residual", ctypes.c_int),
                 ("stop_stationarity", ctypes.c_double), ("spin_limit", ctypes.c_int64)]
 
@@ -276,11 +278,15 @@ def cp_gn_matvec(h: Handle, A, W, lam, Q=None):
 
 
 def gn_params(lam, lam_lo, lam_hi, mu=2.0, eps_cg=1e-3, cg_max_iter=250, prec="fp64", cg_fp32=None,
-              lam_dir=0, lam_fixed=False, want_residual=False, stop_stationarity=0.0, spin_limit=0):
+              lam_dir=0, lam_fixed=False, want_residual=False, stop_stationarity=0.0, spin_limit=0,
+              reg="identity"):
+    """reg: "identity" damps by lam I, "diag" by lam diag(J^T J) (then lam is
+    dimensionless)."""
     p = cp_gn_params()
     p.eps_cg, p.cg_max_iter = float(eps_cg), int(cg_max_iter)
     p.lam, p.lam_lo, p.lam_hi, p.mu = float(lam), float(lam_lo), float(lam_hi), float(mu)
     p.lam_dir, p.lam_fixed = int(lam_dir), int(bool(lam_fixed))
+    p.reg = REG[reg]
     p.prec = PREC[prec]
     p.cg_fp32 = int(prec in ("bf16x3", "residual")) if cg_fp32 is None else int(bool(cg_fp32))
     p.want_residual = int(bool(want_residual))

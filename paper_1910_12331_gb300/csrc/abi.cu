@@ -426,15 +426,23 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
     launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
                     (double*)h->grad_part.p, ds, h->stream, p->prec == CP_PREC_RESIDUAL);
     h->launches += 1;  // the fixed-order norm reduction
+    // Damping lam diag(J^T J): fold it into the diagonals of Gamma^(n,n) (the
+    // gradient above used them undamped) and solve the system with lam = 0.
+    cp_gn_params q = *p;
+    if (p->reg == CP_REG_DIAG) {
+        launch_damp_diag(s, (double*)h->Gam.p, (float*)h->GamF.p, p->lam, h->stream);
+        h->launches += 1;
+        q.lam = 0.0;
+    }
     // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
-    launch_precond(s, (const double*)h->Gam.p, p->lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
+    launch_precond(s, (const double*)h->Gam.p, q.lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
                    (double*)h->precond_scratch.p, ds, h->stream, p->cg_fp32 != 0);
     h->launches += 2;
     CUDA_TRY(cudaGetLastError());
     if (p->cg_fp32)
-        CP_TRY(gn_pcg<float>(h, s, Ac, p));
+        CP_TRY(gn_pcg<float>(h, s, Ac, &q));
     else
-        CP_TRY(gn_pcg<double>(h, s, Ac, p));
+        CP_TRY(gn_pcg<double>(h, s, Ac, &q));
     h->launches += 2;  // pack + persistent CG
     // A^(n) += V^(n)
     Ptrs<double> Am = ptrs_of(A, s.N);
@@ -485,6 +493,7 @@ static cp_status check_params(const cp_gn_params* p) {
     if (!p) return CP_ERR_ARG;
     if (!(p->eps_cg >= 0.0) || p->cg_max_iter < 0) return CP_ERR_ARG;
     if (!(p->lam >= 0.0) || !isfinite(p->lam)) return CP_ERR_ARG;
+    if (p->reg != CP_REG_IDENTITY && p->reg != CP_REG_DIAG) return CP_ERR_ARG;
     if (!p->lam_fixed && !(p->mu > 1.0 && p->lam_lo > 0.0 && p->lam_hi >= p->lam_lo)) return CP_ERR_ARG;
     if (p->prec != CP_PREC_FP64 && p->prec != CP_PREC_BF16X3 && p->prec != CP_PREC_RESIDUAL) return CP_ERR_ARG;
     return CP_OK;

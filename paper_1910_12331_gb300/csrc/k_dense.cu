@@ -107,6 +107,30 @@ void launch_gamma(const Shape& s, const double* part, int chunks, double* S, dou
     gamma_kernel<<<(RR + 255) / 256, 256, 0, st>>>(s, part, chunks, S, Gam, GamF);
 }
 
+// ------------------------------------------------------ diagonal damping
+// Damping by lam diag(J^T J) (Section 3.2): the diagonal of the block (n,n) of
+// J^T J is Gamma^(n,n)_{rr} at every row of column r, so the damped system is
+// the undamped one with each Gamma^(n,n)_{rr} replaced by
+// Gamma^(n,n)_{rr} + lam Gamma^(n,n)_{rr}.  Rewrites those N R entries of the
+// FP64 Gamma and of its FP32 copy (which may be null); the preconditioner and
+// the CG matvec then run with lam = 0.  One thread per (n, r).
+__global__ void damp_diag_kernel(Shape s, double* Gam, float* GamF, double lam) {
+    const int R = s.R;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= s.N * R) return;
+    const int n = t / R, r = t - n * R;
+    const int64_t e = ((int64_t)n * s.N + n) * R * R + (int64_t)r * R + r;
+    const double g = Gam[e];
+    const double v = g + lam * g;
+    Gam[e] = v;
+    if (GamF) GamF[e] = (float)v;
+}
+
+void launch_damp_diag(const Shape& s, double* Gam, float* GamF, double lam, cudaStream_t st) {
+    const int nr = s.N * s.R;
+    damp_diag_kernel<<<(nr + 127) / 128, 128, 0, st>>>(s, Gam, GamF, lam);
+}
+
 // -------------------------------------------------------------- gradient
 // One thread per (row, column) of the packed gradient.  Each block writes its
 // partial ||G||^2 and ||M||^2 to part[n][block]; grad_norms_kernel adds them in

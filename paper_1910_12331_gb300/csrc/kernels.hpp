@@ -24,6 +24,9 @@ void launch_gamma(const Shape& s, const double* part, int chunks, double* S, dou
 void launch_gradient(const Shape& s, Ptrs<const double> A, const double* Gam, const double* M, double* G,
                      double* part, DevStats* stats, cudaStream_t st, bool resid);
 size_t gradient_part_doubles(const Shape& s);
+// Damping by lam diag(J^T J): Gamma^(n,n)_{rr} += lam Gamma^(n,n)_{rr} in Gam
+// and GamF (may be null); the system is then solved with lam = 0.
+void launch_damp_diag(const Shape& s, double* Gam, float* GamF, double lam, cudaStream_t st);
 // Pinv[n] = (Gam[n][n] + lam I)^{-1} (FP64 Cholesky + inverse); PinvF float copy (may be null).
 // scratch: precond_scratch_doubles(s) doubles, used only when precond_smem_bytes(R) == 0.
 // fp32: the FP32 factorisation with clamped pivots (writes PinvF only).

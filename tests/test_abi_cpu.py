@@ -106,3 +106,27 @@ int main(void) {
     mine = [ctypes.sizeof(c) for c in (api.cp_desc, api.cp_gn_params, api.cp_gn_stats, api.cp_solve_opts,
                                        api.cp_solve_result, api.cp_batch_problem, api.cp_batch_result)]
     assert sizes == mine
+
+
+def test_struct_field_offsets_match_header():
+    """Every field of every ctypes mirror sits at the C offset of the header's
+    field of the same name (offsetof, compiled with gcc)."""
+    import subprocess
+    import tempfile
+
+    from paper_1910_12331_gb300 import api
+
+    structs = (api.cp_desc, api.cp_gn_params, api.cp_gn_stats, api.cp_solve_opts, api.cp_solve_result,
+               api.cp_batch_problem, api.cp_batch_result)
+    lines = [f'  printf("%zu\\n", offsetof({c.__name__}, {f}));' for c in structs for f, _ in c._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"cpgn.h\"\nint main(void) {\n" + \
+        "\n".join(lines) + "\n  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "o.c"), os.path.join(d, "o")
+        open(src, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        offs = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
+    mine = [getattr(c, f).offset for c in structs for f, _ in c._fields_]
+    names = [f"{c.__name__}.{f}" for c in structs for f, _ in c._fields_]
+    assert [n for n, a, b in zip(names, offs, mine) if a != b] == []
+    assert len(offs) == len(mine)

@@ -146,6 +146,75 @@ def test_gn_step_fixed_cg_fp32(env, orc, dims, R, k):
     assert _relerr(d_gpu, d_orc) <= 1e-4
 
 
+@pytest.mark.parametrize("dims,R,k", [((20, 20, 20), 5, 5), ((6, 5, 4, 7), 4, 7), ((37, 70, 45), 9, 4),
+                                      ((8, 6), 3, 3), ((130, 3, 97), 9, 3)])
+def test_gn_step_diag_damping(env, orc, dims, R, k):
+    """Damping by lam diag(J^T J) (Section 3.2): one FP64 GN step with k CG
+    iterations against the oracle's step with the same damping."""
+    torch, api, h = env
+    A = _factors(dims, R, 16)
+    X = _tensor(dims, 16)
+    lam, lo, hi = 0.05, 1e-7, 0.1
+    Ad = _dev(torch, A)
+    params = api.gn_params(lam, lo, hi, eps_cg=0.0, cg_max_iter=k, reg="diag")
+    s, st = api.cp_gn_step(h, torch.from_numpy(X).cuda(), Ad, params)
+    Ao, lam_o, dir_o, so, sto = orc.gn_step(X, A, lam, 0, lo, hi, 2.0, 0.0, k, reg=orc.REG_DIAG)
+    assert st["cg_iters"] == so["cg_iters"] == k
+    assert s == sto == api.CP_WARN_CG_MAXIT
+    got = [a.cpu().numpy() for a in Ad]
+    assert _relerr(got, Ao) <= 1e-11
+    assert st["lam_used"] == lam and params.lam == lam_o and params.lam_dir == dir_o
+    # the damping option is honoured: lam I gives another step
+    Ai, _, _, _, _ = orc.gn_step(X, A, lam, 0, lo, hi, 2.0, 0.0, k)
+    assert _relerr(got, Ai) > 1e-6
+
+
+@pytest.mark.parametrize("dims,R,k", [((20, 20, 20), 5, 5), ((150, 120, 90), 12, 6)])
+def test_gn_step_diag_damping_cg_fp32(env, orc, dims, R, k):
+    """The same with FP32 CG vectors; tolerance as for the FP32 CG step with
+    lam I (the damped system at lam = 0.1 is as well conditioned)."""
+    torch, api, h = env
+    A = _factors(dims, R, 17)
+    X = _tensor(dims, 17)
+    lam, lo, hi = 0.1, 1e-7, 0.1
+    Ad = _dev(torch, A)
+    params = api.gn_params(lam, lo, hi, eps_cg=0.0, cg_max_iter=k, cg_fp32=True, reg="diag")
+    s, st = api.cp_gn_step(h, torch.from_numpy(X).cuda(), Ad, params)
+    Ao, _, _, so, sto = orc.gn_step(X, A, lam, 0, lo, hi, 2.0, 0.0, k, reg=orc.REG_DIAG)
+    assert st["cg_iters"] == so["cg_iters"] == k
+    assert s == sto == api.CP_WARN_CG_MAXIT
+    d_gpu = [a.cpu().numpy() - a0 for a, a0 in zip(Ad, A)]
+    d_orc = [a - a0 for a, a0 in zip(Ao, A)]
+    assert _relerr(d_gpu, d_orc) <= 1e-4
+
+
+def test_gn_step_damping_kind_rejected(env):
+    torch, api, h = env
+    A = _factors((5, 6, 7), 2, 18)
+    X = torch.from_numpy(_tensor((5, 6, 7), 18)).cuda()
+    Ad = _dev(torch, A)
+    params = api.gn_params(0.1, 1e-7, 0.1)
+    params.reg = 2
+    s, _ = api.cp_gn_step(h, X, Ad, params, check=False)
+    assert s == api.CP_ERR_ARG
+    np.testing.assert_array_equal(Ad[0].cpu().numpy(), A[0])  # nothing ran
+
+
+def test_gn_solve_diag_damping_recovery(env, orc):
+    """Algorithm 1 with the varying lam applied to lam diag(J^T J) (lam between
+    1e-7 and 0.1, dimensionless) recovers the 20^3 rank-5 exact decompositions."""
+    torch, api, h = env
+    from paper_1910_12331_gb300 import datagen
+
+    for seed in range(4):
+        p = datagen.workload("exact20", seed=seed)
+        Ad = _dev(torch, p["init"])
+        params = api.gn_params(0.1, 1e-7, 0.1, reg="diag")
+        opts = api.solve_opts(max_iters=100, target_residual=1e-10)
+        _, res = api.cp_gn_solve(h, torch.from_numpy(p["X"]).cuda(), Ad, params, opts)
+        assert res["converged"] == 1 and res["rel_residual"] <= 1e-10
+
+
 def test_gn_step_tolerance_stop(env, orc):
     torch, api, h = env
     from paper_1910_12331_gb300 import datagen

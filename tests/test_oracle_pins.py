@@ -377,6 +377,31 @@ def test_pcg_diag_damping_solves_normal_equations(orc, dims, R, lam):
     np.testing.assert_allclose(cpref.pack(V), ref, rtol=1e-8, atol=1e-9 * np.abs(ref).max())
 
 
+def test_diag_damping_is_folded_gamma_diagonal(orc):
+    """lam diag(J^T J) touches only the diagonal of each Gamma^(n,n): the damped
+    preconditioner, matvec and CG equal the undamped ones (lam = 0) on Gamma
+    with Gamma^(n,n)_{rr} replaced by (1 + lam) Gamma^(n,n)_{rr}, the form in
+    which the library applies it."""
+    dims, R, lam = (6, 7, 5, 4), 3, 0.3
+    A = _rand_factors(dims, R, 46)
+    W = _rand_factors(dims, R, 47)
+    X = _rand_tensor(dims, 46)
+    Gam = orc.gamma(orc.gram(A))
+    Gd = Gam.copy()
+    for n in range(len(dims)):
+        Gd[n, n][np.diag_indices(R)] += lam * np.diag(Gam[n, n])
+    for q, qd in zip(orc.matvec(A, Gam, W, lam, orc.REG_DIAG), orc.matvec(A, Gd, W, 0.0)):
+        np.testing.assert_allclose(q, qd, rtol=1e-13, atol=1e-13 * np.abs(q).max())
+    for n in range(len(dims)):
+        np.testing.assert_allclose(orc.precond_inv(Gam[n, n], lam, orc.REG_DIAG)[0],
+                                   orc.precond_inv(Gd[n, n], 0.0)[0], rtol=1e-12, atol=1e-15)
+    G, _ = orc.gradient(A, Gam, orc.mttkrp(X, A))
+    V, _, _, _ = orc.pcg(A, Gam, G, lam, 0.0, 6, 0, orc.REG_DIAG)
+    Vd, _, _, _ = orc.pcg(A, Gd, G, 0.0, 0.0, 6)
+    for v, vd in zip(V, Vd):
+        np.testing.assert_allclose(v, vd, rtol=1e-10, atol=1e-12 * np.abs(v).max())
+
+
 def test_gn_step_diag_damping_commutes_with_column_scaling(orc):
     """The CP model is unchanged by A^(1) c, A^(2) / c (column scaling, Section
     3.2).  The map is linear in the unknowns, J(phi(A)) = J(A) S^-1, so the
