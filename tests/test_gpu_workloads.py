@@ -1,0 +1,200 @@
+"""Parity at the full sizes of the two large synthetic workloads: 400^3 with
+R = 50 and column collinearity 0.9 (the one bench.py solves, FP32 storage) and
+the order-4 120^4 with R = 40 and U(0,1) factors.  Both are compared with the
+FP64 oracle: whole results where the oracle's dimension-tree MTTKRP finishes
+in seconds, rows computed one by one from the definition of Eq. (2.3), and
+properties that hold at any size.
+
+Tolerances, from the arithmetic of each result:
+- bf16 split products (TOL_BF16X3 = 2e-5 of the largest entry, as at small
+  sizes).  An emulation of the operand splits on these inputs gives at most
+  6e-6 (400^3) and 5e-7 (120^4) on the definition rows; FP32 accumulation adds
+  about 1e-6.
+- residual-form gradient G = -E_(n) P^(n): 5 TOL_BF16X3 of max |G|.  Its error
+  scales with the entries of E, not with M.
+- FP32 CG of the bench's step, compared with the oracle's FP64 CG run on the
+  same gradient: 1e-4.  An FP32 emulation of k = 2..4 iterations differs from
+  FP64 by 1e-6 on these systems.  The gradient error itself is checked apart
+  from the CG: a 1e-5 gradient perturbation grows to 1e-4 .. 4e-4 in the
+  preconditioned direction.
+- FP64 path: 1e-12 (MTTKRP), 1e-11 (one GN step with a fixed CG count)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_BF16X3 = 2e-5
+WORKLOADS = ("collinear400", "uniform120x4")
+K_CG = 3
+
+_oracle_cache = {}
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_12331_gb300 import api
+
+    api.load(build_if_missing=True)
+    h = api.Handle(0)
+    yield torch, api, h
+    h.close()
+
+
+@pytest.fixture(scope="module", params=WORKLOADS)
+def wl(request, env):
+    torch, _, _ = env
+    from paper_1910_12331_gb300 import datagen
+
+    p = datagen.workload(request.param, seed=0)
+    X64 = p["X"].astype(np.float64)  # the exact upcast of the bytes the GPU reads
+    Xd = torch.from_numpy(p["X"]).cuda()
+    yield request.param, p, X64, Xd
+    _oracle_cache.clear()
+    del Xd
+    torch.cuda.empty_cache()
+
+
+def _oracle(orc, name, X64, A):
+    """Gamma, M (dimension tree) and G at the workload's starting point, once per workload."""
+    if name not in _oracle_cache:
+        Gam = orc.gamma(orc.gram(A))
+        M = orc.mttkrp(X64, A, "dt")
+        G, gn = orc.gradient(A, Gam, M)
+        _oracle_cache[name] = (Gam, M, G, gn)
+    return _oracle_cache[name]
+
+
+def _rows(s):
+    return sorted({i for i in (0, 7, 63, s - 1) if 0 <= i < s})
+
+
+def _oracle_rows(orc, name, X64, A, n):
+    """Rows of M^(n) by the definition (one row at a time), once per workload and mode."""
+    key = (name, "rows", n)
+    if key not in _oracle_cache:
+        rows = _rows(X64.shape[n])
+        _oracle_cache[key] = (rows, np.stack([orc.mttkrp_row(X64, A, n, i) for i in rows]))
+    return _oracle_cache[key]
+
+
+def _dev(torch, arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def _relerr(got, ref):
+    return np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def test_mttkrp_bf16x3(env, orc, wl):
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    A = p["init"]
+    M = [m.cpu().numpy() for m in api.cp_mttkrp_all(h, Xd, _dev(torch, A), prec="bf16x3")]
+    _, Mo, _, _ = _oracle(orc, name, X64, A)
+    for n, (m, mo) in enumerate(zip(M, Mo)):
+        assert _relerr(m, mo) <= TOL_BF16X3, (name, n)
+        rows, ref = _oracle_rows(orc, name, X64, A, n)
+        assert _relerr(m[rows], ref) <= TOL_BF16X3, (name, n)
+
+
+def test_mttkrp_fp64(env, orc, wl):
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    A = p["init"]
+    M = [m.cpu().numpy() for m in api.cp_mttkrp_all(h, Xd, _dev(torch, A), prec="fp64")]
+    _, Mo, _, _ = _oracle(orc, name, X64, A)
+    for n, (m, mo) in enumerate(zip(M, Mo)):
+        assert _relerr(m, mo) <= 1e-12, (name, n)
+        rows, ref = _oracle_rows(orc, name, X64, A, n)
+        assert _relerr(m[rows], ref) <= 1e-12, (name, n)
+
+
+def test_gradient_residual_form(env, orc, wl):
+    """The gradient of every GN iteration of the bench's solve: -E_(n) P^(n)
+    with E reconstructed on the tensor cores."""
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    A = p["init"]
+    G, gn, _ = api.cp_gradient(h, Xd, _dev(torch, A), prec="residual")
+    _, _, Go, gno = _oracle(orc, name, X64, A)
+    for n, (g, go) in enumerate(zip(G, Go)):
+        assert _relerr(g.cpu().numpy(), go) <= 5 * TOL_BF16X3, (name, n)
+    np.testing.assert_allclose(gn, gno[:len(gn)], rtol=1e-4)
+
+
+def test_gn_step_fp64(env, orc, wl):
+    """One plain FP64 GN step with K_CG CG iterations against the oracle's step."""
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    A = p["init"]
+    hi, lo = orc.default_lambda(A)
+    Ad = _dev(torch, A)
+    params = api.gn_params(hi, lo, hi, eps_cg=0.0, cg_max_iter=K_CG, prec="fp64", cg_fp32=False)
+    s, st = api.cp_gn_step(h, Xd, Ad, params)
+    Ao, lam_o, dir_o, so, sto = orc.gn_step(X64, A, hi, 0, lo, hi, 2.0, 0.0, K_CG, use_dt=True)
+    assert s == sto == api.CP_WARN_CG_MAXIT
+    assert st["cg_iters"] == so["cg_iters"] == K_CG
+    for n, (a, ao) in enumerate(zip(Ad, Ao)):
+        assert _relerr(a.cpu().numpy(), ao) <= 1e-11, (name, n)
+    assert abs(st["grad_norm_sum"] - so["grad_norm_sum"]) <= 1e-10 * so["grad_norm_sum"]
+    assert params.lam == lam_o and params.lam_dir == dir_o
+
+
+def test_gn_step_bench_precision(env, orc, wl):
+    """One step in the bench's arithmetic (residual-form gradient, FP32 CG
+    vectors, FP64 CG scalars): its update equals the oracle's FP64 CG on the
+    gradient the library computed (the same kernels, deterministic)."""
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    A = p["init"]
+    hi, lo = orc.default_lambda(A)
+    Ad = _dev(torch, A)
+    G, _, _ = api.cp_gradient(h, Xd, Ad, prec="residual")
+    G = [g.cpu().numpy() for g in G]
+    params = api.gn_params(hi, lo, hi, eps_cg=0.0, cg_max_iter=K_CG, prec="residual", cg_fp32=True)
+    s, st = api.cp_gn_step(h, Xd, Ad, params)
+    assert s == api.CP_WARN_CG_MAXIT and st["cg_iters"] == K_CG
+    Gam, _, _, _ = _oracle(orc, name, X64, A)
+    Vo, it, _, sto = orc.pcg(A, Gam, G, hi, 0.0, K_CG)
+    assert it == K_CG and sto == orc.WARN_CG_MAXIT
+    V = [a.cpu().numpy() - a0 for a, a0 in zip(Ad, A)]
+    scale = max(np.abs(v).max() for v in Vo)
+    assert max(np.abs(v - vo).max() for v, vo in zip(V, Vo)) <= 1e-4 * scale, name
+
+
+def test_als_sweep_normal_equations(env, orc, wl):
+    """After a sweep (Section 2.2) the mode updated last solves its normal
+    equations A^(N) Gamma^(N) = M^(N) with the other, already updated, factors;
+    the objective does not increase."""
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    A = p["init"]
+    Ad = _dev(torch, A)
+    r0 = api.cp_residual(h, Xd, Ad)
+    r1 = api.cp_als_sweep(h, Xd, Ad, 0.0, prec="fp64")
+    assert r1 <= r0
+    A1 = [a.cpu().numpy() for a in Ad]
+    N = len(A1)
+    Gam = orc.gamma(orc.gram(A1))
+    MN = orc.mttkrp(X64, A1, "dt")[N - 1]
+    ref = np.linalg.solve(Gam[N - 1, N - 1], MN.T).T
+    assert _relerr(A1[N - 1], ref) <= 1e-10, name
+    _, gn, mn = api.cp_gradient(h, Xd, Ad, prec="fp64")
+    assert gn[N - 1] <= 1e-10 * mn[N - 1]
+
+
+def test_residual_at_generating_factors(env, orc, wl):
+    """r = ||X - [[A*]]|| / ||X|| at the generating factors is the injected
+    noise level (Section 5's generator) up to the FP32 storage of X; the
+    library's FP64 direct reconstruction matches the oracle's."""
+    torch, api, h = env
+    name, p, X64, Xd = wl
+    eta = {"collinear400": 1e-6, "uniform120x4": 1e-4}[name]
+    r = api.cp_residual(h, Xd, _dev(torch, p["truth"]))
+    ro = orc.residual(X64, p["truth"])
+    assert abs(r - ro) <= 1e-9 * ro
+    assert abs(ro - eta) <= 1e-3 * eta
