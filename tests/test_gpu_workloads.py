@@ -198,3 +198,30 @@ def test_residual_at_generating_factors(env, orc, wl):
     ro = orc.residual(X64, p["truth"])
     assert abs(r - ro) <= 1e-9 * ro
     assert abs(ro - eta) <= 1e-3 * eta
+
+
+def test_als_exact_recovery_exact20(env, orc):
+    """ALS (Section 2.2) on the exact rank-5 20^3 Gaussian tensors reaches
+    r <= 1e-10 from the seeded N(0,1) start in about as many sweeps as the
+    oracle's ALS (21-42 for these seeds; a residual at the threshold may move
+    the count by a sweep)."""
+    torch, api, h = env
+    from paper_1910_12331_gb300 import datagen
+
+    for seed in range(4):
+        p = datagen.workload("exact20", seed=seed)
+        X = torch.from_numpy(p["X"]).cuda()
+        Ad = _dev(torch, p["init"])
+        A = [a.copy() for a in p["init"]]
+        n_gpu = n_orc = None
+        for it in range(1, 201):
+            if n_gpu is None and api.cp_als_sweep(h, X, Ad, 0.0, prec="fp64") <= 1e-10:
+                n_gpu = it
+            if n_orc is None:
+                A, _ = orc.als_sweep(p["X"], A)
+                if orc.residual(p["X"], A) <= 1e-10:
+                    n_orc = it
+            if n_gpu is not None and n_orc is not None:
+                break
+        assert n_gpu is not None and n_orc is not None, seed
+        assert abs(n_gpu - n_orc) <= 2, (seed, n_gpu, n_orc)
