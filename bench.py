@@ -45,7 +45,7 @@ EPS_CG = 1e-3
 CG_MAX = 250
 MU = 2.0
 # GN iterations the FP64 path needs on this workload and seed (measured on a
-# GB300, recorded in the design doc); scales the CPU oracle's per-iteration time.
+# GB300 with this benchmark's FP64 mode); scales the CPU oracle's per-iteration time.
 GN_ITERS_FP64 = 51
 
 # DRAM traffic of the dominant kernels from one ncu capture each (profiles/pcg_kernel_collinear400.md,
@@ -496,7 +496,8 @@ def main():
     else:
         cg_it = max(last["cg_iters_total"], 1)
         rows = sum(X.shape)
-        state_bytes = 4.0 * rows * R * 12  # FP32 CG vectors read/written per iteration
+        # twelve FP32 passes over the CG vectors per iteration (W, Q, V, R, Z read and written)
+        state_bytes = 4.0 * rows * R * 12
         ach = state_bytes / (pcg_phase / cg_it) / 1e9
         rec = profiled("pcg")
         traffic = rec["dram_bytes"] / rec["cg_iters"] if rec and rec["cg_iters"] else None

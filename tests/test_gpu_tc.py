@@ -2,7 +2,7 @@
 
 The split products carry about 2^-16 relative error each; the bound used here,
 max |M_gpu - M_oracle| <= TOL_BF16X3 * max |M_oracle| per call, was set from
-measurement (see DESIGN.md) and holds with margin on these shapes, which cover
+measurement and holds with margin on these shapes, which cover
 ragged i-blocks and k-chunks, several k-groups, several rank tiles, orders 2-5."""
 import numpy as np
 import pytest
