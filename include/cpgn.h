@@ -43,7 +43,7 @@ typedef enum {
     CP_ERR_ARG = 1,          /* invalid argument (shape, pointer, aliasing, dtype) */
     CP_ERR_CUDA = 2,         /* a CUDA runtime call failed */
     CP_ERR_NOMEM = 3,        /* workspace allocation failed */
-    CP_ERR_UNSUPPORTED = 4,  /* valid but not supported by this build/path */
+    CP_ERR_UNSUPPORTED = 4,  /* valid, but not supported by the library on this code path */
     CP_ERR_NOT_SPD = 5,      /* Gamma^(n,n) + lambda I has a non-positive Cholesky pivot */
     CP_ERR_NONFINITE = 6,    /* a NaN/Inf appeared in a gradient or CG scalar */
     CP_ERR_BREAKDOWN = 7,    /* CG curvature <W, (J^T J + lambda I) W> <= 0 */
