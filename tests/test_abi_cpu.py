@@ -82,6 +82,56 @@ def test_batch_plan_arguments_rejected_without_gpu(lib):
     assert lib.cp_batch_plan_destroy(None) == 1
 
 
+def test_noalloc_matvec_degenerate_arguments_rejected(lib):
+    """cp_gn_matvec_noalloc takes no handle and checks every argument before
+    its first CUDA call: order < 2, rank < 1, an empty mode, null factor
+    pointers, an output that aliases an input or another output, and a
+    negative or non-finite lambda are CP_ERR_ARG; order or rank beyond the
+    static scratch is CP_ERR_UNSUPPORTED.  (Skipped where a GPU is visible:
+    the fake device addresses must never reach a kernel.)"""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("argument checks only; fake device pointers")
+    from paper_1910_12331_gb300 import api
+
+    hdr = open(os.path.join(ROOT, "include", "cpgn.h")).read()
+    max_order = int(re.search(r"#define CP_NOALLOC_MAX_ORDER (\d+)", hdr).group(1))
+    max_rank = int(re.search(r"#define CP_NOALLOC_MAX_RANK (\d+)", hdr).group(1))
+    vp = ctypes.c_void_p
+    f = lib.cp_gn_matvec_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(api.cp_desc), vp, vp, ctypes.c_double, vp, vp]
+
+    def ptrs(*vals):
+        arr = (ctypes.c_void_p * len(vals))()
+        for k, v in enumerate(vals):
+            arr[k] = v
+        return arr
+
+    def call(dims, R, lam=0.5, A=None, W=None, Q=None):
+        d = api.make_desc(dims, R, torch.float64)
+        n = len(dims)
+        A = A if A is not None else ptrs(*[0x1000 + 0x100 * k for k in range(n)])
+        W = W if W is not None else ptrs(*[0x2000 + 0x100 * k for k in range(n)])
+        Q = Q if Q is not None else ptrs(*[0x3000 + 0x100 * k for k in range(n)])
+        return f(ctypes.byref(d), A, W, lam, Q, None)
+
+    assert f(None, None, None, 0.0, None, None) == api.CP_ERR_ARG
+    assert call((5,), 2) == api.CP_ERR_ARG                       # order 1
+    assert call((5, 6, 7), 0) == api.CP_ERR_ARG                  # rank 0
+    assert call((5, 0, 7), 2) == api.CP_ERR_ARG                  # empty mode
+    assert call((5, 6, 7), 2, A=ptrs(0x1000, 0, 0x1200)) == api.CP_ERR_ARG           # null factor
+    assert call((5, 6, 7), 2, Q=ptrs(0x3000, 0x1100, 0x3200)) == api.CP_ERR_ARG      # Q aliases A
+    assert call((5, 6, 7), 2, Q=ptrs(0x3000, 0x2000, 0x3200)) == api.CP_ERR_ARG      # Q aliases W
+    assert call((5, 6, 7), 2, Q=ptrs(0x3000, 0x3000, 0x3200)) == api.CP_ERR_ARG      # Q[0] is Q[1]
+    assert call((5, 6, 7), 2, lam=-1.0) == api.CP_ERR_ARG
+    assert call((5, 6, 7), 2, lam=float("nan")) == api.CP_ERR_ARG
+    assert call((5, 6, 7), 2, lam=float("inf")) == api.CP_ERR_ARG
+    assert call((3,) * (max_order + 1), 2) == api.CP_ERR_UNSUPPORTED
+    assert call((5, 6, 7), max_rank + 1) == api.CP_ERR_UNSUPPORTED
+
+
 def test_struct_layouts_match_header():
     """The ctypes mirrors of the header structs have the C sizes (checked with gcc)."""
     import subprocess
