@@ -7,9 +7,9 @@ properties that hold at any size.
 
 Tolerances, from the arithmetic of each result:
 - bf16 split products (TOL_BF16X3 = 2e-5 of the largest entry, as at small
-  sizes).  An emulation of the operand splits on these inputs gives at most
-  6e-6 (400^3) and 5e-7 (120^4) on the definition rows; FP32 accumulation adds
-  about 1e-6.
+  sizes).  The CPU emulation of the operand splits (tests/test_split_scheme.py)
+  run on these whole inputs gives at most 5.7e-6 (400^3) and 4.8e-7 (120^4);
+  FP32 accumulation adds about 1e-6.
 - residual-form gradient G = -E_(n) P^(n): 5 TOL_BF16X3 of max |G|.  Its error
   scales with the entries of E, not with M.
 - FP32 CG of the bench's step, compared with the oracle's FP64 CG run on the
