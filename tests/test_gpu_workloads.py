@@ -11,7 +11,8 @@ Tolerances, from the arithmetic of each result:
   run on these whole inputs gives at most 5.7e-6 (400^3) and 4.8e-7 (120^4);
   FP32 accumulation adds about 1e-6.
 - residual-form gradient G = -E_(n) P^(n): 5 TOL_BF16X3 of max |G|.  Its error
-  scales with the entries of E, not with M.
+  scales with the entries of E, not with M; the split emulation on E at these
+  starting points gives at most 1.2e-6 of max |G|.
 - FP32 CG of the bench's step, compared with the oracle's FP64 CG run on the
   same gradient: 1e-4.  An FP32 emulation of k = 2..4 iterations differs from
   FP64 by 1e-6 on these systems.  The gradient error itself is checked apart
