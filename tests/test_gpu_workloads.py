@@ -170,7 +170,11 @@ def test_gn_step_bench_precision(env, orc, wl):
 def test_als_sweep_normal_equations(env, orc, wl):
     """After a sweep (Section 2.2) the mode updated last solves its normal
     equations A^(N) Gamma^(N) = M^(N) with the other, already updated, factors;
-    the objective does not increase."""
+    the objective does not increase.  Both checks scale with cond(Gamma^(N)) u
+    (4.5e5 u after one sweep on the collinear workload, 1.8e3 u on the uniform
+    one): on these systems an inverse-based solve differs from a backward-stable
+    one by 0.5 cond u and a 1e-15 change of M moves the solution by cond u; the
+    residual of the inverse-based solve is 0.1 cond u."""
     torch, api, h = env
     name, p, X64, Xd = wl
     A = p["init"]
@@ -183,9 +187,10 @@ def test_als_sweep_normal_equations(env, orc, wl):
     Gam = orc.gamma(orc.gram(A1))
     MN = orc.mttkrp(X64, A1, "dt")[N - 1]
     ref = np.linalg.solve(Gam[N - 1, N - 1], MN.T).T
-    assert _relerr(A1[N - 1], ref) <= 1e-10, name
+    tol = 100 * np.linalg.cond(Gam[N - 1, N - 1]) * 2.0 ** -53
+    assert _relerr(A1[N - 1], ref) <= tol, name
     _, gn, mn = api.cp_gradient(h, Xd, Ad, prec="fp64")
-    assert gn[N - 1] <= 1e-10 * mn[N - 1]
+    assert gn[N - 1] <= tol * mn[N - 1]
 
 
 def test_residual_at_generating_factors(env, orc, wl):
