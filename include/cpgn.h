@@ -183,13 +183,18 @@ cp_status cp_gn_matvec(cp_handle h, const cp_desc* desc, const double* const* A,
                        double lambda, double* const* Q);
 
 /* One CP-GN iteration (Algorithm 1 loop body): MTTKRP, Gram/Gamma, gradient,
- * preconditioner (Gamma^(n,n) + lambda I)^{-1} (Cholesky then explicit
- * inverse, Section 3.3), CP-CG (Algorithm 2, standard PCG beta) as one
- * persistent device kernel, then A^(n) += V^(n) in place, then lambda
- * advances (unless lam_fixed).  A is in/out.  Synchronises; fills *stats
- * (host, may be NULL).  Returns the step's status: CP_OK, CP_WARN_CG_MAXIT
- * (update applied), or an error (A unchanged for CP_ERR_NOT_SPD,
- * CP_ERR_NONFINITE; unspecified for CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT). */
+ * preconditioner (Gamma^(n,n) + lambda D)^{-1} with D = I or diag(Gamma^(n,n))
+ * by params->reg (Cholesky then explicit inverse, Section 3.3), CP-CG
+ * (Algorithm 2, standard PCG beta) as one persistent device kernel, then
+ * A^(n) += V^(n) in place, then lambda advances (unless lam_fixed).  A is
+ * in/out.  Synchronises; fills *stats (host, may be NULL).  Returns the step's
+ * status: CP_OK, CP_WARN_CG_MAXIT (update applied), or an error (A unchanged
+ * for CP_ERR_NOT_SPD, CP_ERR_NONFINITE, CP_ERR_UNSUPPORTED; unspecified for
+ * CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT).
+ * Rank limit: the CG kernel keeps N + 2 R x R matrices (its mode's row of
+ * Gamma, P_inv^(n), T^(n)) in shared memory, so R <= 69 at N = 3 and R <= 64
+ * at N = 4 with FP64 CG vectors, R <= 100 and R <= 91 with FP32 ones
+ * (cg_fp32 = 1); a larger R gives CP_ERR_UNSUPPORTED. */
 cp_status cp_gn_step(cp_handle h, const cp_desc* desc, const void* X, double* const* A,
                      cp_gn_params* params, cp_gn_stats* stats);
 
