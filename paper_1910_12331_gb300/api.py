@@ -8,8 +8,10 @@ fallback).  All device work is enqueued on torch's current CUDA stream.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 import threading
+import weakref
 
 import torch
 
@@ -184,6 +186,42 @@ def _check_x(X):
         raise ValueError("X: expected a contiguous CUDA float32/float64 tensor")
 
 
+class XVersions:
+    """Version stamps for the library's cache of the bf16 split of X, which it
+    keys by X's address, size, dtype and the descriptor's x_version.  A tensor
+    gets a new stamp whenever the object at its address is not the one seen
+    there last, or torch's in-place version counter of it has moved, or
+    bump() is called; stamps come from one counter, so a stamp is never reused
+    (a new tensor that the caching allocator places at a freed address can
+    never match the old tensor's cached split)."""
+
+    def __init__(self):
+        self._seen = {}
+        self._next = itertools.count(1)
+
+    @staticmethod
+    def _inplace(X):
+        try:
+            return X._version
+        except RuntimeError:  # inference-mode tensors keep no version counter
+            return None
+
+    def stamp(self, X) -> int:
+        ptr = X.data_ptr()
+        seen = self._seen.get(ptr)
+        tv = self._inplace(X)
+        if seen is not None and seen[0]() is X and seen[1] == tv:
+            return seen[2]
+        ver = next(self._next)
+        self._seen[ptr] = (weakref.ref(X), tv, ver)
+        return ver
+
+    def bump(self, X) -> int:
+        ver = next(self._next)
+        self._seen[X.data_ptr()] = (weakref.ref(X), self._inplace(X), ver)
+        return ver
+
+
 class Handle:
     """Owns a cp_handle bound to a CUDA device; work goes to torch's current stream."""
 
@@ -194,7 +232,7 @@ class Handle:
         h = ctypes.c_void_p()
         _check(L.cp_create(ctypes.byref(h), self.device), "cp_create")
         self.h = h
-        self._version = {}
+        self._xv = XVersions()
 
     def close(self):
         if getattr(self, "h", None):
@@ -212,11 +250,14 @@ class Handle:
 
     def desc(self, X, rank):
         _check_x(X)
-        return make_desc(X.shape, rank, X.dtype, self._version.get(X.data_ptr(), 0))
+        return make_desc(X.shape, rank, X.dtype, self._xv.stamp(X))
 
     def bump_version(self, X):
-        """Declare that the contents of X changed (invalidates the split cache)."""
-        self._version[X.data_ptr()] = self._version.get(X.data_ptr(), 0) + 1
+        """Declare that the contents of X changed (invalidates the split cache).
+        Changes made through torch in place, and new tensors, are detected
+        without it; writes that bypass torch (a raw pointer, another library)
+        need it."""
+        self._xv.bump(X)
 
 
 def _factors(X, A):

@@ -180,3 +180,48 @@ def test_struct_field_offsets_match_header():
     names = [f"{c.__name__}.{f}" for c in structs for f, _ in c._fields_]
     assert [n for n, a, b in zip(names, offs, mine) if a != b] == []
     assert len(offs) == len(mine)
+
+
+def test_split_cache_version_stamps():
+    """The binding's x_version stamps (the library caches the bf16 split of X
+    by address, size, dtype and stamp): same tensor unchanged -> same stamp;
+    in-place change, explicit bump, or another tensor at a freed address ->
+    a stamp never used before."""
+    import gc
+
+    import torch
+
+    from paper_1910_12331_gb300 import api
+
+    xv = api.XVersions()
+    X = torch.zeros(64, 64)
+    s1 = xv.stamp(X)
+    assert xv.stamp(X) == s1
+    X.mul_(2.0)                      # in place through torch
+    s2 = xv.stamp(X)
+    assert s2 != s1 and xv.stamp(X) == s2
+    s3 = xv.bump(X)                  # a write torch cannot see
+    assert s3 not in (s1, s2) and xv.stamp(X) == s3
+    Y = torch.ones(64, 64)
+    sy = xv.stamp(Y)
+    assert sy not in (s1, s2, s3)
+    # a new tensor at the freed address of an old one gets a new stamp
+    ptr = X.data_ptr()
+    del X
+    gc.collect()
+    used = {s1, s2, s3, sy}
+    for _ in range(50):
+        Z = torch.empty(64, 64)
+        sz = xv.stamp(Z)
+        assert sz not in used
+        used.add(sz)
+        if Z.data_ptr() == ptr:
+            break
+        del Z
+    # a view at the same address is another object: a new stamp (a re-split, never a stale hit)
+    W = Y.view(4096)
+    assert xv.stamp(W) not in used
+    with torch.inference_mode():
+        I = torch.zeros(8)
+    si = xv.stamp(I)
+    assert xv.stamp(I) == si

@@ -65,6 +65,25 @@ def test_mttkrp_bf16x3_fp64_input_and_cache(env, orc):
         np.testing.assert_allclose(b, 2.0 * a, rtol=1e-6, atol=1e-6 * np.abs(a).max())
 
 
+def test_mttkrp_bf16x3_new_tensor_at_freed_address(env, orc):
+    """The split of X is cached by address, size, dtype and version: a new
+    tensor that the caching allocator places where a freed one lived gets its
+    own split (the binding's version stamps), not the stale one."""
+    torch, api, h = env
+    X1, A = _problem((48, 20, 36), 5, 8)
+    X2, _ = _problem((48, 20, 36), 5, 9)
+    Ad = [torch.from_numpy(a).cuda() for a in A]
+    Xd = torch.from_numpy(X1).cuda()
+    ptr = Xd.data_ptr()
+    api.cp_mttkrp_all(h, Xd, Ad, prec="bf16x3")
+    del Xd
+    Xd = torch.from_numpy(X2).cuda()
+    M = [m.cpu().numpy() for m in api.cp_mttkrp_all(h, Xd, Ad, prec="bf16x3")]
+    ref = orc.mttkrp(X2, A)
+    assert max(np.abs(m - r).max() / np.abs(r).max() for m, r in zip(M, ref)) <= TOL_BF16X3
+    print("same address reused:", Xd.data_ptr() == ptr)
+
+
 def test_mttkrp_bf16x3_exact_gradient_invariant(env):
     """At an exact decomposition M^(n) = A^(n) Gamma^(n): checked at 256^3, R=32,
     a size the oracle cannot brute-force, through the invariant alone."""
