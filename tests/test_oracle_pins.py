@@ -115,6 +115,22 @@ def test_mttkrp_exact_decomposition(orc, dims, R):
         assert abs(np.sum(M[n] * A[n]) - np.sum(X * X)) <= 1e-12 * np.sum(X * X)
 
 
+@pytest.mark.parametrize("perm", [(1, 0, 2, 3), (3, 2, 1, 0), (2, 0, 3, 1), (0, 3, 1, 2)])
+def test_mttkrp_mode_permutation_equivariance(orc, perm):
+    """M^(n) depends on which factor multiplies which mode, not on the order
+    the modes are stored in: permuting X's modes and the factor list permutes
+    the outputs.  The dimension tree treats the first, middle and last modes
+    differently, so this exercises each of its index paths."""
+    dims, R = (5, 4, 6, 3), 3
+    A = _rand_factors(dims, R, 31)
+    X = _rand_tensor(dims, 31)
+    M = orc.mttkrp(X, A, "dt")
+    Xp = np.ascontiguousarray(np.transpose(X, perm))
+    Mp = orc.mttkrp(Xp, [A[q] for q in perm], "dt")
+    for k, q in enumerate(perm):
+        np.testing.assert_allclose(Mp[k], M[q], rtol=1e-12, atol=1e-12 * np.abs(M[q]).max())
+
+
 # ---------------------------------------------------------------- matmul tensor
 
 def test_strassen_golden(orc):
