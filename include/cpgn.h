@@ -15,7 +15,10 @@
  *  - The caller owns every buffer it passes.  The library never frees or
  *    retains caller memory beyond the call.  The handle owns its device
  *    workspace (grown on demand with cudaMalloc, freed by cp_destroy) and a
- *    cache of split-precision copies of X keyed by (pointer, size, version).
+ *    cache of split-precision copies of X keyed by (pointer, size, dtype,
+ *    x_version).  The caller must change x_version whenever the bytes at that
+ *    pointer change, including when a new tensor is allocated at the address
+ *    of a freed one; otherwise a bf16x3 call reuses the old split.
  *  - Outputs must not alias inputs (CP_ERR_ARG).
  *  - All device work is enqueued on the handle's stream (cp_set_stream;
  *    default: the legacy default stream).  Calls that return host scalars or
@@ -82,7 +85,8 @@ typedef struct {
     int rank;                      /* R */
     int64_t dims[CP_MAX_ORDER];    /* s_1 .. s_N */
     cp_dtype x_dtype;              /* element type of X */
-    uint64_t x_version;            /* bump when the contents of X change (split cache key) */
+    uint64_t x_version;            /* change whenever the bytes of X change, or a new tensor
+                                      reuses X's address (split cache key) */
 } cp_desc;
 
 /* Damping of the Gauss-Newton system (Section 3.2).  CP_REG_IDENTITY solves
