@@ -57,7 +57,7 @@ PROFILED = {
             "dram_bytes": 927744 + 8192, "cg_iters": 4},
     # recon_tc_kernel (258194688 B read + 237863424 B written) + mttkrp_tc_kernel (287438592 + 5595904)
     "gradient": {"src": {"paper_1910_12331_gb300/csrc/k_resid_tc.cu": "dcfadb974a14b7ccaed7e02f71dc37c219b22be8",
-                         "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu": "6a6404b2f6d34a94965684bfdb3e7d5295a65bc0"},
+                         "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu": "0d5783d6ab04114cc790bebc1315ce9a5ec4f50d"},
                  "dram_bytes": 258194688 + 237863424 + 287438592 + 5595904},
 }
 # The mixed path of the timed solve: residual-form gradient every iteration, FP32 CG vectors.

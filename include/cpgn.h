@@ -154,8 +154,12 @@ cp_status cp_destroy(cp_handle h);
 cp_status cp_set_stream(cp_handle h, void* stream);
 
 /* Bytes of handle-owned device workspace a call pattern on `desc` needs at
- * precision `prec` (excluding the split-X cache, which is reported by
- * *split_bytes when non-null). */
+ * precision `prec`, an upper bound: the Gram/Gamma/gradient/CG buffers, for
+ * CP_PREC_BF16X3 and CP_PREC_RESIDUAL also the tensor-core MTTKRP's partial
+ * sums, and for CP_PREC_RESIDUAL the bf16 planes of E = X - [[A]] and the
+ * reconstruction's scratch.  The split-X cache (CP_PREC_BF16X3 only) is
+ * reported apart, by *split_bytes when non-null.  Errors: CP_ERR_ARG,
+ * CP_ERR_CUDA (device query). */
 cp_status cp_workspace_size(cp_handle h, const cp_desc* desc, cp_precision prec, size_t* bytes,
                             size_t* split_bytes);
 

@@ -273,6 +273,7 @@ cp_status cp_set_stream(cp_handle h, void* stream) {
 cp_status cp_workspace_size(cp_handle h, const cp_desc* d, cp_precision prec, size_t* bytes, size_t* split_bytes) {
     if (!h || !bytes) return CP_ERR_ARG;
     CP_TRY(check_desc(d));
+    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3 && prec != CP_PREC_RESIDUAL) return CP_ERR_ARG;
     const Shape s = make_shape(d);
     const size_t RR = (size_t)s.R * s.R, rows = (size_t)s.roff[s.N];
     size_t b = 0;
@@ -280,6 +281,17 @@ cp_status cp_workspace_size(cp_handle h, const cp_desc* d, cp_precision prec, si
     b += rows * s.R * 8 * 2;                    // M, G
     b += rows * s.R * 8 * 7;                    // packed A and CG vectors (FP64 worst case)
     b += (size_t)4096 * RR * 8 + s.N * RR * 8;  // partial A^T W per block, T
+    if (prec != CP_PREC_FP64) {                 // tensor-core MTTKRP: partial sums and operand planes
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+            cudaGetLastError();
+            return CP_ERR_CUDA;
+        }
+        b += tc_workspace_bytes(s, sms);
+    }
+    if (prec == CP_PREC_RESIDUAL)  // bf16 planes of E and the reconstruction's scratch
+        b += (size_t)PlaneTiling::of(s).total() * 2 +
+             (resid_tc_supported(s) ? resid_tc_scratch_bytes(s) : resid_scratch_bytes(s));
     *bytes = b;
     if (split_bytes) *split_bytes = prec == CP_PREC_BF16X3 ? split_cache_bytes(d) : 0;
     return CP_OK;

@@ -895,6 +895,20 @@ static TcGeom tc_geom(const Shape& s, int sms) {
     return g;
 }
 
+// Device workspace tc_main allocates for one shape (its operand planes,
+// partial sums and segment records; the rank tiles reuse it), for
+// cp_workspace_size.  Same formulas as tc_main.
+size_t tc_workspace_bytes(const Shape& s, int sms) {
+    const TcGeom g = tc_geom(s, sms);
+    const int64_t pitch = (int64_t)g.nch * kKC;
+    const size_t nslots = (size_t)g.grid * g.smax;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    return al((size_t)2 * kRT * pitch * sizeof(__nv_bfloat16)) + al((size_t)s.dims[0] * kRT * sizeof(float)) +
+           al((size_t)s.mid * kRT * sizeof(float)) + al(nslots * kBI * kRT * sizeof(float)) +
+           al(nslots * kGroup * kRT * kKC * sizeof(float)) +
+           al((size_t)g.nib * g.ngr * s.mid * kRT * sizeof(float)) + al(nslots * sizeof(int4));
+}
+
 // bf16 planes of X, cached by pointer / size / version.
 static cp_status tc_split_x(SplitCache& c, const cp_desc* d, const Shape& s, const void* X, int sms,
                             cudaStream_t st) {

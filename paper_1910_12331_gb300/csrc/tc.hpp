@@ -23,6 +23,8 @@ struct SplitCache {
 };
 
 size_t split_cache_bytes(const cp_desc* d);
+// Device workspace (partials, operand planes) one tensor-core MTTKRP call needs, on a GPU with `sms` SMs.
+size_t tc_workspace_bytes(const Shape& s, int sms);
 // Kernels one tensor-core MTTKRP call launches (before it runs: counts the split if the cache misses).
 int tc_launch_count(const SplitCache& c, const cp_desc* d, const Shape& s);
 void split_cache_free(SplitCache& c);
