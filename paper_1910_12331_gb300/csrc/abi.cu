@@ -658,7 +658,11 @@ cp_status cp_batch_plan_create(cp_handle h, int nprob, const cp_batch_problem* p
     BatchPlan* p = nullptr;
     CP_TRY(batch_plan_create(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters, target_residual,
                              autotune, &p));
-    *plan = new cp_batch_plan_s{h->device, nprob, p};
+    *plan = new (std::nothrow) cp_batch_plan_s{h->device, nprob, p};
+    if (!*plan) {
+        batch_plan_destroy(p);
+        return CP_ERR_NOMEM;
+    }
     return CP_OK;
 }
 
@@ -682,7 +686,10 @@ cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads) {
 
 cp_status cp_batch_plan_destroy(cp_batch_plan plan) {
     if (!plan) return CP_ERR_ARG;
-    batch_plan_destroy(plan->p);
+    {
+        DeviceGuard g(plan->device);  // the caller's current device is restored
+        batch_plan_destroy(plan->p);
+    }
     delete plan;
     return CP_OK;
 }
