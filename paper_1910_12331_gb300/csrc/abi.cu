@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "cpgn.h"
@@ -34,6 +35,19 @@ struct DeviceGuard {
 };
 
 constexpr long long kDefaultSpin = 1LL << 24;  // polls (with 64 ns sleeps: about a second or more)
+
+// Host code behind some entry points uses standard containers; no exception
+// may leave the C ABI: an allocation failure becomes CP_ERR_NOMEM.
+template <typename F>
+cp_status no_throw(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return CP_ERR_NOMEM;
+    } catch (...) {
+        return CP_ERR_CUDA;
+    }
+}
 
 }  // namespace
 
@@ -634,8 +648,10 @@ cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* pr
         return CP_ERR_ARG;
     if (nprob == 0) return CP_OK;
     DeviceGuard g(h->device);
-    return run_batched(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters, target_residual,
-                       results);
+    return no_throw([&] {
+        return run_batched(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters, target_residual,
+                           results);
+    });
 }
 
 }  // extern "C"
@@ -656,8 +672,10 @@ cp_status cp_batch_plan_create(cp_handle h, int nprob, const cp_batch_problem* p
     *plan = nullptr;
     DeviceGuard g(h->device);
     BatchPlan* p = nullptr;
-    CP_TRY(batch_plan_create(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters, target_residual,
-                             autotune, &p));
+    CP_TRY(no_throw([&] {
+        return batch_plan_create(h->device, h->stream, nprob, problems, eps_cg, cg_max_iter, max_iters,
+                                 target_residual, autotune, &p);
+    }));
     *plan = new (std::nothrow) cp_batch_plan_s{h->device, nprob, p};
     if (!*plan) {
         batch_plan_destroy(p);
@@ -675,7 +693,7 @@ cp_status cp_batch_plan_launch(cp_handle h, cp_batch_plan plan) {
 cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result* results) {
     if (!h || !plan || !results || plan->device != h->device) return CP_ERR_ARG;
     DeviceGuard g(h->device);
-    return batch_plan_results(plan->p, h->stream, results);
+    return no_throw([&] { return batch_plan_results(plan->p, h->stream, results); });
 }
 
 cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads) {

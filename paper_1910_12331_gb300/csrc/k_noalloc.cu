@@ -119,7 +119,12 @@ extern "C" cp_status cp_gn_matvec_noalloc(const cp_desc* d, const double* const*
         return CP_ERR_CUDA;
     }
     double* scratch = nullptr;
-    const cp_status st = scratch_on(dev, &scratch);
+    cp_status st = CP_OK;
+    try {  // the lookup's mutex may throw; nothing may leave the C ABI
+        st = scratch_on(dev, &scratch);
+    } catch (...) {
+        return CP_ERR_CUDA;
+    }
     if (st != CP_OK) return st;
     const Shape s = make_shape(d);
     const size_t RR = (size_t)s.R * s.R;
