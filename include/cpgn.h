@@ -140,7 +140,8 @@ typedef struct {
     int kernel_launches;     /* kernels this step launched */
 } cp_gn_stats;
 
-/* Human-readable name of a status code (static storage). */
+/* Human-readable name of a status code (static storage; unknown codes give
+ * "CP_UNKNOWN_STATUS").  Never fails. */
 const char* cp_status_string(cp_status s);
 
 /* Create a handle bound to CUDA device `device`.  Allocates nothing on the
@@ -150,7 +151,9 @@ cp_status cp_create(cp_handle* out, int device);
 /* Free the handle and all of its workspace.  Synchronises its stream. */
 cp_status cp_destroy(cp_handle h);
 
-/* Enqueue all later work of `h` on `stream` (a cudaStream_t; NULL = default). */
+/* Enqueue all later work of `h` on `stream` (a cudaStream_t of the handle's
+ * device, owned by the caller; NULL = the legacy default stream).  Errors:
+ * CP_ERR_ARG (null handle). */
 cp_status cp_set_stream(cp_handle h, void* stream);
 
 /* Bytes of handle-owned device workspace a call pattern on `desc` needs at
@@ -176,9 +179,14 @@ cp_status cp_mttkrp_all(cp_handle h, const cp_desc* desc, const void* X, const d
                         double* const* M, cp_precision prec);
 
 /* Gradient of f (Eq. (2.3)) through Algorithm 1's gradient line:
- * G^(n) = A^(n) Gamma^(n,n) - M^(n), with M from cp_mttkrp_all at `prec`.
- * Also returns, in host memory, gnorm[n] = ||G^(n)||_F and mnorm[n] =
- * ||M^(n)||_F (either may be NULL).  Synchronises. */
+ * G^(n) = A^(n) Gamma^(n,n) - M^(n), with M from cp_mttkrp_all at `prec`;
+ * at CP_PREC_RESIDUAL the same quantity in residual form, -E_(n) P^(n) with
+ * E = X - [[A]].  G: host array of N device pointers (s_n x R doubles,
+ * overwritten).  Also returns, in host memory, gnorm[n] = ||G^(n)||_F and
+ * mnorm[n] = ||M^(n)||_F (either may be NULL).  Synchronises.  Errors:
+ * CP_ERR_ARG (null or aliased pointers, bad descriptor or precision),
+ * CP_ERR_NOMEM, CP_ERR_CUDA, CP_ERR_TIMEOUT (a bounded wait of a tensor-core
+ * kernel expired). */
 cp_status cp_gradient(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
                       double* const* G, cp_precision prec, double* gnorm, double* mnorm);
 
@@ -213,7 +221,7 @@ typedef struct {
     double target_stationarity; /* stop when sum||G||/sum||M|| (FP64 gradient) <= this (<= 0: unused) */
     double refine_below;     /* BF16X3 only: switch the gradient to refine_prec once the
                                 low-precision stationarity falls below this (<= 0: never) */
-    cp_precision refine_prec; /* CP_PREC_RESIDUAL (default when 0 is given for BF16X3) or CP_PREC_FP64 */
+    cp_precision refine_prec; /* CP_PREC_FP64 (= 0) or CP_PREC_RESIDUAL (any other value) */
     int residual_every;      /* evaluate the residual every k iterations (0: only when targeted) */
 } cp_solve_opts;
 
@@ -233,23 +241,31 @@ typedef struct {
 } cp_solve_result;
 
 /* Run Algorithm 1 from the factors in A (in/out) until a target of `opts` is
- * met or max_iters steps have run.  params is in/out as in cp_gn_step.
- * Synchronises. */
+ * met or max_iters steps have run.  params is in/out as in cp_gn_step; *result
+ * (host) receives the counts, the last stationarity and residual, and summed
+ * device times.  Synchronises once per GN iteration.  Returns CP_OK when the
+ * loop ended without a step error, whether or not a target was met (see
+ * result->converged; a step that hit the CG cap is not an error here), else
+ * the failing step's status (as in cp_gn_step).  Argument errors: CP_ERR_ARG. */
 cp_status cp_gn_solve(cp_handle h, const cp_desc* desc, const void* X, double* const* A,
                       cp_gn_params* params, const cp_solve_opts* opts, cp_solve_result* result);
 
 /* One CP-ALS sweep (Section 2.2): for n = 1..N in order,
  * A^(n) <- M^(n) (Gamma^(n) + lambda I)^{-1} with M^(n) = X_(n) P^(n) formed
  * from the factors already updated in this sweep; the inverse is built from
- * the Cholesky factor.  lambda = 0 is plain ALS.  A is in/out.  If
- * rel_residual is non-null, the direct FP64 residual after the sweep is
- * written there (synchronises); otherwise asynchronous. */
+ * the Cholesky factor.  lambda = 0 is plain ALS.  A is in/out.  prec:
+ * CP_PREC_FP64 or CP_PREC_BF16X3 (the MTTKRP's arithmetic).  If rel_residual
+ * is non-null, the direct FP64 residual after the sweep is written there
+ * (synchronises); otherwise asynchronous.  Errors: CP_ERR_ARG, CP_ERR_NOMEM,
+ * CP_ERR_CUDA, and, observed when synchronising, CP_ERR_NOT_SPD (a singular
+ * Gamma^(n) + lambda I) or CP_ERR_TIMEOUT. */
 cp_status cp_als_sweep(cp_handle h, const cp_desc* desc, const void* X, double* const* A, double lambda,
                        cp_precision prec, double* rel_residual);
 
 /* Relative residual r = ||X - [[A]]||_F / ||X||_F (Section 5), with the
  * reconstruction formed element by element in FP64 and both squared sums
- * accumulated in FP64.  Writes the host scalar; synchronises. */
+ * accumulated in FP64.  Writes the host scalar; synchronises.  Errors:
+ * CP_ERR_ARG (null pointers, bad descriptor), CP_ERR_NOMEM, CP_ERR_CUDA. */
 cp_status cp_residual(cp_handle h, const cp_desc* desc, const void* X, const double* const* A,
                       double* rel_residual);
 
@@ -292,7 +308,9 @@ typedef struct {
     double lam;            /* lambda of the last iteration */
 } cp_batch_result;
 
-/* problems and results are host arrays of nprob entries.  The shared memory a
+/* Many small order-3 problems, each by Algorithm 1 with CP-CG (Algorithm 2)
+ * and the varying lambda of Section 3.2, in one persistent launch (a CTA per
+ * problem at a time).  problems and results are host arrays of nprob entries.  The shared memory a
  * problem needs, 8 (R^2 + R + 96) + 4 (6 (s_1 + s_2 + s_3) R + 21 R^2) bytes,
  * must not exceed 220 KB (CP_ERR_UNSUPPORTED).  Synchronises.
  * Errors: CP_ERR_ARG (null pointers, sizes out of range, mu <= 1, lam < 0,
