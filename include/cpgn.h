@@ -335,7 +335,9 @@ cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* pr
  * Launches of one plan must not overlap on the GPU (they share the counter
  * and the results).  cp_batch_plan_results copies the results of the last
  * completed launch to `results` (host, nprob entries); synchronises.
- * cp_batch_plan_threads returns the block size in use.  Errors: CP_ERR_ARG,
+ * cp_batch_plan_threads returns the block size in use.  cp_batch_plan_destroy
+ * frees the plan's device memory (after its launches have finished; the
+ * caller's current device is kept) and the plan.  Errors: CP_ERR_ARG,
  * CP_ERR_UNSUPPORTED, CP_ERR_NOMEM, CP_ERR_CUDA. */
 typedef struct cp_batch_plan_s* cp_batch_plan;
 cp_status cp_batch_plan_create(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
