@@ -181,6 +181,17 @@ def _check_factor(t, rows, rank, name):
         raise ValueError(f"{name}: expected contiguous CUDA float64 tensor of shape ({rows}, {rank})")
 
 
+def _check_outputs(outs, shape, rank, name, device):
+    """Caller-supplied outputs: one contiguous float64 (s_n, R) tensor per mode
+    on `device` (the library cannot see the size of a device buffer)."""
+    if len(outs) != len(shape):
+        raise ValueError(f"{name}: need one output per mode")
+    for n, t in enumerate(outs):
+        _check_factor(t, shape[n], rank, f"{name}[{n}]")
+        if t.device != device:
+            raise ValueError(f"{name}[{n}] is on {t.device}, expected {device}")
+
+
 def _check_x(X):
     if not (X.is_cuda and X.dtype in (torch.float32, torch.float64) and X.is_contiguous()):
         raise ValueError("X: expected a contiguous CUDA float32/float64 tensor")
@@ -250,6 +261,8 @@ class Handle:
 
     def desc(self, X, rank):
         _check_x(X)
+        if X.device.index != self.device:
+            raise ValueError(f"X is on {X.device}, the handle on cuda:{self.device}")
         return make_desc(X.shape, rank, X.dtype, self._xv.stamp(X))
 
     def bump_version(self, X):
@@ -266,6 +279,8 @@ def _factors(X, A):
     R = A[0].shape[1]
     for n, a in enumerate(A):
         _check_factor(a, X.shape[n], R, f"A[{n}]")
+        if a.device != X.device:
+            raise ValueError(f"A[{n}] is on {a.device}, X on {X.device}")
     return R
 
 
@@ -281,8 +296,7 @@ def cp_mttkrp_all(h: Handle, X, A, M=None, prec="fp64"):
     R = _factors(X, A)
     if M is None:
         M = [torch.empty_like(a) for a in A]
-    for n, m in enumerate(M):
-        _check_factor(m, X.shape[n], R, f"M[{n}]")
+    _check_outputs(M, X.shape, R, "M", X.device)
     h._bind_stream()
     d = h.desc(X, R)
     _check(load().cp_mttkrp_all(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), _ptr_array(M), PREC[prec]),
@@ -294,6 +308,7 @@ def cp_gradient(h: Handle, X, A, G=None, prec="fp64"):
     R = _factors(X, A)
     if G is None:
         G = [torch.empty_like(a) for a in A]
+    _check_outputs(G, X.shape, R, "G", X.device)
     h._bind_stream()
     d = h.desc(X, R)
     N = X.dim()
@@ -309,8 +324,16 @@ def cp_gn_matvec(h: Handle, A, W, lam, Q=None):
     for n in range(len(A)):
         _check_factor(A[n], shape[n], R, f"A[{n}]")
         _check_factor(W[n], shape[n], R, f"W[{n}]")
+    if len(W) != len(A):
+        raise ValueError("need one W per factor")
+    for n in range(len(A)):
+        if A[n].device != A[0].device or W[n].device != A[0].device:
+            raise ValueError("A and W must be on one device")
+    if A[0].device.index != h.device:
+        raise ValueError(f"A is on {A[0].device}, the handle on cuda:{h.device}")
     if Q is None:
         Q = [torch.empty_like(a) for a in A]
+    _check_outputs(Q, shape, R, "Q", A[0].device)
     h._bind_stream()
     d = make_desc(shape, R, torch.float64)
     _check(load().cp_gn_matvec(h.h, ctypes.byref(d), _ptr_array(A), _ptr_array(W), float(lam), _ptr_array(Q)),

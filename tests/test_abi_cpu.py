@@ -225,3 +225,51 @@ def test_split_cache_version_stamps():
         I = torch.zeros(8)
     si = xv.stamp(I)
     assert xv.stamp(I) == si
+
+
+def test_binding_rejects_bad_outputs_and_devices():
+    """The binding checks what the library cannot see: the shape, dtype,
+    layout and device of every caller-supplied output (a wrong-sized device
+    buffer would be written out of bounds), and that factors sit on X's
+    device and X on the handle's."""
+    import torch
+
+    from paper_1910_12331_gb300 import api
+
+    class T:  # the attributes the validators read, on a chosen device
+        def __init__(self, shape, dev=0, dtype=torch.float64, contiguous=True):
+            self.shape, self.dtype, self.is_cuda = tuple(shape), dtype, True
+            self.device = torch.device("cuda", dev)
+            self._c = contiguous
+
+        def is_contiguous(self):
+            return self._c
+
+        def dim(self):
+            return len(self.shape)
+
+    shape, R = (5, 6, 7), 3
+    ok = [T((s, R)) for s in shape]
+    api._check_outputs(ok, shape, R, "G", torch.device("cuda", 0))
+    bad_cases = [
+        [T((5, R)), T((6, R))],                                          # one missing
+        [T((5, R)), T((6, R + 1)), T((7, R))],                           # wrong rank
+        [T((5, R)), T((7, R)), T((7, R))],                               # wrong rows
+        [T((5, R)), T((6, R), dtype=torch.float32), T((7, R))],          # wrong dtype
+        [T((5, R)), T((6, R), contiguous=False), T((7, R))],             # not contiguous
+        [T((5, R)), T((6, R), dev=1), T((7, R))],                        # another device
+    ]
+    for outs in bad_cases:
+        with pytest.raises(ValueError):
+            api._check_outputs(outs, shape, R, "G", torch.device("cuda", 0))
+    X = T(shape)
+    X.dtype = torch.float32
+    assert api._factors(X, ok) == R
+    with pytest.raises(ValueError):
+        api._factors(X, [T((5, R)), T((6, R), dev=1), T((7, R))])
+    with pytest.raises(ValueError):
+        api._factors(X, ok[:2])
+    h = object.__new__(api.Handle)  # a handle record without a device context
+    h.device, h._xv, h.h = 0, api.XVersions(), None
+    with pytest.raises(ValueError):
+        h.desc(T(shape, dev=1, dtype=torch.float32), R)
