@@ -424,16 +424,20 @@ def cp_residual_sums(h: Handle, X, A):
     return e.value, x.value
 
 
-def _batch_array(problems):
+def _batch_array(problems, device: int):
     n = len(problems)
     arr = (cp_batch_problem * max(n, 1))()
     for k, q in enumerate(problems):
         X, A = q["X"], q["A"]
         if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 3 or not X.is_contiguous():
             raise ValueError("batched: X must be a contiguous 3-D float32 CUDA tensor")
+        if X.device.index != device:
+            raise ValueError(f"batched: problem {k} is on {X.device}, the handle on cuda:{device}")
         R = A[0].shape[1]
         for m in range(3):
             _check_factor(A[m], X.shape[m], R, f"A[{m}]")
+            if A[m].device != X.device:
+                raise ValueError(f"batched: problem {k}, A[{m}] is on {A[m].device}, X on {X.device}")
         arr[k].dims = (ctypes.c_int64 * 3)(*X.shape)
         arr[k].rank = R
         arr[k].X = X.data_ptr()
@@ -450,7 +454,7 @@ def cp_gn_solve_batched(h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_i
     dicts with X (float32 CUDA, 3-D), A (three float64 CUDA (s_n, R) tensors, updated in
     place), lam, lam_lo, lam_hi, mu.  Returns a list of result dicts."""
     n = len(problems)
-    arr = _batch_array(problems)
+    arr = _batch_array(problems, h.device)
     res = (cp_batch_result * max(n, 1))()
     h._bind_stream()
     _check(load().cp_gn_solve_batched(h.h, n, arr, eps_cg, cg_max_iter, max_iters, target_residual, res),
@@ -467,7 +471,7 @@ class BatchPlan:
                  autotune=True):
         self.h, self.n = h, len(problems)
         self._keep = problems  # the plan holds their device pointers
-        arr = _batch_array(problems)
+        arr = _batch_array(problems, h.device)
         p = ctypes.c_void_p()
         h._bind_stream()
         _check(load().cp_batch_plan_create(h.h, self.n, arr, eps_cg, cg_max_iter, max_iters, target_residual,
