@@ -513,10 +513,14 @@ def cp_gn_matvec_noalloc(A, W, lam, Q):
     caller; work goes to torch's current stream on the current device."""
     R = A[0].shape[1]
     shape = [a.shape[0] for a in A]
+    if len(W) != len(A) or len(Q) != len(A):
+        raise ValueError("need one W and one Q per factor")
+    dev = torch.device("cuda", torch.cuda.current_device())
     for n in range(len(A)):
-        _check_factor(A[n], shape[n], R, f"A[{n}]")
-        _check_factor(W[n], shape[n], R, f"W[{n}]")
-        _check_factor(Q[n], shape[n], R, f"Q[{n}]")
+        for name, t in (("A", A[n]), ("W", W[n]), ("Q", Q[n])):
+            _check_factor(t, shape[n], R, f"{name}[{n}]")
+            if t.device != dev:
+                raise ValueError(f"{name}[{n}] is on {t.device}; the call runs on the current device {dev}")
     d = make_desc(shape, R, torch.float64)
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     _check(load().cp_gn_matvec_noalloc(ctypes.byref(d), _ptr_array(A), _ptr_array(W), float(lam), _ptr_array(Q),
