@@ -15,7 +15,8 @@ from paper_1910_12331_gb300 import datagen
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
-SHAPES = [((5, 7, 9), 3), ((6, 5, 4, 7), 4), ((8, 6), 3), ((3, 4, 2, 3, 2), 2)]
+SHAPES = [((5, 7, 9), 3), ((6, 5, 4, 7), 4), ((8, 6), 3), ((3, 4, 2, 3, 2), 2),
+          ((2, 3, 2, 2, 3, 2, 2, 2), 2)]  # the largest order, 8
 
 
 def _rand_factors(dims, R, seed):
@@ -235,7 +236,7 @@ def test_precond_not_spd(orc):
 
 # ----------------------------------------------------------------------- matvec
 
-@pytest.mark.parametrize("dims,R", [((20, 20, 20), 5), ((4, 3, 5, 2), 3), ((5, 6), 2)])
+@pytest.mark.parametrize("dims,R", [((20, 20, 20), 5), ((4, 3, 5, 2), 3), ((5, 6), 2), ((2, 2, 3, 2, 2, 2, 2, 2), 2)])
 @pytest.mark.parametrize("lam", [0.0, 0.37])
 def test_matvec_explicit_jacobian(orc, dims, R, lam):
     """Q = (J^T J + lam I) w with J formed explicitly (Eq. (3.1)); checks the
