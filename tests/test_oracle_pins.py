@@ -289,6 +289,26 @@ def test_matvec_symmetric_psd_nullspace(orc):
     assert max(np.abs(h).max() for h in HD) <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("dims,R", [((7, 6, 5, 4), 3), ((9, 8), 4), ((6, 5, 7), 5)])
+def test_matvec_quadratic_form_from_grams(orc, dims, R):
+    """<W, (J^T J + lam I) W> from R x R quantities only: lam ||W||^2 +
+    sum_n <W^(n)T W^(n), Gamma^(n,n)> + sum_n <Y^(n)T, T^(n)>, Y^(p) = A^(p)T W^(p),
+    T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p) (the curvature of a CG step without
+    forming Q)."""
+    A = _rand_factors(dims, R, 51)
+    W = _rand_factors(dims, R, 52)
+    lam = 0.3
+    Gam = orc.gamma(orc.gram(A))
+    N = len(dims)
+    direct = sum(float(np.sum(w * q)) for w, q in zip(W, orc.matvec(A, Gam, W, lam)))
+    Y = [a.T @ w for a, w in zip(A, W)]
+    T = [sum(Gam[n, p] * Y[p] for p in range(N) if p != n) for n in range(N)]
+    grams = lam * sum(float(np.sum(w * w)) for w in W) + sum(float(np.sum((w.T @ w) * Gam[n, n]))
+                                                            for n, w in enumerate(W))
+    grams += sum(float(np.sum(Y[n].T * T[n])) for n in range(N))
+    assert abs(grams - direct) <= 1e-12 * abs(direct)
+
+
 # -------------------------------------------------------------------------- PCG
 
 @pytest.mark.parametrize("dims,R,lam", [((5, 4, 6), 3, 1e-2), ((4, 3, 3, 2), 2, 0.5)])
