@@ -361,8 +361,12 @@ cp_status cp_batch_plan_destroy(cp_batch_plan plan);
  * GPU loading the library holds until the process exits.  The call allocates
  * nothing and calls no allocating routine; the caller passes inputs and
  * outputs (host arrays of N device pointers, s_n x R doubles each).
- * The first call on a device looks up the array's device address (and may
- * load the library's module); make that first call before any stream capture.
+ * The first call on a device (and the first after its CUDA context was
+ * destroyed and created again, e.g. by cudaDeviceReset) looks up the array's
+ * device address in the current context and loads the modules of the kernels
+ * the call launches, which commits their device memory (the array included):
+ * make that first call before any region in which nothing may be allocated,
+ * and before any stream capture.
  * All calls share the array: calls that overlap on the GPU race, so the
  * caller must serialise them.  Each call rewrites all scratch it reads.
  * Errors: CP_ERR_ARG (null/aliased pointers, bad shape, lambda < 0),

@@ -48,19 +48,18 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str | None = None) -> str:
-    """Compile into LIB (or `out` with its own object folder, for variant builds)."""
-    lib = out or LIB
-    if out is None and not force and up_to_date():
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source under csrc/ and link LIB (skipped when up to date)."""
+    if not force and up_to_date():
         return LIB
     nvcc = _nvcc()
-    bdir = BUILD if out is None else out + ".objs"
+    bdir = BUILD
     os.makedirs(bdir, exist_ok=True)
     objs = []
 
     def compile_one(src):
         obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -70,13 +69,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str |
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = lib + ".tmp"
+    tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, lib)
-    return lib
+    os.replace(tmp, LIB)
+    return LIB
 
 
 if __name__ == "__main__":

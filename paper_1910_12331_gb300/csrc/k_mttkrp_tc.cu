@@ -59,10 +59,7 @@ namespace tc {
 
 using namespace tcx;
 
-#ifndef CPGN_TC_WQ
-#define CPGN_TC_WQ 2
-#endif
-constexpr int kWQ = CPGN_TC_WQ;          // worker warps per TMEM lane quadrant
+constexpr int kWQ = 2;                   // worker warps per TMEM lane quadrant
 constexpr int kWork = 128 * kWQ;         // worker threads
 constexpr int kThreads = 128 + kWork;    // four role warps + the workers
 constexpr int kWCols = 64 / kWQ;         // rank columns of D_Y / D_Z per worker warp
@@ -82,17 +79,7 @@ constexpr uint32_t kPayload = kStages * kTile + kBYBytes + 2 * kBZBytes;  // 102
 constexpr int kWRing = 6;                // w_m rows in flight (shared by builders and epilogue)
 constexpr int kWAhead = 3;               // the producer loads w_m this many steps ahead of its X loads
 constexpr uint32_t kTmemCols = 512;      // D_Y x2 (128 columns each) + D_Z x2 chunks (128 each)
-#ifndef CPGN_TC_PREFETCH
-#define CPGN_TC_PREFETCH 0
-#endif
-// The producer asks L2 for the X tiles of the step this many steps ahead, so
-// that the shared-memory ring only has to cover L2 latency, not DRAM latency
-// under load.
-constexpr int kPrefetchSteps = CPGN_TC_PREFETCH;
-#ifndef CPGN_TC_L2PROMO
-#define CPGN_TC_L2PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_128B
-#endif
-constexpr CUtensorMapL2promotion kL2Promo = CPGN_TC_L2PROMO;
+constexpr CUtensorMapL2promotion kL2Promo = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
 
 struct Params {
     int N;
@@ -111,7 +98,6 @@ struct Params {
     float* P_c;         // [nib][ngr][mid][64]        c_m partial of a step
     int4* seg;          // [slot]: (b, g, y, 0) of the segment in a slot; b = -1 if unused
     int* status;
-    long long* trace;   // event timestamps of block 0 (trace builds only), else null
 };
 
 // Barriers, flags and small arrays, placed after the operand buffers in the
@@ -132,18 +118,6 @@ struct SmemCtl {
 constexpr uint32_t kDynSmem = kPayload + (uint32_t)sizeof(SmemCtl);
 static_assert(kDynSmem <= 227 * 1024, "shared memory above the per-block limit");
 
-// Optional event trace of block 0 (compiled in with -DCPGN_TC_TRACE): slot
-// ev * 1024 + idx receives clock64() at event ev, occurrence idx.
-#ifdef CPGN_TC_TRACE
-#define TC_TRACE(ev, idx)                                                                          \
-    do {                                                                                           \
-        if (p.trace && blockIdx.x == 0 && (idx) < 1024) p.trace[(ev) * 1024 + (idx)] = clock64(); \
-    } while (0)
-#else
-#define TC_TRACE(ev, idx) \
-    do {                  \
-    } while (0)
-#endif
 
 // Sum 16 per-lane values over the 32 lanes of a warp.  Afterwards lane l holds
 // in v[0] the warp total of column butterfly16_col(l) (lanes l and l^1 agree).
@@ -273,19 +247,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             int yg = -1;
             int64_t it = 0;
-            StepId pf = step_of(p, T0);  // the step kPrefetchSteps ahead
-            auto prefetch = [&]() {
-                const int nq = (int)imin(kGroup, p.nch - pf.g * kGroup);
-                const uint32_t bytes = 2u * p.pt.rows(pf.b) * 128u;
-                for (int cc = 0; cc < nq; ++cc)
-                    bulk_prefetch(p.planes + 2 * p.pt.tile(pf.b, pf.g * kGroup + cc, pf.m), bytes);
-                pf.next(p);
-            };
-            for (int64_t t = T0; t < T0 + kPrefetchSteps && t < T1; ++t) prefetch();
             StepId sp = step_of(p, T0), wsp = sp;  // wsp: the next step whose w_m row is loaded
             int64_t wl = 0;                         // w_m rows loaded so far
             for (int64_t t = T0; t < T1 && ok; ++t, sp.next(p)) {
-                if (t + kPrefetchSteps < T1) prefetch();
                 for (; ok && wl <= (t - T0) + kWAhead && T0 + wl < T1; ++wl, wsp.next(p)) {
                     const int ws = (int)(wl % kWRing);
                     if (!(ok = mbar_wait(smem_u32(&C.w_empty[ws]), (uint32_t)(((wl / kWRing) & 1) ^ 1), abort_s,
@@ -311,7 +275,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int slot = (int)(it & 1);
                 if (!(ok = mbar_wait(smem_u32(&C.empty[slot]), (uint32_t)(((it >> 1) & 1) ^ 1), abort_s, p.status)))
                     break;
-                TC_TRACE(0, (int)it);
                 const uint32_t fb = smem_u32(&C.full[slot]);
                 mbar_expect_tx(fb, 2 * nc * pbytes);
                 for (int cc = 0; cc < nc; ++cc) {
@@ -354,7 +317,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ys1 = p.sN > k0 + kKC ? (int)((imin(kKC, p.sN - k0 - kKC) + 15) / 16) : 0;
                 if (!(ok = mbar_wait(smem_u32(&C.dy_empty[db]), ph ^ 1, abort_s, p.status))) break;
                 if (!(ok = mbar_wait(smem_u32(&C.full[slot]), ph, abort_s, p.status))) break;
-                TC_TRACE(1, (int)tt);
                 tc_fence_after();
                 const uint32_t t_dy = t_dy0 + db * 128;
                 const uint64_t dx0 = sdesc(s_stage0 + (2 * slot) * kTile, 16, 1024), dby0 = sdesc(s_by, 16, 1024);
@@ -374,7 +336,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_commit(smem_u32(&C.dy_full[db]));
                 tc_commit(smem_u32(&C.empty[slot]));
                 if (run_last(p, t, T1, sp.m)) tc_commit(smem_u32(&C.by_empty));
-                TC_TRACE(2, (int)tt);
             }
             // every issued MMA must have completed before TMEM is freed
             tc_commit(smem_u32(&C.drain[0]));
@@ -471,7 +432,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int db = (int)(tb & 1), ws = (int)(tb % kWRing);
             if (!grp_wait(smem_u32(&C.bz_empty[db]), (uint32_t)(((tb >> 1) & 1) ^ 1))) return false;
             if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tb / kWRing) & 1))) return false;
-            if (et == 0) TC_TRACE(3, (int)tb);
             const uint32_t boff = db * kBZBytes;
             const float4* wv = reinterpret_cast<const float4*>(&C.wring[ws][rq]);
 #pragma unroll
@@ -490,7 +450,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&C.bz_full[db]));
-            if (et == 0) TC_TRACE(7, (int)tb);
             return true;
         };
         StepId sp = step_of(p, T0), nx = sp;
@@ -516,7 +475,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int db = (int)(tt & 1);
             const int ws = (int)(tt % kWRing);
             if (!(ok = grp_wait(smem_u32(&C.dy_full[db]), (uint32_t)((tt >> 1) & 1)))) break;
-            if (et == 0) TC_TRACE(4, (int)tt);
             tc_fence_after();
             const uint32_t ta = t_dy0 + db * 128 + cb + ((uint32_t)(q * 32) << 16);
 #pragma unroll
@@ -550,7 +508,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         C.red[0][et] + C.red[1][et] + C.red[2][et] + C.red[3][et];
                 named_sync(2, kWork);
             }
-            if (et == 0) TC_TRACE(5, (int)tt);
             const bool rl = run_last(p, t, T1, sp.m);
             if (rl || seg.zl == kLmax) {
                 const bool slot_ok = seg.zs < p.smax;
@@ -837,9 +794,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
 static EncodeTiledFn encode_fn() { return tc_encode_fn(); }
 
 
-#ifdef CPGN_TC_TRACE
-long long* tc_trace_ptr = nullptr;
-#endif
 
 }  // namespace tc
 
@@ -984,16 +938,6 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
     p.P_c = (float*)(wb += pz_b);
     p.seg = (int4*)(wb += pc_b);
     p.status = status;
-    p.trace = nullptr;
-#ifdef CPGN_TC_TRACE
-    {
-        static long long* trace_buf = nullptr;
-        if (!trace_buf) cudaMalloc(&trace_buf, 8 * 1024 * sizeof(long long));
-        cudaMemsetAsync(trace_buf, 0, 8 * 1024 * sizeof(long long), st);
-        p.trace = trace_buf;
-        tc_trace_ptr = trace_buf;
-    }
-#endif
     // ---- tensor map of the B_Y planes (rows of s_N elements; the pitch padding reads as zero)
     CUtensorMap tmBY;
     {
@@ -1057,10 +1001,3 @@ cp_status tc_mttkrp_planes(SplitCache& c, const void* planes, const Shape& s, Pt
 
 }  // namespace cpgn
 
-#ifdef CPGN_TC_TRACE
-// trace builds only: copy the last trace buffer (8 x 1024 int64) to the host
-extern "C" int cpgn_tc_trace_copy(long long* host) {
-    if (!cpgn::tc::tc_trace_ptr) return 1;
-    return cudaMemcpy(host, cpgn::tc::tc_trace_ptr, 8 * 1024 * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess;
-}
-#endif

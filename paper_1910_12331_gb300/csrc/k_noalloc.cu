@@ -12,13 +12,19 @@
 // The array is part of the library's device image: every GPU on which the
 // library's module is loaded holds it (CP_NOALLOC_SCRATCH_BYTES) until the
 // process exits.  Host code cannot use its name as a device address, so the
-// first call on each device asks the runtime for that device's address
-// (cudaGetSymbolAddress, with the device current) and caches it; that first
-// call may also load the module, so it should come before any stream capture.
-// Every call overwrites all of the scratch it reads (nothing accumulates from
-// an earlier call), and all calls share the one array: calls that overlap on
-// the GPU (two streams, two host threads) race and must be serialised by the
-// caller.
+// first call on each device (with that device current) asks the runtime for
+// the array's address there (cudaGetSymbolAddress) and caches it together
+// with the identity of the current CUDA context; a later call in another
+// context (after cudaDeviceReset, or once the primary context was released
+// and created again) looks the address up afresh instead of reusing a stale
+// one.  That first call also makes the runtime load the modules of every
+// kernel the call launches (through cudaFuncGetAttributes), which commits
+// their device memory, this array included: make the first call on a device
+// before any region in which nothing may be allocated, and before any
+// stream capture.  Every call overwrites all of the scratch it reads
+// (nothing accumulates from an earlier call), and all calls share the one
+// array: calls that overlap on the GPU (two streams, two host threads) race
+// and must be serialised by the caller.
 #include <math.h>
 
 #include <mutex>
@@ -41,22 +47,67 @@ static __device__ __align__(256) double g_matvec_scratch[kScratchDoubles];
 
 namespace {
 
-std::mutex g_addr_mu;
-double* g_addr[kMaxDevices] = {};
+// Identity of the current CUDA context (its unique id where the driver
+// offers cuCtxGetId, else its handle); 0 if none can be had.
+unsigned long long current_context_id() {
+    typedef int (*GetCurrentFn)(void**);
+    typedef int (*GetIdFn)(void*, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetIdFn)f;
+        cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    if (!get_current || get_current(&ctx) != 0 || !ctx) return 0;
+    unsigned long long id = 0;
+    if (get_id && get_id(ctx, &id) == 0) return id + 1;
+    return (unsigned long long)(uintptr_t)ctx;
+}
 
-// Device address of the scratch array on the current device (looked up once per device).
+struct ScratchAddr {
+    unsigned long long ctx = 0;  // context the address belongs to (0: none cached)
+    double* p = nullptr;
+};
+std::mutex g_addr_mu;
+ScratchAddr g_addr[kMaxDevices];
+
+__global__ void gram_direct_kernel(Shape s, Ptrs<const double> A, double* S);
+__global__ void gamma_direct_kernel(Shape s, const double* S, double* Gam);
+
+// Device address of the scratch array in the current device's current
+// context, looked up once per (device, context).  The lookup also loads the
+// modules of every kernel a call launches.
 cp_status scratch_on(int dev, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return CP_ERR_UNSUPPORTED;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_addr_mu);
-    if (!g_addr[dev]) {
+    ScratchAddr& c = g_addr[dev];
+    if (!c.p || ctx == 0 || c.ctx != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_matvec_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return CP_ERR_CUDA;
         }
-        g_addr[dev] = static_cast<double*>(p);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, gram_direct_kernel) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, gamma_direct_kernel) != cudaSuccess || preload_matvec_f64() != cudaSuccess) {
+            cudaGetLastError();
+            return CP_ERR_CUDA;
+        }
+        c.p = static_cast<double*>(p);
+        c.ctx = current_context_id();  // the lookup created the context if there was none
     }
-    *out = g_addr[dev];
+    *out = c.p;
     return CP_OK;
 }
 

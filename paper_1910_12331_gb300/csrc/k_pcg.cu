@@ -259,18 +259,6 @@ __device__ __forceinline__ void dot2_rows(const T* x, const T* y, const T* u, co
 
 }  // namespace
 
-#ifdef CPGN_PCG_TRACE
-__device__ long long g_pcg_trace[8 * 64];
-#define PCG_TRACE(ev)                                                                          \
-    do {                                                                                       \
-        if (blockIdx.x == 0 && threadIdx.x == 0 && it < 64) g_pcg_trace[(ev) * 64 + it] = clock64(); \
-    } while (0)
-#else
-#define PCG_TRACE(ev) \
-    do {              \
-    } while (0)
-#endif
-
 // ---- register-tiled row products on shared memory (row stride Rp = R rounded up to 4)
 template <typename T>
 struct V4;
@@ -509,7 +497,6 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         if (!(rsum > tol)) break;
         if (!isfinite(rsum) || !isfinite(rz)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
-        PCG_TRACE(0);
         // ---- Y^(p) = sum over the blocks of mode p of A^T Z, + beta Y^(p): fixed order
         {
             const T be = (T)beta;
@@ -561,16 +548,13 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
             }
         }
         __syncthreads();
-        PCG_TRACE(1);
         // ---- Q = lam W + W Gamma^(n,n) + A T^(n)^T, partial <W,Q>
         rows_mm<T>(sW, Gm, sA, Tt, (T)a.lam, sQ, rows, R, Rp);
         __syncthreads();
         double wq_h, wq_l, unused_h, unused_l;
         dot2_rows<T>(sW, sQ, nullptr, nullptr, lenp, red, wq_h, wq_l, unused_h, unused_l);
         if (threadIdx.x == 0) Slot<T>::put(part_wq + b, wq_h, wq_l);
-        PCG_TRACE(2);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
-        PCG_TRACE(3);
         double alpha;
         const double wq = gather_sum<T>(part_wq, (int)nb, bcast, rz, alpha);
         if (!isfinite(wq)) { set_status(status, CP_ERR_NONFINITE); break; }
@@ -589,9 +573,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
             Slot<T>::put(part_rn + b, rn_h, rn_l);
         }
         y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
-        PCG_TRACE(4);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
-        PCG_TRACE(5);
         double rz_new;
         reduce_r(rz, rz_new, rsum);
         ++it;
@@ -703,7 +685,6 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
     // (about 32 rows each) to shorten the barriers and reductions.
     int want = max_blocks > 0 ? max_blocks
                               : (sizeof(T) == 8 ? sms : (int)std::min<int64_t>(sms, (rows_total + 31) / 32));
-    if (const char* env = getenv(sizeof(T) == 8 ? "CPGN_PCG_BLOCKS_F64" : "CPGN_PCG_BLOCKS_F32")) want = atoi(env);
     static thread_local PcgGeom cache[2];
     PcgGeom& g = cache[sizeof(T) == 8];
     bool hit = g.N == s.N && g.R == s.R && g.want == want && g.sms == sms && g.dev == dev;
@@ -726,11 +707,6 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
     return CP_OK;
 }
 template cp_status launch_pcg<double>(PcgArgs<double>&, int, cudaStream_t);
-#ifdef CPGN_PCG_TRACE
-extern "C" int cpgn_pcg_trace_copy(long long* host) {
-    return cudaMemcpyFromSymbol(host, g_pcg_trace, sizeof(long long) * 8 * 64) != cudaSuccess;
-}
-#endif
 template cp_status launch_pcg<float>(PcgArgs<float>&, int, cudaStream_t);
 
 // ------------------------------------------------------------ plain matvec
@@ -768,6 +744,12 @@ __global__ void matvec_q_kernel(Shape s, Ptrs<const double> A, const double* Gam
         for (int z = 0; z < R; ++z) acc += a[z] * Gnp[r * R + z] * Yp[r * R + z];
     }
     Q.p[n][e] = acc;
+}
+
+cudaError_t preload_matvec_f64() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, matvec_y_kernel);
+    return e != cudaSuccess ? e : cudaFuncGetAttributes(&fa, matvec_q_kernel);
 }
 
 void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,

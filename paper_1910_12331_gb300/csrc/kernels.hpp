@@ -83,6 +83,8 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st);
 // Plain (non-persistent) FP64 matvec used by cp_gn_matvec: Q = (J^T J + lam I) W.
 void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
                        Ptrs<double> Q, double* Y, cudaStream_t st);
+// Loads the module of the plain matvec's kernels now (cudaFuncGetAttributes), not at their first launch.
+cudaError_t preload_matvec_f64();
 
 // ---- residual tensor in double-float, as bf16 planes in PlaneTiling layout (k_resid.cu)
 // scratch: resid_scratch_bytes(s) bytes (double-float copy of the factors and
