@@ -40,14 +40,20 @@ WORKLOAD = "collinear400"
 WORKLOAD_DESC = ("400x400x400 FP32 tensor, rank-50 N(0,1) factors with column collinearity 0.9, "
                  "1e-6 relative noise; R=50; seeded N(0,1) start")
 TARGET_STAT = 1e-8
+# The metric's name says "residual 1e-8"; on FP32-stored inputs with 1e-6 noise the relative residual
+# cannot fall below ~1e-6, so the solve is timed to relative stationarity instead (Algorithm 1's loop
+# test on sum||G||, made scale-free), with an FP64-accurate gradient.
+TARGET_NOTE = ("time to relative stationarity sum||G||/sum||M|| <= 1e-8 (FP64-accurate gradient) in place of "
+               "residual 1e-8, which FP32 storage and the 1e-6 noise floor make unreachable")
+CONFIG = {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
+          "target": f"sum||G||/sum||M|| <= {TARGET_STAT} with an FP64 gradient",
+          "target_note": TARGET_NOTE,
+          "step": "one full CP-GN solve (residual-form gradient every iteration, FP32 CG vectors)",
+          "l2": "inputs larger than L2 (X 256 MB, planes of E 256 MB)"}
 MAX_GN = 300
 EPS_CG = 1e-3
 CG_MAX = 250
 MU = 2.0
-# GN iterations the FP64 path needs on this workload and seed (measured on a
-# GB300 with this benchmark's FP64 mode); scales the CPU oracle's per-iteration time.
-GN_ITERS_FP64 = 51
-
 # DRAM traffic of the dominant kernels from one ncu capture each (profiles/pcg_kernel_collinear400.md,
 # profiles/resid_gradient_collinear400.md).  It is reported only while every source of the record
 # still has the SHA-1 it had when the counters were taken.
@@ -178,21 +184,50 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sel)}
 
 
-def cpu_oracle_sample(p, lam_hi, lam_lo, gn_iters, n_steps=1):
-    """The FP64 oracle (as it stands) timed on the host cores: n_steps GN
-    iterations of Algorithm 1 from the workload's starting point, scaled to a
-    time-to-target by the GN iteration count of the FP64 solve."""
+def oracle_solve(p, lam_hi, lam_lo):
+    """The FP64 oracle (as it stands) solving the workload to the same target
+    as the GPU: Algorithm 1 with CP-CG to eps_cg = 1e-3, dimension-tree
+    MTTKRP, the same lambda schedule and starting point.  Returns (seconds,
+    info, cores)."""
     import oracle
 
     oracle.build()
-    X, A = p["X"], [a.copy() for a in p["init"]]
-    lam, d = lam_hi, 0
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
-        A, lam, d, s, st = oracle.gn_step(X, A, lam, d, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, 0, True)
-    dt = (time.perf_counter() - t0) / n_steps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dt * gn_iters, dt, cores
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    _, st, info = oracle.gn_solve(p["X"], [a.copy() for a in p["init"]], lam_hi, lam_lo, lam_hi, MU, EPS_CG,
+                                  CG_MAX, TARGET_STAT, MAX_GN)
+    return time.perf_counter() - t0, dict(info, status=st), cores
+
+
+def oracle_gn_iteration(p, lam_hi, lam_lo, threads):
+    """One GN iteration of the oracle from the starting point on `threads`
+    threads (seconds)."""
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.gn_step(p["X"], [a.copy() for a in p["init"]], lam_hi, 0, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, 0, True)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+    return dt
+
+
+def cpu_baseline_record(p, lam_hi, lam_lo):
+    """The oracle's full solve on all host cores (measured), plus the one-core
+    figure: one GN iteration on one thread against one on all of them, which
+    scales the measured full solve (a projection, marked as such)."""
+    t_all, info, cores = oracle_solve(p, lam_hi, lam_lo)
+    it1 = oracle_gn_iteration(p, lam_hi, lam_lo, 1)
+    itn = oracle_gn_iteration(p, lam_hi, lam_lo, cores)
+    return {"value": t_all, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": (f"one full FP64 oracle solve of the workload to the same target, timed once: "
+                       f"{info['updates']} GN and {info['cg_iters']} CG iterations, stationarity "
+                       f"{info['stationarity']:.3g}, converged={info['converged']}"),
+            "one_core": {"value": t_all * it1 / itn, "unit": "s", "cores": 1,
+                         "kind": "projected: measured solve x (one GN iteration on 1 thread / on all threads)",
+                         "gn_iteration_s_1_core": it1, "gn_iteration_s_all_cores": itn}}
 
 
 def run_reference(args):
@@ -203,19 +238,21 @@ def run_reference(args):
 
     p = datagen.workload(WORKLOAD, seed=0)
     lam_hi, lam_lo = lam_thresholds(p["init"])
-    gn_iters = GN_ITERS_FP64 or 30
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, per_it, cores = cpu_oracle_sample(p, lam_hi, lam_lo, gn_iters)
-        if i >= args.warmup:
-            vals.append(v)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # warm-up: one GN iteration each (pages in the oracle and the workload; a solve keeps no other state)
+    for _ in range(args.warmup):
+        oracle_gn_iteration(p, lam_hi, lam_lo, cores)
+    vals, info = [], None
+    for _ in range(args.steps):
+        t, info, cores = oracle_solve(p, lam_hi, lam_lo)
+        vals.append(t)
     value = statistics.median(vals)
-    sample = (f"one GN iteration of the FP64 oracle per step (dimension-tree MTTKRP, CG to 1e-3) on the "
-              f"full workload, times {gn_iters} GN iterations to target")
+    sample = (f"each timed step is one full FP64 oracle solve of the workload to the target ({info['updates']} GN, "
+              f"{info['cg_iters']} CG iterations); each warm-up step one GN iteration")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "target": f"sum||G||/sum||M|| <= {TARGET_STAT}"},
+            "config": dict(CONFIG, parallelism=f"replicas x{args.gpus}"),
             "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -479,56 +516,62 @@ def main():
             pg.destroy_process_group()
         return
 
-    # roofline of the dominant phase inside the timed solve
-    mt_phase = last["mttkrp_ms"] / 1e3
-    pcg_phase = last["pcg_ms"] / 1e3
-    gn = last["iters"] + (1 if last["converged"] else 0)
-    mt_per_launch = mt_phase / max(gn, 1)
-    if mt_phase >= pcg_phase:
-        # residual-form gradient per GN iteration: the reconstruction reads X (4 B) and writes the
-        # bf16 hi/lo planes of E (4 B), the MTTKRP of E reads the planes (4 B) -- 12 B per element
-        grad_bytes = 12.0 * total
-        ach = grad_bytes / mt_per_launch / 1e9
-        rec = profiled("gradient")
-        roof = {"kernel": "residual-form gradient phase (tcgen05 reconstruction of E + tcgen05 MTTKRP of E)",
-                "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": rec["dram_bytes"] if rec else None}
-    else:
-        cg_it = max(last["cg_iters_total"], 1)
-        rows = sum(X.shape)
-        # twelve FP32 passes over the CG vectors per iteration (W, Q, V, R, Z read and written)
-        state_bytes = 4.0 * rows * R * 12
-        ach = state_bytes / (pcg_phase / cg_it) / 1e9
-        rec = profiled("pcg")
-        traffic = rec["dram_bytes"] / rec["cg_iters"] if rec and rec["cg_iters"] else None
-        roof = {"kernel": "persistent CP-CG kernel pcg_kernel<float> (per CG iteration)", "bound": "hbm",
-                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic,
-                "us_per_cg_iteration": pcg_phase / cg_it * 1e6,
-                "note": "latency-bound (three grid barriers per iteration); state L2-resident"}
+    # roofline of the dominant phase inside the timed solve: the gradient of every GN iteration
+    # (reconstruction of E on the tensor cores + the tensor-core MTTKRP of E), timed with CUDA events on
+    # the handle's stream around the phase.  Algorithmic bytes of a gradient: one read of the FP32 X
+    # (4 B per element); the planes of E written and read back are this design's own traffic, counted
+    # in `traffic` (ncu DRAM bytes of the phase's kernels per gradient) and not in `achieved`.
+    n_grad = last["iters"] + (1 if last["converged"] else 0)
+    grad_s = last["mttkrp_ms"] / 1e3 / max(n_grad, 1)
+    alg_bytes = 4.0 * total
+    ach = alg_bytes / grad_s / 1e9
+    rec = profiled("gradient")
+    roof = {"kernel": "gradient phase of a GN iteration: recon_tc_kernel (E = X - [[A]]) + mttkrp_tc_kernel on E",
+            "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": rec["dram_bytes"] if rec else None, "algorithmic_bytes": alg_bytes,
+            "us_per_gradient": grad_s * 1e6, "gradients": n_grad, "peak_source": "measured (MEASURED_PEAKS.json)"}
+    # the CG kernel: latency-bound; its floor is three grid barriers per iteration
+    cg_it = max(last["cg_iters_total"], 1)
+    pcg_s = last["pcg_ms"] / 1e3
+    barrier_us = api.cp_probe_grid_barrier(local, last["cg_blocks"], 512)
+    cg_roof = {"kernel": "pcg_kernel<float>", "bound": "latency (grid barriers)",
+               "us_per_cg_iteration": pcg_s / cg_it * 1e6, "barrier_us": barrier_us, "blocks": last["cg_blocks"],
+               "floor_us": 3 * barrier_us, "frac": 3 * barrier_us / (pcg_s / cg_it * 1e6),
+               "cg_iterations": cg_it}
+    # the plain FP64 path: FP64-ALU-bound; its MTTKRP against the measured DFMA rate
+    fp64_peak = api.cp_probe_fp64_fma(local)
+    Xf = X.double()
+    api.cp_mttkrp_all(h, Xf, init, M, prec="fp64")
+    torch.cuda.synchronize()
+    m0.record(stream)
+    for _ in range(5):
+        api.cp_mttkrp_all(h, Xf, init, M, prec="fp64")
+    m1.record(stream)
+    torch.cuda.synchronize()
+    t_mt64 = m0.elapsed_time(m1) / 1e3 / 5
+    del Xf
+    fp64_roof = {"kernel": "FP64 all-mode MTTKRP (mttkrp_y/z_kernel)", "bound": "fp64 alu",
+                 "achieved": mt_flops / t_mt64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                 "frac": mt_flops / t_mt64 / 1e12 / fp64_peak, "us": t_mt64 * 1e6,
+                 "peak_source": "measured (cp_probe_fp64_fma)"}
     cpu = None
     if not args.no_cpu_baseline:
-        gn64 = res64["iters"] + 1
-        v, per_it, cores = cpu_oracle_sample(p, lam_hi, lam_lo, gn64)
-        cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"one GN iteration of the FP64 oracle ({per_it:.2f} s) times the {gn64} GN iterations "
-                         f"the FP64 GPU path needed"}
+        cpu = cpu_baseline_record(p, lam_hi, lam_lo)
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3/f32/f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
-                   "target": f"sum||G||/sum||M|| <= {TARGET_STAT} with an FP64 gradient",
-                   "step": "one full CP-GN solve (residual-form gradient every iteration, FP32 CG vectors)",
-                   "l2": "inputs larger than L2 (X 256 MB, split planes 256 MB)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": dict(CONFIG, parallelism=f"replicas x{ws}"),
         "converged": converged, "gn_iters": last["iters"], "gradient": "residual form -E_(n) P^(n) every iteration",
         "cg_iters": last["cg_iters_total"], "stationarity": last["stationarity"],
         "phase_ms": {"mttkrp": last["mttkrp_ms"], "pcg": last["pcg_ms"], "device": last["device_ms"]},
         "mttkrp": {"tflops": mt_flops / t_mt / 1e12, "us": t_mt * 1e6, "gbs": mt_bytes / t_mt / 1e9,
-                   "prec": "bf16x3"},
+                   "hbm_frac": mt_bytes / t_mt / 1e9 / hbm_peak, "prec": "bf16x3"},
         "fp64_path": {"time_to_target_s": t64, "gn_iters": res64["iters"], "converged": bool(res64["converged"]),
                       "speedup_of_mixed": t64 / t_step},
         "roofline": roof,
+        "roofline_cg": cg_roof,
+        "roofline_fp64": fp64_roof,
         "cpu_baseline": cpu,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "cp_loss": loss_info,

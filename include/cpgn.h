@@ -138,6 +138,7 @@ typedef struct {
     double pcg_ms;           /* device time of the CG kernel */
     double step_ms;          /* device time of the whole step */
     int kernel_launches;     /* kernels this step launched */
+    int cg_blocks;           /* blocks of the persistent CG kernel's launch (0 if it did not run) */
 } cp_gn_stats;
 
 /* Human-readable name of a status code (static storage; unknown codes give
@@ -193,10 +194,19 @@ cp_status cp_gradient(cp_handle h, const cp_desc* desc, const void* X, const dou
 /* Implicit Gauss-Newton matvec of Algorithm 2 (Eq. (3.4)):
  * Q^(n) = lambda W^(n) + W^(n) Gamma^(n,n) + sum_{p != n} A^(n) (Gamma^(n,p) * Y^(p))^T,
  * Y^(p) = A^(p)^T W^(p), i.e. Q = (J^T J + lambda I) W with J the Jacobian of
- * Eq. (3.1).  FP64.  Gamma is formed from A inside the call.
- * Asynchronous.  Errors: CP_ERR_ARG, CP_ERR_NOMEM, CP_ERR_CUDA. */
-cp_status cp_gn_matvec(cp_handle h, const cp_desc* desc, const double* const* A, const double* const* W,
-                       double lambda, double* const* Q);
+ * Eq. (3.1); with reg = CP_REG_DIAG, Q = (J^T J + lambda diag(J^T J)) W
+ * (Section 3.2's alternative damping; see cp_reg).
+ * grams: NULL (the Gram matrices S^(n) = A^(n)^T A^(n) are formed from A
+ * inside the call) or a DEVICE array of N row-major R x R FP64 matrices S^(n)
+ * (read; Gamma^(n,p) is formed from them).
+ * prec: CP_PREC_FP64 -- every product and sum in FP64; CP_PREC_BF16X3 or
+ * CP_PREC_RESIDUAL -- the arithmetic of the mixed CG (cg_fp32 = 1): A, W and
+ * Gamma rounded to FP32 once (Gamma formed in FP64), then Y, T^(n) and Q in
+ * FP32 fused multiply-adds; Q is returned in FP64.
+ * Asynchronous.  Errors: CP_ERR_ARG (null or aliased pointers, bad descriptor,
+ * lambda < 0 or non-finite, unknown reg or prec), CP_ERR_NOMEM, CP_ERR_CUDA. */
+cp_status cp_gn_matvec(cp_handle h, const cp_desc* desc, const double* const* A, const double* grams,
+                       const double* const* W, double lambda, int reg, double* const* Q, cp_precision prec);
 
 /* One CP-GN iteration (Algorithm 1 loop body): MTTKRP, Gram/Gamma, gradient,
  * preconditioner (Gamma^(n,n) + lambda D)^{-1} with D = I or diag(Gamma^(n,n))
@@ -238,6 +248,7 @@ typedef struct {
     double pcg_ms;           /* summed device time of the CG kernels */
     double device_ms;        /* summed device time of all steps */
     long long kernel_launches; /* kernels launched by the solve */
+    int cg_blocks;           /* blocks of the last persistent CG launch */
 } cp_solve_result;
 
 /* Run Algorithm 1 from the factors in A (in/out) until a target of `opts` is
@@ -347,6 +358,28 @@ cp_status cp_batch_plan_launch(cp_handle h, cp_batch_plan plan);
 cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result* results);
 cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads);
 cp_status cp_batch_plan_destroy(cp_batch_plan plan);
+
+/* ---------------------------------------------------------------------------
+ * Measurement probes: the denominators of the rooflines of the kernels that
+ * are bound by neither HBM nor the tensor cores.
+ *
+ * cp_probe_grid_barrier times `iters` back-to-back grid barriers of the kind
+ * the persistent CG kernel (Algorithm 2) takes three of per iteration: the
+ * same barrier code, `blocks` co-resident blocks of `threads` threads launched
+ * cooperatively on `device`, nothing else between the barriers.  Writes the
+ * device time per barrier in microseconds (launch overhead removed by
+ * differencing against a one-barrier launch).  Synchronises.  Errors:
+ * CP_ERR_ARG, CP_ERR_UNSUPPORTED (the blocks cannot be co-resident),
+ * CP_ERR_NOMEM, CP_ERR_CUDA, CP_ERR_TIMEOUT (a barrier's bounded wait expired).
+ *
+ * cp_probe_fp64_fma measures the FP64 fused multiply-add rate of `device`
+ * (eight independent chains per thread, eight blocks of 256 threads per SM),
+ * in TFLOP/s counting two flops per FMA: the ceiling of the plain FP64 path,
+ * whose MTTKRP and CG kernels are FP64-ALU-bound.  Synchronises.  Errors:
+ * CP_ERR_ARG, CP_ERR_NOMEM, CP_ERR_CUDA.
+ * Both work on the legacy default stream and restore the caller's device. */
+cp_status cp_probe_grid_barrier(int device, int blocks, int threads, int iters, double* us_per_barrier);
+cp_status cp_probe_fp64_fma(int device, double* tflops);
 
 /* ---------------------------------------------------------------------------
  * Matvec without device allocation.  The paper has no counterpart: this call

@@ -92,6 +92,12 @@ def _load():
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, dp]
             lib.orc_gn_step.restype = ctypes.c_int
+            lib.orc_gn_solve.argtypes = [d, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+            lib.orc_gn_solve.restype = ctypes.c_int
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_threads.restype = None
             lib.orc_residual.argtypes = [d, dp, dp]
             lib.orc_residual.restype = ctypes.c_double
             lib.orc_als_sweep.argtypes = [d, dp, dp, ctypes.c_double]
@@ -227,6 +233,27 @@ def gn_step(X, A, lam, direction, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind=0
     s = dict(zip(keys, stats.tolist()))
     s["cg_iters"] = int(s["cg_iters"])
     return _unpack(Abuf, dims, R), float(l[0]), dr.value, s, st
+
+
+def gn_solve(X, A, lam0, lam_lo, lam_hi, mu, eps_cg, maxit, target, max_gn, use_dt=True, reg=REG_IDENTITY):
+    """Algorithm 1 until the entry point of an iteration has
+    sum||G||/sum||M|| <= target (no update there) or max_gn updates.
+    Returns (A_new, status, dict(updates, cg_iters, stationarity, converged, lam))."""
+    X = _x64(X)
+    dims, R = list(X.shape), A[0].shape[1]
+    Abuf = _pack(A)
+    out = np.zeros(5)
+    st = _load().orc_gn_solve(ctypes.byref(_desc(dims, R)), _ptr(X), _ptr(Abuf), float(lam0), float(lam_lo),
+                              float(lam_hi), float(mu), float(eps_cg), int(maxit), float(target), int(max_gn),
+                              int(bool(use_dt)), int(reg), _ptr(out))
+    info = {"updates": int(out[0]), "cg_iters": int(out[1]), "stationarity": float(out[2]),
+            "converged": bool(out[3]), "lam": float(out[4])}
+    return _unpack(Abuf, dims, R), st, info
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    _load().orc_set_threads(int(n))
 
 
 def residual(X, A):

@@ -22,6 +22,9 @@
  * the pins live in the CPU test-suite.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -483,6 +486,53 @@ void orc_lambda_next(double* lam, int* dir, double lo, double hi, double mu) {
 /* ------------------------------------------------------------------ GN step */
 
 /* One iteration of CP-GN, Algorithm 1: M^(n) for all n, Gamma^(n,p), G^(n),
+ * then Algorithm 1's loop test (stop_ratio > 0: if sum_n ||G^(n)||_F <=
+ * stop_ratio sum_n ||M^(n)||_F -- the scale-free reading of the test on
+ * sum_n ||G^(n)||_F -- the entry point is accepted: no CG, no update,
+ * *stopped = 1), else CP-CG with the current lambda, A^(n) += V^(n), and
+ * lambda advances by the varying rule (the lambda of the next iteration).
+ * stats as orc_gn_step. */
+static int gn_iteration(const orc_desc* d, const double* X, double* A, double* lam, int* dir, double lam_lo,
+                        double lam_hi, double mu, double eps_cg, int maxit, int beta_kind, int use_dt, int reg,
+                        double stop_ratio, double* stats, int* stopped) {
+    const int N = d->N, R = d->R;
+    const int64_t len = factor_total(d);
+    double* M = (double*)malloc(sizeof(double) * len);
+    double* G = (double*)malloc(sizeof(double) * len);
+    double* V = (double*)calloc((size_t)len, sizeof(double));
+    double* S = (double*)malloc(sizeof(double) * (size_t)N * R * R);
+    double* Gam = (double*)malloc(sizeof(double) * (size_t)N * N * R * R);
+    double gnorm[ORC_MAXN];
+    if (use_dt) orc_mttkrp_dt(d, X, A, M); else orc_mttkrp_def(d, X, A, M);
+    orc_gram(d, A, S);
+    orc_gamma(d, S, Gam);
+    orc_gradient(d, A, Gam, M, G, gnorm);
+    double gsum = 0.0;
+    for (int n = 0; n < N; ++n) gsum += gnorm[n];
+    const double msum = fro_sum(d, M);
+    int iters = 0;
+    double rnorm = 0.0;
+    const double lam_used = *lam;
+    int status = ORC_OK;
+    *stopped = stop_ratio > 0.0 && gsum <= stop_ratio * msum;
+    if (!*stopped) {
+        status = orc_pcg(d, A, Gam, G, lam_used, reg, eps_cg, maxit, beta_kind, V, &iters, &rnorm);
+        if (status == ORC_OK || status == ORC_WARN_CG_MAXIT) {
+            for (int64_t i = 0; i < len; ++i) A[i] += V[i];
+            orc_lambda_next(lam, dir, lam_lo, lam_hi, mu);
+        }
+    }
+    stats[0] = gsum;
+    stats[1] = fro_sum(d, V);
+    stats[2] = lam_used;
+    stats[3] = iters;
+    stats[4] = rnorm;
+    stats[5] = msum;
+    free(M); free(G); free(V); free(S); free(Gam);
+    return status;
+}
+
+/* One iteration of CP-GN, Algorithm 1: M^(n) for all n, Gamma^(n,p), G^(n),
  * CP-CG with the current lambda, A^(n) += V^(n); then lambda advances by the
  * varying rule (the lambda of the next iteration).
  * stats[0] = sum_n ||G^(n)||_F at the entry point, stats[1] = sum_n ||V^(n)||_F,
@@ -493,36 +543,50 @@ void orc_lambda_next(double* lam, int* dir, double lo, double hi, double mu) {
 int orc_gn_step(const orc_desc* d, const double* X, double* A, double* lam, int* dir, double lam_lo,
                 double lam_hi, double mu, double eps_cg, int maxit, int beta_kind, int use_dt, int reg,
                 double* stats) {
-    const int N = d->N, R = d->R;
-    const int64_t len = factor_total(d);
-    double* M = (double*)malloc(sizeof(double) * len);
-    double* G = (double*)malloc(sizeof(double) * len);
-    double* V = (double*)malloc(sizeof(double) * len);
-    double* S = (double*)malloc(sizeof(double) * (size_t)N * R * R);
-    double* Gam = (double*)malloc(sizeof(double) * (size_t)N * N * R * R);
-    double gnorm[ORC_MAXN];
-    if (use_dt) orc_mttkrp_dt(d, X, A, M); else orc_mttkrp_def(d, X, A, M);
-    orc_gram(d, A, S);
-    orc_gamma(d, S, Gam);
-    orc_gradient(d, A, Gam, M, G, gnorm);
-    double gsum = 0.0;
-    for (int n = 0; n < N; ++n) gsum += gnorm[n];
-    int iters = 0;
-    double rnorm = 0.0;
-    const double lam_used = *lam;
-    int status = orc_pcg(d, A, Gam, G, lam_used, reg, eps_cg, maxit, beta_kind, V, &iters, &rnorm);
-    if (status == ORC_OK || status == ORC_WARN_CG_MAXIT) {
-        for (int64_t i = 0; i < len; ++i) A[i] += V[i];
-        orc_lambda_next(lam, dir, lam_lo, lam_hi, mu);
+    int stopped = 0;
+    return gn_iteration(d, X, A, lam, dir, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind, use_dt, reg, 0.0, stats,
+                        &stopped);
+}
+
+/* Algorithm 1 to a target: GN iterations from A (in/out) with lambda starting
+ * at lam0 in the decreasing direction, until the entry point of an iteration
+ * has sum_n ||G^(n)||_F <= target sum_n ||M^(n)||_F (converged; that
+ * iteration applies no update) or max_gn updates have been applied.
+ * out[0] = updates applied, out[1] = CG iterations in all, out[2] = the last
+ * sum||G|| / sum||M||, out[3] = 1 if converged, out[4] = lambda after the last
+ * update.  Returns the status of the last iteration (ORC_WARN_CG_MAXIT is not
+ * an error here). */
+int orc_gn_solve(const orc_desc* d, const double* X, double* A, double lam0, double lam_lo, double lam_hi,
+                 double mu, double eps_cg, int maxit, double target, int max_gn, int use_dt, int reg,
+                 double* out) {
+    double lam = lam0, stats[6];
+    int dir = 0, status = ORC_OK, updates = 0, cg = 0, stopped = 0;
+    double ratio = 0.0;
+    while (updates < max_gn) {
+        status = gn_iteration(d, X, A, &lam, &dir, lam_lo, lam_hi, mu, eps_cg, maxit, 0, use_dt, reg, target,
+                              stats, &stopped);
+        ratio = stats[5] > 0.0 ? stats[0] / stats[5] : 0.0;
+        if (stopped) break;
+        if (status != ORC_OK && status != ORC_WARN_CG_MAXIT) break;
+        cg += (int)stats[3];
+        ++updates;
     }
-    stats[0] = gsum;
-    stats[1] = fro_sum(d, V);
-    stats[2] = lam_used;
-    stats[3] = iters;
-    stats[4] = rnorm;
-    stats[5] = fro_sum(d, M);
-    free(M); free(G); free(V); free(S); free(Gam);
-    return status;
+    out[0] = updates;
+    out[1] = cg;
+    out[2] = ratio;
+    out[3] = stopped;
+    out[4] = lam;
+    return status == ORC_WARN_CG_MAXIT ? ORC_OK : status;
+}
+
+/* Threads of the OpenMP loops from now on (a timing aid: 1 gives the
+ * one-core figure). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
 }
 
 /* ----------------------------------------------------------------- residual */

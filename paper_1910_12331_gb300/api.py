@@ -31,7 +31,7 @@ SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_w
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
            "cp_residual", "cp_residual_sums", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
            "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads",
-           "cp_batch_plan_destroy")
+           "cp_batch_plan_destroy", "cp_probe_grid_barrier", "cp_probe_fp64_fma")
 
 
 class cp_desc(ctypes.Structure):
@@ -53,7 +53,7 @@ class cp_gn_stats(ctypes.Structure):
                 ("update_norm_sum", ctypes.c_double), ("factor_norm_sum", ctypes.c_double),
                 ("lam_used", ctypes.c_double), ("cg_rnorm", ctypes.c_double), ("rel_residual", ctypes.c_double),
                 ("entry_residual", ctypes.c_double), ("mttkrp_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("cg_blocks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +69,8 @@ class cp_solve_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("iters_refined", ctypes.c_int),
                 ("cg_iters_total", ctypes.c_int), ("converged", ctypes.c_int), ("stationarity", ctypes.c_double),
                 ("rel_residual", ctypes.c_double), ("lam", ctypes.c_double), ("mttkrp_ms", ctypes.c_double),
-                ("pcg_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+                ("pcg_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+                ("cg_blocks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -123,7 +124,7 @@ def load(build_if_missing: bool = False):
         L.cp_workspace_size.argtypes = [vp, pd, i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
         L.cp_mttkrp_all.argtypes = [vp, pd, vp, vp, vp, i]
         L.cp_gradient.argtypes = [vp, pd, vp, vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(d)]
-        L.cp_gn_matvec.argtypes = [vp, pd, vp, vp, d, vp]
+        L.cp_gn_matvec.argtypes = [vp, pd, vp, vp, vp, d, i, vp, i]
         L.cp_gn_step.argtypes = [vp, pd, vp, vp, ctypes.POINTER(cp_gn_params), ctypes.POINTER(cp_gn_stats)]
         L.cp_gn_solve.argtypes = [vp, pd, vp, vp, ctypes.POINTER(cp_gn_params), ctypes.POINTER(cp_solve_opts),
                                   ctypes.POINTER(cp_solve_result)]
@@ -139,6 +140,8 @@ def load(build_if_missing: bool = False):
         L.cp_batch_plan_results.argtypes = [vp, vp, ctypes.POINTER(cp_batch_result)]
         L.cp_batch_plan_threads.argtypes = [vp, ctypes.POINTER(i)]
         L.cp_batch_plan_destroy.argtypes = [vp]
+        L.cp_probe_grid_barrier.argtypes = [i, i, i, i, ctypes.POINTER(d)]
+        L.cp_probe_fp64_fma.argtypes = [i, ctypes.POINTER(d)]
         for name in SYMBOLS:
             if name != "cp_status_string":
                 getattr(L, name).restype = ctypes.c_int
@@ -318,7 +321,11 @@ def cp_gradient(h: Handle, X, A, G=None, prec="fp64"):
     return G, list(gn), list(mn)
 
 
-def cp_gn_matvec(h: Handle, A, W, lam, Q=None):
+def cp_gn_matvec(h: Handle, A, W, lam, Q=None, grams=None, reg="identity", prec="fp64"):
+    """Q = (J^T J + lam D) W with D = I (reg="identity") or diag(J^T J)
+    (reg="diag"); grams: optional (N, R, R) float64 CUDA tensor of the Gram
+    matrices A^(n)^T A^(n); prec "fp64" or the mixed CG's FP32 arithmetic
+    ("bf16x3" / "residual")."""
     R = A[0].shape[1]
     shape = [a.shape[0] for a in A]
     for n in range(len(A)):
@@ -331,13 +338,17 @@ def cp_gn_matvec(h: Handle, A, W, lam, Q=None):
             raise ValueError("A and W must be on one device")
     if A[0].device.index != h.device:
         raise ValueError(f"A is on {A[0].device}, the handle on cuda:{h.device}")
+    if grams is not None:
+        if not (grams.is_cuda and grams.dtype == torch.float64 and grams.is_contiguous()
+                and tuple(grams.shape) == (len(A), R, R) and grams.device == A[0].device):
+            raise ValueError(f"grams: expected a contiguous CUDA float64 tensor of shape ({len(A)}, {R}, {R})")
     if Q is None:
         Q = [torch.empty_like(a) for a in A]
     _check_outputs(Q, shape, R, "Q", A[0].device)
     h._bind_stream()
     d = make_desc(shape, R, torch.float64)
-    _check(load().cp_gn_matvec(h.h, ctypes.byref(d), _ptr_array(A), _ptr_array(W), float(lam), _ptr_array(Q)),
-           "cp_gn_matvec")
+    _check(load().cp_gn_matvec(h.h, ctypes.byref(d), _ptr_array(A), grams.data_ptr() if grams is not None else None,
+                               _ptr_array(W), float(lam), REG[reg], _ptr_array(Q), PREC[prec]), "cp_gn_matvec")
     return Q
 
 
@@ -526,3 +537,19 @@ def cp_gn_matvec_noalloc(A, W, lam, Q):
     _check(load().cp_gn_matvec_noalloc(ctypes.byref(d), _ptr_array(A), _ptr_array(W), float(lam), _ptr_array(Q),
                                        st), "cp_gn_matvec_noalloc")
     return Q
+
+
+def cp_probe_grid_barrier(device: int, blocks: int, threads: int = 512, iters: int = 20000) -> float:
+    """Device time of one grid barrier of the persistent CG kernel's kind, in
+    microseconds, with `blocks` co-resident blocks of `threads` threads."""
+    us = ctypes.c_double()
+    _check(load().cp_probe_grid_barrier(int(device), int(blocks), int(threads), int(iters), ctypes.byref(us)),
+           "cp_probe_grid_barrier")
+    return us.value
+
+
+def cp_probe_fp64_fma(device: int) -> float:
+    """Measured FP64 FMA rate of the device in TFLOP/s (2 flops per FMA)."""
+    t = ctypes.c_double()
+    _check(load().cp_probe_fp64_fma(int(device), ctypes.byref(t)), "cp_probe_fp64_fma")
+    return t.value

@@ -60,6 +60,7 @@ struct cp_handle_s {
     SplitCache split;             // bf16 planes of X (tensor-core path)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
     int launches = 0;             // kernels launched by the current call
+    int cg_blocks = 0;            // blocks of the last persistent CG launch
 };
 
 static cp_status ensure_events(cp_handle h) {
@@ -351,24 +352,36 @@ cp_status cp_gradient(cp_handle h, const cp_desc* d, const void* X, const double
     return h->h_stats->status ? (cp_status)h->h_stats->status : CP_OK;
 }
 
-cp_status cp_gn_matvec(cp_handle h, const cp_desc* d, const double* const* A, const double* const* W, double lambda,
-                       double* const* Q) {
+cp_status cp_gn_matvec(cp_handle h, const cp_desc* d, const double* const* A, const double* grams,
+                       const double* const* W, double lambda, int reg, double* const* Q, cp_precision prec) {
     if (!h) return CP_ERR_ARG;
     CP_TRY(check_desc(d));
     CP_TRY(check_ptrs((const void* const*)A, d->order));
     CP_TRY(check_ptrs((const void* const*)W, d->order));
     CP_TRY(check_ptrs((const void* const*)Q, d->order));
-    if (aliased((const void* const*)Q, d->order, (const void* const*)A, d->order, nullptr)) return CP_ERR_ARG;
+    if (aliased((const void* const*)Q, d->order, (const void* const*)A, d->order, grams)) return CP_ERR_ARG;
     if (aliased((const void* const*)Q, d->order, (const void* const*)W, d->order, nullptr)) return CP_ERR_ARG;
     if (!(lambda >= 0.0) || !isfinite(lambda)) return CP_ERR_ARG;
+    if (reg != CP_REG_IDENTITY && reg != CP_REG_DIAG) return CP_ERR_ARG;
+    if (prec != CP_PREC_FP64 && prec != CP_PREC_BF16X3 && prec != CP_PREC_RESIDUAL) return CP_ERR_ARG;
     DeviceGuard g(h->device);
     const Shape s = make_shape(d);
     CP_TRY(ensure_common(h, s));
     CP_TRY(grow(h->Y, (size_t)s.N * s.R * s.R * sizeof(double)));
     const Ptrs<const double> Ap = ptrs_of(A, s.N);
-    CP_TRY(gram_gamma(h, s, Ap));
-    launch_matvec_f64(s, Ap, (const double*)h->Gam.p, ptrs_of(W, s.N), lambda, ptrs_of(Q, s.N), (double*)h->Y.p,
-                      h->stream);
+    if (grams) {  // the caller's Gram matrices: Gamma from them directly
+        launch_gamma(s, grams, 1, (double*)h->S.p, (double*)h->Gam.p, nullptr, h->stream);
+        CUDA_TRY(cudaGetLastError());
+    } else {
+        CP_TRY(gram_gamma(h, s, Ap));
+    }
+    const bool diag = reg == CP_REG_DIAG;
+    if (prec == CP_PREC_FP64)
+        launch_matvec<double>(s, Ap, (const double*)h->Gam.p, ptrs_of(W, s.N), lambda, diag, ptrs_of(Q, s.N),
+                              (double*)h->Y.p, h->stream);
+    else
+        launch_matvec<float>(s, Ap, (const double*)h->Gam.p, ptrs_of(W, s.N), lambda, diag, ptrs_of(Q, s.N),
+                             (float*)h->Y.p, h->stream);
     CUDA_TRY(cudaGetLastError());
     return CP_OK;
 }
@@ -431,6 +444,7 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     a.spin_limit = p->spin_limit > 0 ? p->spin_limit : kDefaultSpin;
     CUDA_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(GridBarrier), h->stream));
     CP_TRY(launch_pcg<T>(a, 0, h->stream));
+    h->cg_blocks = a.nblocks;
     return CP_OK;
 }
 
@@ -510,6 +524,7 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
         st->pcg_ms = t23;  // CG kernel plus the factor update
         st->step_ms = t03;
         st->kernel_launches = h->launches;
+        st->cg_blocks = h->cg_blocks;
     }
     if ((status == CP_OK || status == CP_WARN_CG_MAXIT) && !hs.stopped) lambda_advance(p);
     return status;
@@ -569,6 +584,7 @@ cp_status cp_gn_solve(cp_handle h, const cp_desc* d, const void* X, double* cons
         res->pcg_ms += st.pcg_ms;
         res->device_ms += st.step_ms;
         res->kernel_launches += st.kernel_launches;
+        res->cg_blocks = st.cg_blocks;
         res->stationarity = st.m_norm_sum > 0 ? st.grad_norm_sum / st.m_norm_sum : 0.0;
         if (status != CP_OK && status != CP_WARN_CG_MAXIT) break;
         if (st.stopped) {  // no update was applied: the entry point met the target

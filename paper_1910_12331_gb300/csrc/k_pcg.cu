@@ -710,22 +710,29 @@ template cp_status launch_pcg<double>(PcgArgs<double>&, int, cudaStream_t);
 template cp_status launch_pcg<float>(PcgArgs<float>&, int, cudaStream_t);
 
 // ------------------------------------------------------------ plain matvec
+// The implicit matvec as three plain kernels, in FP64 or (T = float) in the
+// FP32 arithmetic of the mixed CG: A, W and Gamma rounded to FP32 once, every
+// product and sum in FP32.
 // Y[p][r][z] = sum_l A^(p)[l][r] W^(p)[l][z]; one thread per entry.
-__global__ void matvec_y_kernel(Shape s, Ptrs<const double> A, Ptrs<const double> W, double* Y) {
+template <typename T>
+__global__ void matvec_y_kernel(Shape s, Ptrs<const double> A, Ptrs<const double> W, T* Y) {
     const int R = s.R, RR = R * R;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)s.N * RR) return;
     const int p = (int)(e / RR), q = (int)(e % RR), r = q / R, z = q % R;
     const double* a = A.p[p];
     const double* w = W.p[p];
-    double acc = 0.0;
-    for (int64_t l = 0; l < s.dims[p]; ++l) acc += a[l * R + r] * w[l * R + z];
+    T acc = 0;
+    for (int64_t l = 0; l < s.dims[p]; ++l) acc = fmadd((T)a[l * R + r], (T)w[l * R + z], acc);
     Y[e] = acc;
 }
 
-// Q^(n)[k][r] = lam w_kr + sum_z w_kz Gamma^(n,n)_zr + sum_{p != n} sum_z a_kz Gamma^(n,p)_rz Y^(p)_rz
+// Q^(n)[k][r] = lam w_kr + sum_z w_kz Gamma^(n,n)_zr + sum_{p != n} sum_z a_kz Gamma^(n,p)_rz Y^(p)_rz.
+// diag = true: damping by lam diag(J^T J) instead, folded into the diagonal of
+// Gamma^(n,n) as (1 + lam) Gamma^(n,n)_rr (rounded once, as in the CG kernel).
+template <typename T>
 __global__ void matvec_q_kernel(Shape s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W,
-                                double lam, const double* Y, Ptrs<double> Q) {
+                                double lam, bool diag, const T* Y, Ptrs<double> Q) {
     const int R = s.R, RR = R * R, N = s.N;
     const int n = blockIdx.y;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -735,31 +742,44 @@ __global__ void matvec_q_kernel(Shape s, Ptrs<const double> A, const double* Gam
     const double* w = W.p[n] + k * R;
     const double* a = A.p[n] + k * R;
     const double* Gnn = Gam + ((int64_t)n * N + n) * RR;
-    double acc = lam * w[r];
-    for (int z = 0; z < R; ++z) acc += Gnn[r * R + z] * w[z];
+    T acc = diag ? (T)0 : (T)lam * (T)w[r];
+    for (int z = 0; z < R; ++z) {
+        const T g = (diag && z == r) ? (T)(Gnn[r * R + r] * (1.0 + lam)) : (T)Gnn[r * R + z];
+        acc = fmadd(g, (T)w[z], acc);
+    }
     for (int p = 0; p < N; ++p) {
         if (p == n) continue;
         const double* Gnp = Gam + ((int64_t)n * N + p) * RR;
-        const double* Yp = Y + (int64_t)p * RR;
-        for (int z = 0; z < R; ++z) acc += a[z] * Gnp[r * R + z] * Yp[r * R + z];
+        const T* Yp = Y + (int64_t)p * RR;
+        for (int z = 0; z < R; ++z) acc = fmadd((T)a[z], (T)Gnp[r * R + z] * Yp[r * R + z], acc);
     }
-    Q.p[n][e] = acc;
+    Q.p[n][e] = (double)acc;
 }
 
 cudaError_t preload_matvec_f64() {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, matvec_y_kernel);
-    return e != cudaSuccess ? e : cudaFuncGetAttributes(&fa, matvec_q_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, matvec_y_kernel<double>);
+    return e != cudaSuccess ? e : cudaFuncGetAttributes(&fa, matvec_q_kernel<double>);
 }
 
-void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
-                       Ptrs<double> Q, double* Y, cudaStream_t st) {
+template <typename T>
+void launch_matvec(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
+                   bool diag, Ptrs<double> Q, T* Y, cudaStream_t st) {
     const int64_t ny = (int64_t)s.N * s.R * s.R;
-    matvec_y_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, st>>>(s, A, W, Y);
+    matvec_y_kernel<T><<<(unsigned)((ny + 255) / 256), 256, 0, st>>>(s, A, W, Y);
     int64_t mx = 0;
     for (int n = 0; n < s.N; ++n) mx = std::max<int64_t>(mx, s.dims[n] * s.R);
     dim3 grid((unsigned)((mx + 255) / 256), s.N);
-    matvec_q_kernel<<<grid, 256, 0, st>>>(s, A, Gam, W, lam, Y, Q);
+    matvec_q_kernel<T><<<grid, 256, 0, st>>>(s, A, Gam, W, lam, diag, Y, Q);
+}
+template void launch_matvec<double>(const Shape&, Ptrs<const double>, const double*, Ptrs<const double>, double,
+                                    bool, Ptrs<double>, double*, cudaStream_t);
+template void launch_matvec<float>(const Shape&, Ptrs<const double>, const double*, Ptrs<const double>, double,
+                                   bool, Ptrs<double>, float*, cudaStream_t);
+
+void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
+                       Ptrs<double> Q, double* Y, cudaStream_t st) {
+    launch_matvec<double>(s, A, Gam, W, lam, false, Q, Y, st);
 }
 
 }  // namespace cpgn

@@ -80,7 +80,13 @@ struct PcgArgs {
 };
 template <typename T>
 cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st);
-// Plain (non-persistent) FP64 matvec used by cp_gn_matvec: Q = (J^T J + lam I) W.
+// Plain (non-persistent) matvec used by cp_gn_matvec: Q = (J^T J + lam D) W,
+// D = I or (diag) diag(J^T J), in FP64 (T = double) or the mixed CG's FP32
+// arithmetic (T = float).  Y: N R^2 elements of T scratch.
+template <typename T>
+void launch_matvec(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
+                   bool diag, Ptrs<double> Q, T* Y, cudaStream_t st);
+// The FP64 matvec with lam I.
 void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, Ptrs<const double> W, double lam,
                        Ptrs<double> Q, double* Y, cudaStream_t st);
 // Loads the module of the plain matvec's kernels now (cudaFuncGetAttributes), not at their first launch.

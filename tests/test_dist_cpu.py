@@ -72,26 +72,28 @@ def test_reference_arm_rank_nonzero_does_no_work(monkeypatch, capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_reference_arm_json_line():
+def test_reference_arm_json_line(monkeypatch, capsys):
     """`bench.py --impl reference` (the FP64 oracle timed on the host cores)
     prints one JSON line with the benchmark's keys, its own e2e figure and a
-    cpu_baseline describing the run; it needs no GPU."""
+    cpu_baseline describing the run; it needs no GPU.  Run here on the small
+    exact 20^3 workload (the full 400^3 solve takes minutes on these cores)."""
+    import argparse
     import json
-    import subprocess
 
-    env = dict(os.environ, OMP_NUM_THREADS="4")
+    import bench
+
+    monkeypatch.setenv("OMP_NUM_THREADS", "4")
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
-        env.pop(k, None)
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
-    assert out.returncode == 0, out.stderr[-2000:]
-    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(bench, "WORKLOAD", "exact20")
+    bench.run_reference(argparse.Namespace(gpus=1, steps=2, warmup=1))
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
     line = json.loads(lines[0])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
                 "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert key in line, key
-    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1 and line["warmup"] == 0
+    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 2 and line["warmup"] == 1
     assert line["value"] > 0 and line["higher_is_better"] is False
     assert abs(line["ms_per_step"] - 1e3 * line["value"]) <= 1e-9 * line["ms_per_step"]
     cb = line["cpu_baseline"]
@@ -99,4 +101,5 @@ def test_reference_arm_json_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert "workload" in line["config"]
+    # the reference arm reports the benchmark's own config (same keys as the GPU arm's line)
+    assert line["config"] == dict(bench.CONFIG, parallelism="replicas x1")

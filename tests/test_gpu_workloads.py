@@ -18,7 +18,8 @@ Tolerances, from the arithmetic of each result:
   FP64 by 1e-6 on these systems.  The gradient error itself is checked apart
   from the CG: a 1e-5 gradient perturbation grows to 1e-4 .. 4e-4 in the
   preconditioned direction.
-- FP64 path: 1e-12 (MTTKRP), 1e-11 (one GN step with a fixed CG count)."""
+- FP64 path: 1e-12 (MTTKRP; the update V of one GN step with a fixed CG
+  count, relative to max |V|; the gradient norm)."""
 import numpy as np
 import pytest
 
@@ -139,9 +140,12 @@ def test_gn_step_fp64(env, orc, wl):
     Ao, lam_o, dir_o, so, sto = orc.gn_step(X64, A, hi, 0, lo, hi, 2.0, 0.0, K_CG, use_dt=True)
     assert s == sto == api.CP_WARN_CG_MAXIT
     assert st["cg_iters"] == so["cg_iters"] == K_CG
-    for n, (a, ao) in enumerate(zip(Ad, Ao)):
-        assert _relerr(a.cpu().numpy(), ao) <= 1e-11, (name, n)
-    assert abs(st["grad_norm_sum"] - so["grad_norm_sum"]) <= 1e-10 * so["grad_norm_sum"]
+    V = [a.cpu().numpy() - a0 for a, a0 in zip(Ad, A)]
+    Vo = [ao - a0 for ao, a0 in zip(Ao, A)]
+    scale = max(np.abs(v).max() for v in Vo)
+    for n, (v, vo) in enumerate(zip(V, Vo)):
+        assert np.abs(v - vo).max() <= 1e-12 * scale, (name, n)
+    assert abs(st["grad_norm_sum"] - so["grad_norm_sum"]) <= 1e-12 * so["grad_norm_sum"]
     assert params.lam == lam_o and params.lam_dir == dir_o
 
 

@@ -568,3 +568,29 @@ def test_als_regularised(orc):
     Gam0 = (A[1].T @ A[1]) * (A[2].T @ A[2])
     M0 = _einsum_mttkrp(X, A, 0)
     np.testing.assert_allclose(A1[0] @ (Gam0 + lam * np.eye(R)), M0, rtol=1e-11, atol=1e-12)
+
+
+def test_gn_solve_is_the_step_loop_with_algorithm1_test(orc):
+    """The oracle's solve is Algorithm 1's loop: the same factors, bit for bit,
+    as repeated single steps stopped at the first entry point whose
+    sum||G||/sum||M|| meets the target; and it recovers the exact 20^3 rank-5
+    decomposition (r <= 1e-10)."""
+    from paper_1910_12331_gb300 import datagen
+
+    p = datagen.workload("exact20", seed=0)
+    hi, lo = orc.default_lambda(p["init"])
+    target = 1e-12
+    A_s, st, info = orc.gn_solve(p["X"], p["init"], hi, lo, hi, 2.0, 1e-3, 250, target, 100)
+    assert st == orc.OK and info["converged"]
+    A, lam, d, n, cg = [a.copy() for a in p["init"]], hi, 0, 0, 0
+    while True:
+        M = orc.mttkrp(p["X"], A, "dt")
+        _, gn = orc.gradient(A, orc.gamma(orc.gram(A)), M)
+        if gn.sum() <= target * sum(np.linalg.norm(m) for m in M):
+            break
+        A, lam, d, s, _ = orc.gn_step(p["X"], A, lam, d, lo, hi, 2.0, 1e-3, 250, use_dt=True)
+        n, cg = n + 1, cg + s["cg_iters"]
+    assert info["updates"] == n and info["cg_iters"] == cg
+    for a, b in zip(A_s, A):
+        assert np.array_equal(a, b)
+    assert orc.residual(p["X"], A_s) <= 1e-10
