@@ -75,7 +75,9 @@ __global__ void gamma_kernel(Shape s, const double* part, int chunks, double* S,
     if (q >= RR) return;
     double Sq[kMaxN];
     for (int m = 0; m < s.N; ++m) {
-        const int cm = (int)((s.dims[m] + kGramRows - 1) / kGramRows);
+        // mode m's chunks (chunks == 1: part holds the finished Gram matrices)
+        const int64_t cmode = (s.dims[m] + kGramRows - 1) / kGramRows;
+        const int cm = cmode < chunks ? (int)cmode : chunks;
         const double* pm = part + (int64_t)m * chunks * RR + q;
         double acc = 0.0;
         int c = 0;
