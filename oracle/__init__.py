@@ -27,6 +27,8 @@ Parity status of each routine (pins live in ``tests/test_oracle_pins.py``):
   lambda_next           pinned (hand-derived sequence, golden fixture)
   gn_step               pinned (exact recovery of exact-rank tensors)
   residual              pinned (numpy reconstruction, zero at exact factors)
+  residual_tensor       pinned (numpy reconstruction, zero at exact factors, its
+                        squared sum is the residual's numerator)
   als_sweep             pinned (monotone objective, zero mode gradient)
   The lambda thresholds, mu and the collinearity/noise recipe are chosen
   conventions: "parity unpinned" beyond the rule itself.
@@ -99,6 +101,8 @@ def _load():
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_set_threads.restype = None
             lib.orc_residual.argtypes = [d, dp, dp]
+            lib.orc_residual_tensor.argtypes = [d, dp, dp, dp]
+            lib.orc_residual_tensor.restype = None
             lib.orc_residual.restype = ctypes.c_double
             lib.orc_als_sweep.argtypes = [d, dp, dp, ctypes.c_double]
             lib.orc_als_sweep.restype = ctypes.c_int
@@ -260,6 +264,15 @@ def residual(X, A):
     X = _x64(X)
     dims, R = list(X.shape), A[0].shape[1]
     return float(_load().orc_residual(ctypes.byref(_desc(dims, R)), _ptr(X), _ptr(_pack(A))))
+
+
+def residual_tensor(X, A):
+    """E = X - [[A]] element by element in FP64 (same shape as X)."""
+    X = _x64(X)
+    dims, R = list(X.shape), A[0].shape[1]
+    E = np.empty(X.shape, dtype=np.float64)
+    _load().orc_residual_tensor(ctypes.byref(_desc(dims, R)), _ptr(X), _ptr(_pack(A)), _ptr(E))
+    return E
 
 
 def als_sweep(X, A, lam=0.0):

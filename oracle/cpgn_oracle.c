@@ -623,6 +623,29 @@ double orc_residual(const orc_desc* d, const double* X, const double* A) {
     return sqrt(num) / sqrt(den);
 }
 
+/* The residual tensor E = X - [[A]] element by element (Section 2.2's CP
+ * model written out: each entry of the reconstruction is the sum over r of
+ * the products of the factors' entries), in FP64, C-contiguous like X. */
+void orc_residual_tensor(const orc_desc* d, const double* X, const double* A, double* E) {
+    const int N = d->N, R = d->R;
+    const int64_t total = tensor_size(d);
+#pragma omp parallel
+    {
+        int64_t idx[ORC_MAXN];
+#pragma omp for schedule(static)
+        for (int64_t e = 0; e < total; ++e) {
+            unravel(d, e, idx);
+            double xt = 0.0;
+            for (int r = 0; r < R; ++r) {
+                double prod = 1.0;
+                for (int m = 0; m < N; ++m) prod *= A[factor_offset(d, m) + idx[m] * R + r];
+                xt += prod;
+            }
+            E[e] = X[e] - xt;
+        }
+    }
+}
+
 /* ----------------------------------------------------------------- ALS sweep */
 
 /* One CP-ALS sweep (Section 2.2): for n = 1..N in order, with the factors

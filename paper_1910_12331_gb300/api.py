@@ -29,7 +29,7 @@ REG = {"identity": CP_REG_IDENTITY, "diag": CP_REG_DIAG}
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
-           "cp_residual", "cp_residual_sums", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
+           "cp_residual", "cp_residual_sums", "cp_residual_tensor", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
            "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads",
            "cp_batch_plan_destroy", "cp_probe_grid_barrier", "cp_probe_fp64_fma")
 
@@ -131,6 +131,7 @@ def load(build_if_missing: bool = False):
         L.cp_als_sweep.argtypes = [vp, pd, vp, vp, d, i, ctypes.POINTER(d)]
         L.cp_residual.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d)]
         L.cp_residual_sums.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.cp_residual_tensor.argtypes = [vp, pd, vp, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.cp_gn_matvec_noalloc.argtypes = [pd, vp, vp, d, vp, vp]
         L.cp_gn_solve_batched.argtypes = [vp, i, ctypes.POINTER(cp_batch_problem), d, i, i, d,
                                           ctypes.POINTER(cp_batch_result)]
@@ -433,6 +434,23 @@ def cp_residual_sums(h: Handle, X, A):
     _check(load().cp_residual_sums(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), ctypes.byref(e),
                                    ctypes.byref(x)), "cp_residual_sums")
     return e.value, x.value
+
+
+def cp_residual_tensor(h: Handle, X, A, E=None):
+    """E = X - [[A]] in FP64 (a CUDA tensor shaped like X) by the residual-form
+    gradient's reconstruction; returns (E, sum E^2, ||X||^2)."""
+    R = _factors(X, A)
+    if E is None:
+        E = torch.empty(X.shape, dtype=torch.float64, device=X.device)
+    if not (E.is_cuda and E.dtype == torch.float64 and E.is_contiguous() and E.shape == X.shape
+            and E.device == X.device):
+        raise ValueError("E: expected a contiguous CUDA float64 tensor shaped like X")
+    h._bind_stream()
+    d = h.desc(X, R)
+    e, x = ctypes.c_double(), ctypes.c_double()
+    _check(load().cp_residual_tensor(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), E.data_ptr(),
+                                     ctypes.byref(e), ctypes.byref(x)), "cp_residual_tensor")
+    return E, e.value, x.value
 
 
 def _batch_array(problems, device: int):

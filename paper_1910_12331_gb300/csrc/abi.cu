@@ -199,11 +199,11 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         DevStats* ds = (DevStats*)h->stats.p;
         if (resid_tc_supported(s)) {  // reconstruction on the tensor cores (R <= 64)
             CP_TRY(grow(h->Adf, resid_tc_scratch_bytes(s)));
-            h->launches += launch_resid_split_tc(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, &ds->status,
-                                                 h->stream);
+            h->launches += launch_resid_split_tc(s, d->x_dtype, X, A, h->resid_planes.p, nullptr, h->Adf.p, ds,
+                                                 &ds->status, h->stream);
         } else {
             CP_TRY(grow(h->Adf, resid_scratch_bytes(s)));
-            launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, h->Adf.p, ds, h->stream);
+            launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, nullptr, h->Adf.p, ds, h->stream);
             h->launches += 2;
         }
         CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
@@ -744,6 +744,35 @@ cp_status cp_residual_sums(cp_handle h, const cp_desc* d, const void* X, const d
     if (sq_err) *sq_err = h->h_stats->res_num;
     if (sq_x) *sq_x = h->h_stats->res_den;
     return CP_OK;
+}
+
+cp_status cp_residual_tensor(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* E,
+                             double* sq_err, double* sq_x) {
+    if (!h || !X || !E) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)A, d->order));
+    {
+        const void* out[1] = {E};
+        if (aliased(out, 1, (const void* const*)A, d->order, X)) return CP_ERR_ARG;
+    }
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    CP_TRY(grow(h->stats, sizeof(DevStats)));
+    if (!h->h_stats) CUDA_TRY(cudaMallocHost((void**)&h->h_stats, sizeof(DevStats)));
+    DevStats* ds = (DevStats*)h->stats.p;
+    CUDA_TRY(cudaMemsetAsync(ds, 0, sizeof(DevStats), h->stream));
+    if (resid_tc_supported(s)) {
+        CP_TRY(grow(h->Adf, resid_tc_scratch_bytes(s)));
+        launch_resid_split_tc(s, d->x_dtype, X, ptrs_of(A, s.N), nullptr, E, h->Adf.p, ds, &ds->status, h->stream);
+    } else {
+        CP_TRY(grow(h->Adf, resid_scratch_bytes(s)));
+        launch_resid_split(s, d->x_dtype, X, ptrs_of(A, s.N), nullptr, E, h->Adf.p, ds, h->stream);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CP_TRY(sync_stats(h));
+    if (sq_err) *sq_err = h->h_stats->eres_num;
+    if (sq_x) *sq_x = h->h_stats->eres_den;
+    return h->h_stats->status ? (cp_status)h->h_stats->status : CP_OK;
 }
 
 }  // extern "C"

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
                                                         const float* __restrict__ amax1,
                                                         const float* __restrict__ amaxN,
                                                         __nv_bfloat16* __restrict__ planes, PlaneTiling pt,
-                                                        DevStats* stats) {
+                                                        double* __restrict__ E64, DevStats* stats) {
     __shared__ __align__(16) float2 As[RC][TI];
     __shared__ __align__(16) float2 Bs[RC][TK];
     __shared__ float2 ws[RC];
@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
                     const float xh = (float)x;
                     df_sq_acc(dh, dl, xh);
                 }
+                if (E64) E64[(i * mid + m) * sN + k] = ((double)x - (double)rh) - (double)sl[u][c];
                 df_sq_acc(nh, nl, e);
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(e);
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(NT) resid_split_kernel(Shape s, const TX* __re
     // is written, zero outside the tensor)
     const int b = (int)(i0 >> 7), r0t = (int)(i0 & 127);
     const int nrow = min(TI, pt.rows(b) - r0t);
-    if (nrow > 0) {
+    if (planes && nrow > 0) {
         const int64_t base = pt.tile(b, (int)(k0 >> 6), m);
         const int chunks = nrow * 8;  // 16-byte pieces per plane
         for (int q = threadIdx.x; q < 2 * chunks; q += NT) {
@@ -285,7 +286,7 @@ size_t resid_scratch_bytes(const Shape& s) {
 }
 
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                        void* scratch, DevStats* stats, cudaStream_t st) {
+                        double* E64, void* scratch, DevStats* stats, cudaStream_t st) {
     float2* Adf = (float2*)scratch;
     float* amax1 = (float*)(Adf + (size_t)s.roff[s.N] * s.R);
     float* amaxN = amax1 + blocks1(s) * s.R;
@@ -305,10 +306,10 @@ void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const 
     dim3 grid((unsigned)s.mid, (unsigned)blocks1(s), (unsigned)blocksN(s));
     if (xdt == CP_F32)
         resid_split_kernel<float><<<grid, NT, resid_dyn_smem<float>(), st>>>(s, (const float*)X, Adf, amax1, amaxN,
-                                                                              (__nv_bfloat16*)planes, pt, stats);
+                                                                              (__nv_bfloat16*)planes, pt, E64, stats);
     else
         resid_split_kernel<double><<<grid, NT, resid_dyn_smem<double>(), st>>>(
-            s, (const double*)X, Adf, amax1, amaxN, (__nv_bfloat16*)planes, pt, stats);
+            s, (const double*)X, Adf, amax1, amaxN, (__nv_bfloat16*)planes, pt, E64, stats);
 }
 
 }  // namespace cpgn

@@ -1,7 +1,8 @@
 // k_resid_tc.cu -- the residual tensor E = X - [[A^(1), ..., A^(N)]] with the
 // reconstruction on tcgen05 tensor cores (sm_103a), written as bf16 high/low
-// planes (PlaneTiling) for the tensor-core MTTKRP, with sum E^2 and sum X^2.
-// Used for R <= 64; larger ranks take the CUDA-core kernel of k_resid.cu.
+// planes (PlaneTiling) for the tensor-core MTTKRP and/or in FP64, with
+// sum E^2 and sum X^2.  Used for R <= 64; larger ranks take the CUDA-core
+// kernel of k_resid.cu.
 //
 // Why: the gradient G^(n) = -E_(n) P^(n) of Eq. (2.3) needs E to far better
 // than FP32's 2^-24 when E is small; see k_resid.cu.
@@ -11,33 +12,40 @@
 // matrix multiplication by using fast routines of matrix multiplication and its
 // applications", Numer. Algorithms 59, 2012), with bf16 slices and the tensor
 // core's FP32 accumulation:
-//   For a slice m of the middle modes, [[A]][i, m, k] = sum_r u_ir v_kr with
-//   u_ir = a^(1)_ir w_m[r] (w_m: the product of the middle factors' rows) and
-//   v_kr = a^(N)_kr.  Row i of u is scaled by the power of two sigma_i >=
-//   max_r |u_ir|, row k of v by tau_k >= max_r |v_kr|, and every scaled value
-//   is cut into six pieces on the grids 2^-8, 2^-16, ..., 2^-48 (round to
-//   nearest on each grid; the remainder goes on to the next).  A piece on grid
-//   2^-8s is an integer of at most 8 significant bits times 2^-8s, exact in
-//   bf16.  The product of pieces s and t is an integer of at most 16 bits on
-//   the grid 2^-8(s+t); all products of one level L = s + t summed over r < 64
-//   stay below 2^23 units of that grid, so the FP32 accumulation of a level is
-//   exact.  Levels L = 2..7 (21 piece pairs) go to six TMEM accumulators; the
-//   pairs with s + t >= 8 and the remainders beyond the sixth piece are below
-//   2^-46 R sigma_i tau_k.  The epilogue adds the levels in double-float (the
-//   FP32 additions of the small levels, |D_4| <~ 2^-16 R, round at most
-//   2^-40 R sigma_i tau_k), subtracts from x (scaled by the same powers of
-//   two) and scales back: error below 2^-39 R sigma_i tau_k in all.
+//   X is viewed as the (s_1 mid) x s_N matrix of its rows (i, m), m indexing
+//   the middle modes, and [[A]][(i, m), k] = sum_r u_r v_kr with
+//   u_r = a^(1)_ir w_m[r] (w_m: the product of the middle factors' rows) and
+//   v_kr = a^(N)_kr.  Row (i, m) of u is scaled by the power of two
+//   sigma >= max_r |u_r|, row k of v by tau_k >= max_r |v_kr|, and every scaled
+//   value is cut into five pieces on the grids 2^-8, 2^-16, ..., 2^-40 (round
+//   to nearest on each grid; the remainder goes on to the next).  A piece on
+//   grid 2^-8s is an integer of at most 8 significant bits times 2^-8s, exact
+//   in bf16; |piece s| <= 2^(9 - 8s) for s >= 2.  The product of pieces s and t
+//   is an integer of at most 16 bits on the grid 2^-8(s+t).  The piece pairs
+//   with s + t = L <= 6 (15 pairs) are accumulated in four TMEM accumulators:
+//     L = 2, 3, 4, one each: every sum of a level over r < 64 stays below 2^23
+//       units of its grid, so the FP32 accumulation is exact;
+//     L = 5 and 6 together: magnitudes below 2^-16 R, so each of the at most
+//       36 accumulating MMAs rounds by at most 2^-41 sigma tau.
+//   The pairs with s + t >= 7 and the remainders beyond the fifth piece are
+//   below 2^-39.5 per rank term.  The epilogue forms (h, l) = the exact
+//   double-float sum of levels 2 and 3 plus the FP32 sum of the rest (rounding
+//   below 2^-40 R), scales back by sigma tau (powers of two) and subtracts from
+//   x: error below 2^-38.5 R sigma tau in all.
 //
-// Kernel: persistent, one CTA per SM, 12 warps.  A run is (i-block b of 128
-// rows, slice m); a step is one 32-column chunk c of a run.
-//   warp 0      producer: the step's pieces of v (6 x 4 KB, one bulk copy,
-//               precomputed once per call, pre-swizzled) into one of two slots.
-//   warp 1      TMEM allocator and MMA issuer (one thread): 21 piece pairs x
-//               K/16 MMAs (M = 128, N = 32) into the six level accumulators of
-//               one of two TMEM buffers (6 levels x 32 columns).
-//   warps 4-11  workers: build the pieces of u for a run (6 x 16 KB), then per
-//               step drain the six levels of D (lane = row i, 16 columns per
-//               warp), form E and write its planes.
+// Kernel: persistent, one CTA per SM, 12 warps.  A run is 128 consecutive rows
+// (i, m); a step is one 64-column chunk c of k (the last chunk's MMAs are
+// only as wide as its columns, rounded up to 16).
+//   warp 0      producer: the step's pieces of v (5 x 8 KB, one bulk copy,
+//               precomputed once per call, pre-swizzled), its tau_k and (FP32
+//               X, s_N a multiple of 4) the 128 x 64 X tile by two 2-D tensor
+//               copies, into one of two slots.
+//   warp 1      TMEM allocator and MMA issuer (one thread): 15 piece pairs x
+//               K/16 MMAs (M = 128, N = 64) into the four accumulators of one
+//               of two TMEM buffers (4 x 64 columns each).
+//   warps 4-11  workers: build the pieces of u for a run (5 x 16 KB), then per
+//               step drain the four accumulators (lane = row, 32 columns per
+//               warp), form E and write it.
 // Every mbarrier wait is bounded (CP_ERR_TIMEOUT, CTA abort flag, drain).
 #include <cuda_bf16.h>
 #include <string.h>
@@ -54,37 +62,42 @@ namespace rtc {
 
 using namespace tcx;
 
-constexpr int kSlices = 6;                         // pieces per value
-constexpr int kLevels = 6;                         // L = 2 .. 7
-constexpr int kBI = 128;                           // rows i of a run (M)
-constexpr int kKC = 32;                            // columns k of a step (N)
+constexpr int kSlices = 5;                         // pieces per value
+constexpr int kAcc = 4;                            // accumulators: L = 2, 3, 4 and L = 5 + 6
+constexpr int kBI = 128;                           // rows (i, m) of a run (M)
+constexpr int kKC = 64;                            // columns k of a step (N, at most)
 constexpr int kRT = 64;                            // rank columns (K), zero padded
 constexpr uint32_t kASlice = kBI * 128;            // 128 rows x 64 bf16, K-major, 128-byte swizzle
-constexpr uint32_t kBSlice = kKC * 128;            // 32 rows x 64 bf16
-constexpr uint32_t kABytes = kSlices * kASlice;    // 96 KB
-constexpr uint32_t kBBytes = kSlices * kBSlice;    // 24 KB per step
-constexpr uint32_t kXTile = kBI * kKC * 4;         // 128 rows x 32 FP32 of X, 128-byte swizzle (TMA)
-constexpr uint32_t kBSlot = kBBytes;                // a step's B slot: the six pieces of v
-constexpr uint32_t kPayload = kABytes + 2 * kBSlot + 2 * kXTile;
+constexpr uint32_t kBSlice = kKC * 128;            // 64 rows x 64 bf16
+constexpr uint32_t kABytes = kSlices * kASlice;    // 80 KB
+constexpr uint32_t kBBytes = kSlices * kBSlice;    // 40 KB per step
+constexpr uint32_t kXBox = kBI * 32 * 4;           // 128 rows x 32 FP32 of X, 128-byte swizzle (one tensor copy)
+constexpr uint32_t kXTile = 2 * kXBox;             // a step's 64 columns
+constexpr uint32_t kPayload = kABytes + 2 * kBBytes + 2 * kXTile;
 constexpr int kWork = 256;
 constexpr int kThreads = 128 + kWork;
-constexpr uint32_t kTmemCols = 512;                // 2 buffers x 6 levels x 32 columns
-constexpr uint32_t kDBuf = kLevels * kKC;          // TMEM columns of one buffer
+constexpr uint32_t kTmemCols = 512;                // 2 buffers x 4 accumulators x 64 columns
+constexpr uint32_t kDBuf = kAcc * kKC;             // TMEM columns of one buffer
+
+// Accumulator of level L = s + t.
+__host__ __device__ constexpr int acc_of_level(int L) { return L <= 4 ? L - 2 : 3; }
 
 struct Params {
     int N, R;
     int64_t s1, mid, sN;
-    int nib, nck;        // 128-row blocks, 32-column chunks (covering the planes' 64-column chunks)
-    int64_t runs;        // nib * mid, run j = b * mid + m
+    int64_t rows;        // s1 * mid rows (i, m), row f = i * mid + m
+    int64_t runs;        // ceil(rows / 128)
+    int nck;             // 64-column chunks of k
     PlaneTiling pt;
     const void* X;
     int x_f64;
-    const float2* A1df;  // [nib * 128][64] (hi, lo) of A^(1), zero padded
-    const float2* Wdf;   // [mid][64] (hi, lo) of w_m, zero padded
-    const unsigned char* Vsl;  // [nck][6][32][128 B] pieces of a^(N)_kr / tau_k, swizzled
-    const float* tau;    // [nck * 32]
     int x_tma;           // X tiles come by tensor copy (FP32, s_N % 4 == 0), else the workers load X
-    __nv_bfloat16* planes;
+    const float2* A1df;  // [s1][64] (hi, lo) of A^(1), zero padded
+    const float2* Wdf;   // [mid][64] (hi, lo) of w_m, zero padded
+    const unsigned char* Vsl;  // [nck][5][64][128 B] pieces of a^(N)_kr / tau_k, swizzled
+    const float* tau;    // [nck * 64]
+    __nv_bfloat16* planes;  // bf16 planes of E (PlaneTiling), or null
+    double* E64;            // E in FP64, C-contiguous like X, or null
     DevStats* stats;
     int* status;
 };
@@ -93,7 +106,7 @@ struct SmemCtl {
     uint64_t a_full, a_empty, b_full[2], b_empty[2], d_full[2], d_empty[2], x_full[2], x_empty[2], drain;
     uint32_t tmem_base;
     int abort_flag;
-    float sig[2][kBI];      // sigma_i of a run, by run parity
+    float sig[2][kBI];      // sigma of each row of a run, by run parity
     double red[2][8];
     alignas(16) float tau_s[2][kKC];  // tau_k of a step, with its X tile
 };
@@ -143,7 +156,7 @@ __device__ __forceinline__ uint32_t bf2(float lo, float hi) {
 }
 
 // Pieces of one scaled double-float value (|h + l| <= 1) on the grids 2^-8s.
-__device__ __forceinline__ void cut6(float h, float l, float* pc) {
+__device__ __forceinline__ void cut5(float h, float l, float* pc) {
     pc[0] = rintf(h * 0x1p8f) * 0x1p-8f;
     h -= pc[0];
     pc[1] = rintf(h * 0x1p16f) * 0x1p-16f;
@@ -155,8 +168,6 @@ __device__ __forceinline__ void cut6(float h, float l, float* pc) {
     pc[3] = rintf(hh * 0x1p32f) * 0x1p-32f;
     hh = (hh - pc[3]) + ll;
     pc[4] = rintf(hh * 0x1p40f) * 0x1p-40f;
-    hh -= pc[4];
-    pc[5] = rintf(hh * 0x1p48f) * 0x1p-48f;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_constant__ CUtensorMap tmX, Params p) {
@@ -167,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
     }
     SmemCtl& C = *reinterpret_cast<SmemCtl*>(dsmem + kPayload);
     volatile int* abort_s = &C.abort_flag;
-    const uint32_t sA = smem_u32(dsmem), sB = sA + kABytes, sX = sB + 2 * kBSlot;
+    const uint32_t sA = smem_u32(dsmem), sB = sA + kABytes, sX = sB + 2 * kBBytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&C.a_full), kWork);
@@ -205,21 +216,22 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
             int64_t tt = 0;
             bool ok = true;
             for (int64_t j = J0; j < J1 && ok; ++j) {
-                const int b = (int)(j / p.mid);
-                const int m = (int)(j - (int64_t)b * p.mid);
                 for (int c = 0; c < p.nck; ++c, ++tt) {
                     const int slot = (int)(tt & 1);
                     const uint32_t pe = (uint32_t)(((tt >> 1) & 1) ^ 1);
                     if (!(ok = mbar_wait(smem_u32(&C.b_empty[slot]), pe, abort_s, p.status))) break;
                     const uint32_t fb = smem_u32(&C.b_full[slot]);
                     mbar_expect_tx(fb, kBBytes);
-                    bulk_load(sB + slot * kBSlot, p.Vsl + (size_t)c * kBBytes, kBBytes, fb);
-                    // the step's tau_k and (tensor copy) X tile, released by the workers
+                    bulk_load(sB + slot * kBBytes, p.Vsl + (size_t)c * kBBytes, kBBytes, fb);
+                    // the step's tau_k and (tensor copy) X tile, released by the workers; a box
+                    // that starts at or beyond s_N is not loaded (its columns are masked)
                     if (!(ok = mbar_wait(smem_u32(&C.x_empty[slot]), pe, abort_s, p.status))) break;
                     const uint32_t fx = smem_u32(&C.x_full[slot]);
-                    mbar_expect_tx(fx, (p.x_tma ? kXTile : 0u) + kKC * 4u);
+                    const int nbox = p.x_tma ? ((int64_t)c * kKC + 32 < p.sN ? 2 : 1) : 0;
+                    mbar_expect_tx(fx, (uint32_t)nbox * kXBox + kKC * 4u);
                     bulk_load(smem_u32(&C.tau_s[slot][0]), p.tau + (size_t)c * kKC, kKC * 4u, fx);
-                    if (p.x_tma) tma_load_3d(sX + slot * kXTile, &tmX, c * kKC, m, b * kBI, fx);
+                    for (int hb = 0; hb < nbox; ++hb)
+                        tma_load_2d(sX + slot * kXTile + hb * kXBox, &tmX, c * kKC + hb * 32, (int)(j * kBI), fx);
                 }
             }
             for (int64_t k = (tt > 2 ? tt - 2 : 0); k < tt; ++k) {
@@ -231,7 +243,6 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id = idesc_bf16(kKC, false, false);
             int64_t tt = 0;
             int jr = 0;
             bool ok = true;
@@ -243,26 +254,28 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
                     if (!(ok = mbar_wait(smem_u32(&C.d_empty[slot]), ph ^ 1, abort_s, p.status))) break;
                     if (!(ok = mbar_wait(smem_u32(&C.b_full[slot]), ph, abort_s, p.status))) break;
                     tc_fence_after();
+                    const int64_t left = p.sN - (int64_t)c * kKC;
+                    const int nstep = left >= kKC ? kKC : (int)((left + 15) / 16 * 16);
+                    const uint32_t id = idesc_bf16(nstep, false, false);
                     const uint32_t dbase = tmem + slot * kDBuf;
-                    const uint64_t a0 = sdesc(sA, 16, 1024), b0 = sdesc(sB + slot * kBSlot, 16, 1024);
-                    // K-step outermost, then level, then piece pair: consecutive MMAs go to
-                    // different level accumulators.  (Two other orders were measured to lose
-                    // MMAs that accumulate back to back into one accumulator: piece pair by
-                    // piece pair with a pair's K-steps adjacent, and one N = 192 MMA per piece
-                    // into all six levels at once; this order gave bit-identical results.)
+                    const uint64_t a0 = sdesc(sA, 16, 1024), b0 = sdesc(sB + slot * kBBytes, 16, 1024);
+                    // K-step outermost, then level, then piece pair (the order of the
+                    // reconstruction's bit-stability tests)
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         if (ks >= ksteps) break;
 #pragma unroll
-                        for (int L = 2; L <= kLevels + 1; ++L) {
+                        for (int L = 2; L <= kSlices + 1; ++L) {
 #pragma unroll
                             for (int sp = 1; sp <= kSlices; ++sp) {
                                 const int t = L - sp;
                                 if (t < 1 || t > kSlices) continue;
-                                const bool first = sp == (L - kSlices > 1 ? L - kSlices : 1);
+                                const int a = acc_of_level(L);
+                                // the first MMA into an accumulator in a step overwrites it
+                                const bool first = ks == 0 && sp == 1 && (a < 3 || L == 5);
                                 const uint64_t ao = (uint64_t)(((sp - 1) * kASlice + ks * 32) >> 4);
                                 const uint64_t bo = (uint64_t)(((t - 1) * kBSlice + ks * 32) >> 4);
-                                tc_mma(dbase + (L - 2) * kKC, a0 + ao, b0 + bo, id, (first && ks == 0) ? 0 : 1);
+                                tc_mma(dbase + a * kKC, a0 + ao, b0 + bo, id, first ? 0 : 1);
                             }
                         }
                     }
@@ -279,43 +292,40 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
         // ------------------------------------------------------------ workers
         const int wk = warp - 4;
         const int q = warp & 3;              // TMEM lane quadrant of this warp
-        const int ch = wk >> 2;              // 16-column half of a step
-        const int row = q * 32 + lane;       // TMEM lane = row of the block
+        const int ch = wk >> 2;              // 32-column half of a step
+        const int row = q * 32 + lane;       // TMEM lane = row of the run
         const int et = wk * 32 + lane;       // 0 .. kWork - 1
         bool ok = true;
         float eh = 0.f, el = 0.f, xh = 0.f, xl = 0.f;
 
-        // pieces of u for run j (all workers; named barrier 1 only, taken by every worker)
         // pieces of u for run j: eight lanes per row (8 rank columns = one 16-byte
         // piece each), four rows per warp and pass, four passes
         auto build = [&](int64_t j, int jr) {
             if (ok) ok = mbar_wait(smem_u32(&C.a_empty), (uint32_t)((jr & 1) ^ 1), abort_s, p.status);
             if (!ok) return;
-            const int64_t b = j / p.mid, m = j - b * p.mid;
             const int c8 = lane & 7;
-            const float4* wsrc = reinterpret_cast<const float4*>(p.Wdf + (size_t)m * kRT + c8 * 8);
-            float2 w[8];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float4 t4 = __ldg(wsrc + u);
-                w[2 * u] = make_float2(t4.x, t4.y);
-                w[2 * u + 1] = make_float2(t4.z, t4.w);
-            }
 #pragma unroll 2
             for (int pass = 0; pass < 4; ++pass) {
                 const int brow = pass * 32 + wk * 4 + (lane >> 3);
-                const float4* asrc =
-                    reinterpret_cast<const float4*>(p.A1df + ((size_t)b * kBI + brow) * kRT + c8 * 8);
+                const int64_t f = j * kBI + brow;
                 float2 v[8];
                 float mx = 0.f;
+                if (f < p.rows) {
+                    const int64_t i = f / p.mid, m = f - i * p.mid;
+                    const float4* asrc = reinterpret_cast<const float4*>(p.A1df + (size_t)i * kRT + c8 * 8);
+                    const float4* wsrc = reinterpret_cast<const float4*>(p.Wdf + (size_t)m * kRT + c8 * 8);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float4 t4 = __ldg(asrc + u);
-                    v[2 * u] = df_mul(make_float2(t4.x, t4.y), w[2 * u]);
-                    v[2 * u + 1] = df_mul(make_float2(t4.z, t4.w), w[2 * u + 1]);
-                    mx = fmaxf(mx, fmaxf(fabsf(v[2 * u].x), fabsf(v[2 * u + 1].x)));
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 a4 = __ldg(asrc + u), w4 = __ldg(wsrc + u);
+                        v[2 * u] = df_mul(make_float2(a4.x, a4.y), make_float2(w4.x, w4.y));
+                        v[2 * u + 1] = df_mul(make_float2(a4.z, a4.w), make_float2(w4.z, w4.w));
+                        mx = fmaxf(mx, fmaxf(fabsf(v[2 * u].x), fabsf(v[2 * u + 1].x)));
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = make_float2(0.f, 0.f);
                 }
-                // sigma_i >= max_r |u_ir| over the row's eight lanes (hi parts; the low
+                // sigma >= max_r |u_r| over the row's eight lanes (hi parts; the low
                 // parts stay inside the 2^-24 slack of the first piece)
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
                 const float inv = pow2_inv(sg);
                 float pc[8][kSlices];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) cut6(v[u].x * inv, v[u].y * inv, pc[u]);
+                for (int u = 0; u < 8; ++u) cut5(v[u].x * inv, v[u].y * inv, pc[u]);
                 const uint32_t off = sw128(brow, c8 * 8);
 #pragma unroll
                 for (int sl = 0; sl < kSlices; ++sl) {
@@ -345,101 +355,121 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
         int jr = 0;
         if (J0 < J1) build(J0, 0);
         for (int64_t j = J0; j < J1; ++j, ++jr) {
-            const int b = (int)(j / p.mid);
-            const int64_t m = j - (int64_t)b * p.mid;
-            const int64_t i = (int64_t)b * kBI + row;
-            const bool row_in = i < p.s1, row_out = row < p.pt.rows(b);
+            const int64_t f = j * kBI + row;  // this thread's row (i, m) of X
+            const bool live = f < p.rows;
+            const int64_t i = live ? f / p.mid : 0;
+            const int64_t m = live ? f - i * p.mid : 0;
+            const int b = (int)(i >> 7), r = (int)(i & 127);
+            const int rows_b = p.pt.rows(b);
             for (int c = 0; c < p.nck; ++c, ++tt) {
                 // the next run's pieces of u go in while this run's last step drains
                 if (c == p.nck - 1 && j + 1 < J1) build(j + 1, jr + 1);
                 if (!ok) continue;
                 const int slot = (int)(tt & 1);
                 const uint32_t ph = (uint32_t)((tt >> 1) & 1);
-                const int64_t k0 = (int64_t)c * kKC + ch * 16;
-                float xv[16];
-                if (!p.x_tma) {
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int64_t k = k0 + u;
-                        xv[u] = (row_in && k < p.sN && !p.x_f64)
-                                    ? __ldg(reinterpret_cast<const float*>(p.X) + (i * p.mid + m) * p.sN + k)
-                                    : 0.f;
-                    }
-                }
                 if (!(ok = mbar_wait(smem_u32(&C.x_full[slot]), ph, abort_s, p.status))) continue;
                 if (!(ok = mbar_wait(smem_u32(&C.d_full[slot]), ph, abort_s, p.status))) continue;
                 tc_fence_after();
-                // sigma_i of this run: written by another worker before its a_full arrival,
+                // sigma of this run: written by another worker before its a_full arrival,
                 // which the MMAs behind d_full waited for
                 const float sg = C.sig[jr & 1][row];
-                uint32_t d[kLevels][16];
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + slot * kDBuf + ch * 16;
-#pragma unroll
-                for (int L = 0; L < kLevels; L += 2) tmem_ld16x2_wait(ta + L * kKC, ta + (L + 1) * kKC, d[L], d[L + 1]);
-                float it[16];
-#pragma unroll
-                for (int u = 0; u < 16; u += 4) {
-                    const float4 t4 = *reinterpret_cast<const float4*>(&C.tau_s[slot][ch * 16 + u]);
-                    it[u] = t4.x;
-                    it[u + 1] = t4.y;
-                    it[u + 2] = t4.z;
-                    it[u + 3] = t4.w;
-                }
-                if (p.x_tma) {
-                    // 128-byte rows; 16-byte piece j of row r sits at piece j ^ (r mod 8)
-                    const unsigned char* xr = dsmem + (kABytes + 2 * kBSlot) + slot * kXTile + row * 128;
+                float e2 = 0.f, x2 = 0.f;
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int cc = ch * 32 + hh * 16;  // first column of this group inside the chunk
+                    const int64_t k0 = (int64_t)c * kKC + cc;
+                    uint32_t d[kAcc][16];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + slot * kDBuf + cc;
+                    tmem_ld16x2_wait(ta, ta + kKC, d[0], d[1]);
+                    tmem_ld16x2_wait(ta + 2 * kKC, ta + 3 * kKC, d[2], d[3]);
+                    float it[16], xv[16];
 #pragma unroll
                     for (int u = 0; u < 16; u += 4) {
-                        const float4 x4 =
-                            *reinterpret_cast<const float4*>(xr + ((((ch * 16 + u) >> 2) ^ (row & 7)) << 4));
-                        xv[u] = x4.x;
-                        xv[u + 1] = x4.y;
-                        xv[u + 2] = x4.z;
-                        xv[u + 3] = x4.w;
+                        const float4 t4 = *reinterpret_cast<const float4*>(&C.tau_s[slot][cc + u]);
+                        it[u] = t4.x;
+                        it[u + 1] = t4.y;
+                        it[u + 2] = t4.z;
+                        it[u + 3] = t4.w;
                     }
-                }
-                mbar_arrive(smem_u32(&C.x_empty[slot]));
-                tc_fence_before();
-                mbar_arrive(smem_u32(&C.d_empty[slot]));
-                const float isg = pow2_inv(sg);
-                float e2 = 0.f, x2 = 0.f;
-                uint32_t hw[8], lw[8];
+                    if (p.x_tma) {
+                        // box cc / 32, 128-byte rows; 16-byte piece j of row r at piece j ^ (r mod 8)
+                        const unsigned char* xr = dsmem + (kABytes + 2 * kBBytes) + slot * kXTile +
+                                                  (cc >> 5) * kXBox + row * 128;
 #pragma unroll
-                for (int u = 0; u < 16; u += 2) {
-                    float ev[2];
-#pragma unroll
-                    for (int v = 0; v < 2; ++v) {
-                        const int w = u + v;
-                        const float small = ((__uint_as_float(d[5][w]) + __uint_as_float(d[4][w])) +
-                                             __uint_as_float(d[3][w])) +
-                                            __uint_as_float(d[2][w]);
-                        float h, l;
-                        two_sum(__uint_as_float(d[0][w]), __uint_as_float(d[1][w]), h, l);
-                        l += small;
-                        // scaled units: x / (sigma_i tau_k) - (h + l), exact scalings by powers of two
-                        const float tk = it[w];
-                        float e;
-                        if (p.x_f64) {  // X in FP64: the subtraction in FP64 (rare path)
-                            const int64_t k = k0 + w;
-                            const double xd = (row_in && k < p.sN)
-                                                  ? reinterpret_cast<const double*>(p.X)[(i * p.mid + m) * p.sN + k]
-                                                  : 0.0;
-                            e = (float)((((xd * (double)isg * (double)pow2_inv(tk)) - (double)h) - (double)l) *
-                                        (double)sg * (double)tk);
-                            xv[w] = (float)xd;
-                        } else {
-                            const float xs = xv[w] * isg * pow2_inv(tk);
-                            e = (((xs - h) - l) * sg) * tk;
+                        for (int u = 0; u < 16; u += 4) {
+                            const float4 x4 =
+                                *reinterpret_cast<const float4*>(xr + (((((cc & 31) + u) >> 2) ^ (row & 7)) << 4));
+                            xv[u] = x4.x;
+                            xv[u + 1] = x4.y;
+                            xv[u + 2] = x4.z;
+                            xv[u + 3] = x4.w;
                         }
-                        ev[v] = e;
-                        e2 = fmaf(e, e, e2);
-                        x2 = fmaf(xv[w], xv[w], x2);
+                    } else if (!p.x_f64) {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            xv[u] = (live && k0 + u < p.sN) ? __ldg(reinterpret_cast<const float*>(p.X) + f * p.sN + k0 + u)
+                                                            : 0.f;
                     }
-                    const __nv_bfloat162 hi2 = __floats2bfloat162_rn(ev[0], ev[1]);
-                    const float2 hf = __bfloat1622float2(hi2);
-                    const __nv_bfloat162 lo2 = __floats2bfloat162_rn(ev[0] - hf.x, ev[1] - hf.y);
-                    hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&hi2);
-                    lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&lo2);
+                    if (hh == 1) {  // every read of this step's slot is done
+                        mbar_arrive(smem_u32(&C.x_empty[slot]));
+                        tc_fence_before();
+                        mbar_arrive(smem_u32(&C.d_empty[slot]));
+                    }
+                    uint32_t hw[8], lw[8];
+#pragma unroll
+                    for (int u = 0; u < 16; u += 2) {
+                        float ev[2];
+#pragma unroll
+                        for (int v = 0; v < 2; ++v) {
+                            const int w = u + v;
+                            const int64_t k = k0 + w;
+                            const bool valid = live && k < p.sN;
+                            // levels 2 and 3 exactly as (h, l); levels 4..6 join l
+                            float h, l;
+                            two_sum(__uint_as_float(d[0][w]), __uint_as_float(d[1][w]), h, l);
+                            l += __uint_as_float(d[2][w]) + __uint_as_float(d[3][w]);
+                            const float tk = it[w];
+                            float e = 0.f;
+                            if (p.x_f64) {  // X in FP64: the subtraction in FP64
+                                const double xd = valid ? reinterpret_cast<const double*>(p.X)[f * p.sN + k] : 0.0;
+                                const double st = (double)sg * (double)tk;
+                                const double ed = (xd - (double)h * st) - (double)l * st;
+                                if (valid && p.E64) p.E64[f * p.sN + k] = ed;
+                                e = valid ? (float)ed : 0.f;
+                                xv[w] = (float)xd;
+                            } else if (valid) {
+                                // x - h sigma tau is exact near the optimum (Sterbenz); the scalings
+                                // by powers of two are exact
+                                const float hs = (h * sg) * tk, ls = (l * sg) * tk;
+                                e = (xv[w] - hs) - ls;
+                                if (p.E64) p.E64[f * p.sN + k] = ((double)xv[w] - (double)hs) - (double)ls;
+                            }
+                            ev[v] = e;
+                            const float xm = valid ? xv[w] : 0.f;  // columns beyond s_N may hold stale data
+                            e2 = fmaf(e, e, e2);
+                            x2 = fmaf(xm, xm, x2);
+                        }
+                        const __nv_bfloat162 hi2 = __floats2bfloat162_rn(ev[0], ev[1]);
+                        const float2 hf = __bfloat1622float2(hi2);
+                        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(ev[0] - hf.x, ev[1] - hf.y);
+                        hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&hi2);
+                        lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&lo2);
+                    }
+                    if (live && p.planes) {
+                        // 16 columns = two 16-byte pieces of the row in each plane
+                        const int64_t tb = p.pt.tile(b, c, m);
+                        __nv_bfloat16* r0 = p.planes + tb + (int64_t)r * 64;
+                        __nv_bfloat16* r1 = p.planes + tb + ((int64_t)rows_b + r) * 64;
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int j8 = (cc >> 3) + h2;
+                            const int pos = ((j8 ^ (r & 7)) << 3);
+                            *reinterpret_cast<uint4*>(r0 + pos) =
+                                make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
+                            *reinterpret_cast<uint4*>(r1 + pos) =
+                                make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
+                        }
+                    }
                 }
                 float s1, s2;
                 two_sum(eh, e2, s1, s2);
@@ -448,23 +478,6 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
                 two_sum(xh, x2, s1, s2);
                 xh = s1;
                 xl += s2;
-                if (row_out) {
-                    // 16 columns = two 16-byte pieces of the row in each plane
-                    const int rows_b = p.pt.rows(b);
-                    const int kc = (int)((int64_t)c * kKC % 64) + ch * 16;  // column inside the 64-column tile
-                    const int64_t tb = p.pt.tile(b, (int)((int64_t)c * kKC / 64), m);
-                    __nv_bfloat16* r0 = p.planes + tb + (int64_t)row * 64;
-                    __nv_bfloat16* r1 = p.planes + tb + ((int64_t)rows_b + row) * 64;
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int j8 = (kc >> 3) + h2;
-                        const int pos = ((j8 ^ (row & 7)) << 3);
-                        *reinterpret_cast<uint4*>(r0 + pos) =
-                            make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
-                        *reinterpret_cast<uint4*>(r1 + pos) =
-                            make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
-                    }
-                }
             }
         }
         // sum E^2 and sum X^2 over the workers (FP64 across threads, fixed order)
@@ -497,15 +510,15 @@ __device__ __forceinline__ float2 split_df(double d) {
     return make_float2(hi, (float)(d - (double)hi));
 }
 
-// A1df rows (zero padded to nib * 128 x 64) and Wdf rows w_m = prod_{middle q} a^(q)_{i_q(m) r}
-__global__ void recon_prep_rows(Shape s, Ptrs<const double> A, int nib, float2* A1df, float2* Wdf) {
+// A1df rows (s1 x 64, zero padded) and Wdf rows w_m = prod_{middle q} a^(q)_{i_q(m) r}
+__global__ void recon_prep_rows(Shape s, Ptrs<const double> A, float2* A1df, float2* Wdf) {
     const int R = s.R, N = s.N;
-    const int64_t na = (int64_t)nib * kBI * kRT, nw = s.mid * kRT;
+    const int64_t na = s.dims[0] * kRT, nw = s.mid * kRT;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + nw; e += (int64_t)gridDim.x * blockDim.x) {
         if (e < na) {
             const int64_t i = e / kRT;
             const int r = (int)(e - i * kRT);
-            A1df[e] = (i < s.dims[0] && r < R) ? split_df(A.p[0][i * R + r]) : make_float2(0.f, 0.f);
+            A1df[e] = r < R ? split_df(A.p[0][i * R + r]) : make_float2(0.f, 0.f);
         } else {
             const int64_t f = e - na, m = f / kRT;
             const int r = (int)(f - m * kRT);
@@ -522,7 +535,7 @@ __global__ void recon_prep_rows(Shape s, Ptrs<const double> A, int nib, float2* 
 }
 
 // Pieces of v_kr = a^(N)_kr / tau_k (one warp per k; lanes r and r + 32),
-// exact in FP64, stored as the swizzled K-major image of each 32-row chunk.
+// exact in FP64, stored as the swizzled K-major image of each 64-row chunk.
 __global__ void recon_prep_v(Shape s, const double* AN, int nck, unsigned char* Vsl, float* tau) {
     const int R = s.R;
     const int64_t sN = s.dims[s.N - 1];
@@ -559,29 +572,48 @@ __global__ void recon_prep_v(Shape s, const double* AN, int nck, unsigned char* 
     }
 }
 
+// The padding rows of the last i-block of every plane tile (rows s1 .. rounded
+// up to 8) are never rows of X: zero, so that the MTTKRP of the planes reads
+// finite values there.
+__global__ void zero_pad_rows(PlaneTiling pt, int64_t s1, __nv_bfloat16* planes) {
+    const int b = pt.nib - 1;
+    const int r0 = (int)(s1 - (int64_t)b * 128), nr = pt.rows_last - r0;
+    const int64_t per_tile = 2LL * nr * 64;
+    const int64_t total = (int64_t)pt.nch * pt.mid * per_tile;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e / per_tile, w = e - t * per_tile;
+        const int c = (int)(t / pt.mid);
+        const int64_t m = t - (int64_t)c * pt.mid;
+        const int plane = (int)(w / (nr * 64)), rr = (int)(w % (nr * 64)) / 64, col = (int)(w % 64);
+        planes[pt.tile(b, c, m) + ((int64_t)plane * pt.rows_last + r0 + rr) * 64 + col] = __float2bfloat16_rn(0.f);
+    }
+}
+
 struct Layout {
     size_t a1, w, v, tau, total;
 };
 inline Layout layout_of(const Shape& s) {
-    const PlaneTiling pt = PlaneTiling::of(s);
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const int nck = (int)((s.dims[s.N - 1] + kKC - 1) / kKC);
     Layout l;
     l.a1 = 0;
-    l.w = up((size_t)pt.nib * kBI * kRT * sizeof(float2));
+    l.w = up((size_t)s.dims[0] * kRT * sizeof(float2));
     l.v = l.w + up((size_t)s.mid * kRT * sizeof(float2));
-    l.tau = l.v + up((size_t)pt.nch * 2 * kBBytes);
-    l.total = l.tau + up((size_t)pt.nch * 2 * kKC * sizeof(float));
+    l.tau = l.v + up((size_t)nck * kBBytes);
+    l.total = l.tau + up((size_t)nck * kKC * sizeof(float));
     return l;
 }
 
 }  // namespace rtc
 
-bool resid_tc_supported(const Shape& s) { return s.R <= rtc::kRT && s.N >= 2; }
+bool resid_tc_supported(const Shape& s) {
+    return s.R <= rtc::kRT && s.N >= 2 && s.dims[0] * s.mid <= 0x7fffffffLL;
+}
 
 size_t resid_tc_scratch_bytes(const Shape& s) { return rtc::layout_of(s).total; }
 
 int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                          void* scratch, DevStats* stats, int* status, cudaStream_t st) {
+                          double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st) {
     using namespace rtc;
     static bool attr_set[64] = {};
     static int sms_of[64] = {};
@@ -606,9 +638,9 @@ int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<cons
     p.s1 = s.dims[0];
     p.mid = s.mid;
     p.sN = s.dims[s.N - 1];
-    p.nib = pt.nib;
-    p.nck = pt.nch * 2;
-    p.runs = (int64_t)pt.nib * s.mid;
+    p.rows = p.s1 * p.mid;
+    p.runs = (p.rows + kBI - 1) / kBI;
+    p.nck = (int)((p.sN + kKC - 1) / kKC);
     p.pt = pt;
     p.X = X;
     p.x_f64 = xdt == CP_F64;
@@ -617,30 +649,36 @@ int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<cons
     p.Vsl = sc + l.v;
     p.tau = (const float*)(sc + l.tau);
     p.planes = (__nv_bfloat16*)planes;
+    p.E64 = E64;
     p.stats = stats;
     p.status = status;
-    recon_prep_rows<<<256, 256, 0, st>>>(s, A, pt.nib, (float2*)(sc + l.a1), (float2*)(sc + l.w));
+    int launched = 3;
+    if (planes && pt.rows_last > (int)(p.s1 - (int64_t)(pt.nib - 1) * 128)) {
+        zero_pad_rows<<<64, 256, 0, st>>>(pt, p.s1, (__nv_bfloat16*)planes);
+        ++launched;
+    }
+    recon_prep_rows<<<256, 256, 0, st>>>(s, A, (float2*)(sc + l.a1), (float2*)(sc + l.w));
     const int64_t nk = (int64_t)p.nck * kKC;
     recon_prep_v<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, st>>>(s, A.p[s.N - 1], p.nck, sc + l.v,
                                                                     (float*)(sc + l.tau));
-    // X tiles by tensor copy: FP32 X viewed as (s_N, mid, s_1), box 32 x 1 x 128, 128-byte
-    // swizzle, zero fill outside the tensor (rows i >= s_1, columns k >= s_N)
+    // X tiles by tensor copy: FP32 X viewed as the (s_1 mid) x s_N matrix of its rows,
+    // box 32 x 128, 128-byte swizzle, zero fill outside the tensor
     CUtensorMap tmX;
     memset(&tmX, 0, sizeof(tmX));
     p.x_tma = 0;
     EncodeTiledFn enc = tc_encode_fn();
     if (enc && xdt == CP_F32 && p.sN % 4 == 0 && ((uintptr_t)X & 15u) == 0) {
-        cuuint64_t dims[3] = {(cuuint64_t)p.sN, (cuuint64_t)p.mid, (cuuint64_t)p.s1};
-        cuuint64_t strides[2] = {(cuuint64_t)p.sN * 4, (cuuint64_t)p.mid * p.sN * 4};
-        cuuint32_t box[3] = {(cuuint32_t)kKC, 1, (cuuint32_t)kBI};
-        cuuint32_t es[3] = {1, 1, 1};
-        p.x_tma = enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(X), dims, strides, box, es,
+        cuuint64_t dims[2] = {(cuuint64_t)p.sN, (cuuint64_t)p.rows};
+        cuuint64_t strides[1] = {(cuuint64_t)p.sN * 4};
+        cuuint32_t box[2] = {32, (cuuint32_t)kBI};
+        cuuint32_t es[2] = {1, 1};
+        p.x_tma = enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X), dims, strides, box, es,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
     const int grid = (int)std::min<int64_t>(sms, p.runs);
     recon_tc_kernel<<<grid, kThreads, kDynSmem, st>>>(tmX, p);
-    return 3;
+    return launched;
 }
 
 }  // namespace cpgn

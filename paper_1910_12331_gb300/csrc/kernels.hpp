@@ -92,18 +92,20 @@ void launch_matvec_f64(const Shape& s, Ptrs<const double> A, const double* Gam, 
 // Loads the module of the plain matvec's kernels now (cudaFuncGetAttributes), not at their first launch.
 cudaError_t preload_matvec_f64();
 
-// ---- residual tensor in double-float, as bf16 planes in PlaneTiling layout (k_resid.cu)
+// ---- residual tensor E = X - [[A]] in extended precision (k_resid.cu): as
+// bf16 planes in PlaneTiling layout (planes, may be null) and/or in FP64,
+// C-contiguous like X (E64, may be null); sum E^2 and sum X^2 into stats.
 // scratch: resid_scratch_bytes(s) bytes (double-float copy of the factors and
 // block maxima of the first and last factor).
 void launch_resid_split(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                        void* scratch, DevStats* stats, cudaStream_t st);
+                        double* E64, void* scratch, DevStats* stats, cudaStream_t st);
 size_t resid_scratch_bytes(const Shape& s);
 // The same residual tensor with the reconstruction on the tensor cores (R <= 64):
 // error-free bf16 slice products; returns the number of kernels launched.
 bool resid_tc_supported(const Shape& s);
 size_t resid_tc_scratch_bytes(const Shape& s);
 int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                          void* scratch, DevStats* stats, int* status, cudaStream_t st);
+                          double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st);
 
 // ---- residual (k_residual.cu) ------------------------------------------------------
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,

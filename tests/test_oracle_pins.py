@@ -594,3 +594,20 @@ def test_gn_solve_is_the_step_loop_with_algorithm1_test(orc):
     for a, b in zip(A_s, A):
         assert np.array_equal(a, b)
     assert orc.residual(p["X"], A_s) <= 1e-10
+
+
+def test_residual_tensor_definition(orc):
+    """E = X - [[A]] element by element: equal to numpy's reconstruction from
+    the definition (tests/cpref.py), zero at an exact decomposition, and its
+    squared sum over ||X||^2 is the squared relative residual."""
+    from tests import cpref
+
+    rng = np.random.default_rng(61)
+    for dims, R in [((5, 4, 6), 3), ((3, 4, 2, 5), 2), ((7, 9), 4)]:
+        A = [rng.standard_normal((s, R)) for s in dims]
+        X = rng.standard_normal(dims)
+        E = orc.residual_tensor(X, A)
+        np.testing.assert_allclose(E, X - cpref.reconstruct(A), rtol=0, atol=1e-13)
+        r = orc.residual(X, A)
+        assert abs(np.sum(E * E) / np.sum(X * X) - r * r) <= 1e-13 * r * r
+        assert np.abs(orc.residual_tensor(cpref.reconstruct(A), A)).max() <= 1e-13
