@@ -33,7 +33,7 @@
 //   below 2^-40 R), scales back by sigma tau (powers of two) and subtracts from
 //   x: error below 2^-38.5 R sigma tau in all.
 //
-// Kernel: persistent, one CTA per SM, 12 warps.  A run is 128 consecutive rows
+// Kernel: persistent, one CTA per SM, 20 warps.  A run is 128 consecutive rows
 // (i, m); a step is one 64-column chunk c of k (the last chunk's MMAs are
 // only as wide as its columns, rounded up to 16).
 //   warp 0      producer: the step's pieces of v (5 x 8 KB, one bulk copy,
@@ -43,9 +43,9 @@
 //   warp 1      TMEM allocator and MMA issuer (one thread): 15 piece pairs x
 //               K/16 MMAs (M = 128, N = 64) into the four accumulators of one
 //               of two TMEM buffers (4 x 64 columns each).
-//   warps 4-11  workers: build the pieces of u for a run (5 x 16 KB), then per
-//               step drain the four accumulators (lane = row, 32 columns per
-//               warp), form E and write it.
+//   warps 4-19  workers: build the pieces of u for a run (5 x 16 KB), then per
+//               step drain the four accumulators (lane = row, 16 columns per
+//               warp in two groups of 8), form E and write it.
 // Every mbarrier wait is bounded (CP_ERR_TIMEOUT, CTA abort flag, drain).
 #include <cuda_bf16.h>
 #include <string.h>
@@ -74,7 +74,8 @@ constexpr uint32_t kBBytes = kSlices * kBSlice;    // 40 KB per step
 constexpr uint32_t kXBox = kBI * 32 * 4;           // 128 rows x 32 FP32 of X, 128-byte swizzle (one tensor copy)
 constexpr uint32_t kXTile = 2 * kXBox;             // a step's 64 columns
 constexpr uint32_t kPayload = kABytes + 2 * kBBytes + 2 * kXTile;
-constexpr int kWork = 256;
+constexpr int kWorkWarps = 16;
+constexpr int kWork = 32 * kWorkWarps;
 constexpr int kThreads = 128 + kWork;
 constexpr uint32_t kTmemCols = 512;                // 2 buffers x 4 accumulators x 64 columns
 constexpr uint32_t kDBuf = kAcc * kKC;             // TMEM columns of one buffer
@@ -107,7 +108,7 @@ struct SmemCtl {
     uint32_t tmem_base;
     int abort_flag;
     float sig[2][kBI];      // sigma of each row of a run, by run parity
-    double red[2][8];
+    double red[2][kWorkWarps];
     alignas(16) float tau_s[2][kKC];  // tau_k of a step, with its X tile
 };
 constexpr uint32_t kDynSmem = kPayload + (uint32_t)sizeof(SmemCtl);
@@ -292,21 +293,21 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
         // ------------------------------------------------------------ workers
         const int wk = warp - 4;
         const int q = warp & 3;              // TMEM lane quadrant of this warp
-        const int ch = wk >> 2;              // 32-column half of a step
+        const int cg = wk >> 2;              // 16-column group of a step
         const int row = q * 32 + lane;       // TMEM lane = row of the run
         const int et = wk * 32 + lane;       // 0 .. kWork - 1
         bool ok = true;
         float eh = 0.f, el = 0.f, xh = 0.f, xl = 0.f;
 
         // pieces of u for run j: eight lanes per row (8 rank columns = one 16-byte
-        // piece each), four rows per warp and pass, four passes
+        // piece each), four rows per warp and pass, two passes
         auto build = [&](int64_t j, int jr) {
             if (ok) ok = mbar_wait(smem_u32(&C.a_empty), (uint32_t)((jr & 1) ^ 1), abort_s, p.status);
             if (!ok) return;
             const int c8 = lane & 7;
-#pragma unroll 2
-            for (int pass = 0; pass < 4; ++pass) {
-                const int brow = pass * 32 + wk * 4 + (lane >> 3);
+#pragma unroll 1
+            for (int pass = 0; pass < kBI / (4 * kWorkWarps); ++pass) {
+                const int brow = pass * (4 * kWorkWarps) + wk * 4 + (lane >> 3);
                 const int64_t f = j * kBI + brow;
                 float2 v[8];
                 float mx = 0.f;
@@ -373,102 +374,89 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
                 // sigma of this run: written by another worker before its a_full arrival,
                 // which the MMAs behind d_full waited for
                 const float sg = C.sig[jr & 1][row];
+                const int64_t tb = live && p.planes ? p.pt.tile(b, c, m) : 0;
                 float e2 = 0.f, x2 = 0.f;
 #pragma unroll 1
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int cc = ch * 32 + hh * 16;  // first column of this group inside the chunk
+                for (int sgp = 0; sgp < 2; ++sgp) {
+                    const int cc = cg * 16 + sgp * 8;  // first column of this group inside the chunk
                     const int64_t k0 = (int64_t)c * kKC + cc;
-                    uint32_t d[kAcc][16];
+                    uint32_t d0[8], d1[8], d2[8], d3[8];
                     const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + slot * kDBuf + cc;
-                    tmem_ld16x2_wait(ta, ta + kKC, d[0], d[1]);
-                    tmem_ld16x2_wait(ta + 2 * kKC, ta + 3 * kKC, d[2], d[3]);
-                    float it[16], xv[16];
-#pragma unroll
-                    for (int u = 0; u < 16; u += 4) {
-                        const float4 t4 = *reinterpret_cast<const float4*>(&C.tau_s[slot][cc + u]);
-                        it[u] = t4.x;
-                        it[u + 1] = t4.y;
-                        it[u + 2] = t4.z;
-                        it[u + 3] = t4.w;
+                    tmem_ld8x4_wait(ta, ta + kKC, ta + 2 * kKC, ta + 3 * kKC, d0, d1, d2, d3);
+                    float it[8], xv[8];
+                    {
+                        const float4 t0 = *reinterpret_cast<const float4*>(&C.tau_s[slot][cc]);
+                        const float4 t1 = *reinterpret_cast<const float4*>(&C.tau_s[slot][cc + 4]);
+                        it[0] = t0.x, it[1] = t0.y, it[2] = t0.z, it[3] = t0.w;
+                        it[4] = t1.x, it[5] = t1.y, it[6] = t1.z, it[7] = t1.w;
                     }
+                    const bool full = live && k0 + 8 <= p.sN;  // every column of the group is in X
                     if (p.x_tma) {
                         // box cc / 32, 128-byte rows; 16-byte piece j of row r at piece j ^ (r mod 8)
                         const unsigned char* xr = dsmem + (kABytes + 2 * kBBytes) + slot * kXTile +
                                                   (cc >> 5) * kXBox + row * 128;
-#pragma unroll
-                        for (int u = 0; u < 16; u += 4) {
-                            const float4 x4 =
-                                *reinterpret_cast<const float4*>(xr + (((((cc & 31) + u) >> 2) ^ (row & 7)) << 4));
-                            xv[u] = x4.x;
-                            xv[u + 1] = x4.y;
-                            xv[u + 2] = x4.z;
-                            xv[u + 3] = x4.w;
-                        }
+                        const int j0 = (cc & 31) >> 2;
+                        const float4 x0 = *reinterpret_cast<const float4*>(xr + ((j0 ^ (row & 7)) << 4));
+                        const float4 x1 = *reinterpret_cast<const float4*>(xr + (((j0 + 1) ^ (row & 7)) << 4));
+                        xv[0] = x0.x, xv[1] = x0.y, xv[2] = x0.z, xv[3] = x0.w;
+                        xv[4] = x1.x, xv[5] = x1.y, xv[6] = x1.z, xv[7] = x1.w;
                     } else if (!p.x_f64) {
 #pragma unroll
-                        for (int u = 0; u < 16; ++u)
+                        for (int u = 0; u < 8; ++u)
                             xv[u] = (live && k0 + u < p.sN) ? __ldg(reinterpret_cast<const float*>(p.X) + f * p.sN + k0 + u)
                                                             : 0.f;
                     }
-                    if (hh == 1) {  // every read of this step's slot is done
+                    if (sgp == 1) {  // every read of this step's slot is done
                         mbar_arrive(smem_u32(&C.x_empty[slot]));
                         tc_fence_before();
                         mbar_arrive(smem_u32(&C.d_empty[slot]));
                     }
-                    uint32_t hw[8], lw[8];
+                    float ev[8];
 #pragma unroll
-                    for (int u = 0; u < 16; u += 2) {
-                        float ev[2];
-#pragma unroll
-                        for (int v = 0; v < 2; ++v) {
-                            const int w = u + v;
-                            const int64_t k = k0 + w;
-                            const bool valid = live && k < p.sN;
-                            // levels 2 and 3 exactly as (h, l); levels 4..6 join l
-                            float h, l;
-                            two_sum(__uint_as_float(d[0][w]), __uint_as_float(d[1][w]), h, l);
-                            l += __uint_as_float(d[2][w]) + __uint_as_float(d[3][w]);
-                            const float tk = it[w];
-                            float e = 0.f;
-                            if (p.x_f64) {  // X in FP64: the subtraction in FP64
-                                const double xd = valid ? reinterpret_cast<const double*>(p.X)[f * p.sN + k] : 0.0;
-                                const double st = (double)sg * (double)tk;
-                                const double ed = (xd - (double)h * st) - (double)l * st;
-                                if (valid && p.E64) p.E64[f * p.sN + k] = ed;
-                                e = valid ? (float)ed : 0.f;
-                                xv[w] = (float)xd;
-                            } else if (valid) {
-                                // x - h sigma tau is exact near the optimum (Sterbenz); the scalings
-                                // by powers of two are exact
-                                const float hs = (h * sg) * tk, ls = (l * sg) * tk;
-                                e = (xv[w] - hs) - ls;
-                                if (p.E64) p.E64[f * p.sN + k] = ((double)xv[w] - (double)hs) - (double)ls;
-                            }
-                            ev[v] = e;
-                            const float xm = valid ? xv[w] : 0.f;  // columns beyond s_N may hold stale data
-                            e2 = fmaf(e, e, e2);
-                            x2 = fmaf(xm, xm, x2);
+                    for (int w = 0; w < 8; ++w) {
+                        const int64_t k = k0 + w;
+                        const bool valid = full || (live && k < p.sN);
+                        // levels 2 and 3 exactly as (h, l); levels 4..6 join l
+                        float h, l;
+                        two_sum(__uint_as_float(d0[w]), __uint_as_float(d1[w]), h, l);
+                        l += __uint_as_float(d2[w]) + __uint_as_float(d3[w]);
+                        const float tk = it[w];
+                        float e = 0.f;
+                        if (p.x_f64) {  // X in FP64: the subtraction in FP64
+                            const double xd = valid ? reinterpret_cast<const double*>(p.X)[f * p.sN + k] : 0.0;
+                            const double st = (double)sg * (double)tk;
+                            const double ed = (xd - (double)h * st) - (double)l * st;
+                            if (valid && p.E64) p.E64[f * p.sN + k] = ed;
+                            e = valid ? (float)ed : 0.f;
+                            xv[w] = (float)xd;
+                        } else if (valid) {
+                            // x - h sigma tau is exact near the optimum (Sterbenz); the scalings
+                            // by powers of two are exact
+                            const float hs = (h * sg) * tk, ls = (l * sg) * tk;
+                            e = (xv[w] - hs) - ls;
+                            if (p.E64) p.E64[f * p.sN + k] = ((double)xv[w] - (double)hs) - (double)ls;
                         }
-                        const __nv_bfloat162 hi2 = __floats2bfloat162_rn(ev[0], ev[1]);
-                        const float2 hf = __bfloat1622float2(hi2);
-                        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(ev[0] - hf.x, ev[1] - hf.y);
-                        hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&hi2);
-                        lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&lo2);
+                        ev[w] = e;
+                        const float xm = valid ? xv[w] : 0.f;  // columns beyond s_N may hold stale data
+                        e2 = fmaf(e, e, e2);
+                        x2 = fmaf(xm, xm, x2);
                     }
                     if (live && p.planes) {
-                        // 16 columns = two 16-byte pieces of the row in each plane
-                        const int64_t tb = p.pt.tile(b, c, m);
-                        __nv_bfloat16* r0 = p.planes + tb + (int64_t)r * 64;
-                        __nv_bfloat16* r1 = p.planes + tb + ((int64_t)rows_b + r) * 64;
+                        // 8 columns = one 16-byte piece of the row in each plane
+                        uint32_t hw[4], lw[4];
 #pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            const int j8 = (cc >> 3) + h2;
-                            const int pos = ((j8 ^ (r & 7)) << 3);
-                            *reinterpret_cast<uint4*>(r0 + pos) =
-                                make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
-                            *reinterpret_cast<uint4*>(r1 + pos) =
-                                make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
+                        for (int u = 0; u < 8; u += 2) {
+                            const __nv_bfloat162 hi2 = __floats2bfloat162_rn(ev[u], ev[u + 1]);
+                            const float2 hf = __bfloat1622float2(hi2);
+                            const __nv_bfloat162 lo2 = __floats2bfloat162_rn(ev[u] - hf.x, ev[u + 1] - hf.y);
+                            hw[u >> 1] = *reinterpret_cast<const uint32_t*>(&hi2);
+                            lw[u >> 1] = *reinterpret_cast<const uint32_t*>(&lo2);
                         }
+                        const int pos = (((cc >> 3) ^ (r & 7)) << 3);
+                        *reinterpret_cast<uint4*>(p.planes + tb + (int64_t)r * 64 + pos) =
+                            make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(p.planes + tb + ((int64_t)rows_b + r) * 64 + pos) =
+                            make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
                 }
                 float s1, s2;
@@ -489,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) recon_tc_kernel(const __grid_cons
         named_sync(1, kWork);
         if (et == 0) {
             double a = 0.0, bsum = 0.0;
-            for (int w = 0; w < 8; ++w) {
+            for (int w = 0; w < kWorkWarps; ++w) {
                 a += C.red[0][w];
                 bsum += C.red[1][w];
             }
