@@ -26,6 +26,9 @@ Parity status of each routine (pins live in ``tests/test_oracle_pins.py``):
                         the column rescaling of the CP model)
   lambda_next           pinned (hand-derived sequence, golden fixture)
   gn_step               pinned (exact recovery of exact-rank tensors)
+  gn_step_ls            pinned (Armijo's condition holds at the accepted step and
+                        fails at the one before, monotone objective, the full
+                        step is taken near an exact decomposition, constant lambda)
   residual              pinned (numpy reconstruction, zero at exact factors)
   residual_tensor       pinned (numpy reconstruction, zero at exact factors, its
                         squared sum is the residual's numerator)
@@ -94,6 +97,11 @@ def _load():
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, dp]
             lib.orc_gn_step.restype = ctypes.c_int
+            lib.orc_gn_step_ls.argtypes = [d, dp, dp, dp, P(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, dp]
+            lib.orc_gn_step_ls.restype = ctypes.c_int
             lib.orc_gn_solve.argtypes = [d, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
@@ -236,6 +244,29 @@ def gn_step(X, A, lam, direction, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind=0
     keys = ("grad_norm_sum", "update_norm_sum", "lam_used", "cg_iters", "cg_rnorm", "m_norm_sum")
     s = dict(zip(keys, stats.tolist()))
     s["cg_iters"] = int(s["cg_iters"])
+    return _unpack(Abuf, dims, R), float(l[0]), dr.value, s, st
+
+
+def gn_step_ls(X, A, lam, direction, lam_lo, lam_hi, mu, eps_cg, maxit, use_dt=False, reg=REG_IDENTITY,
+               lam_fixed=False, armijo_c=0.0, armijo_beta=0.5, armijo_max=10):
+    """One CP-GN iteration with a constant lambda (lam_fixed) and/or Armijo
+    step-size control (armijo_c > 0).  Returns (A_new, lam, dir, stats, status);
+    stats as gn_step plus step (t applied), f0 (1/2 ||X - [[A]]||^2 at entry, -1
+    without the line search) and trials."""
+    X = _x64(X)
+    dims, R = list(X.shape), A[0].shape[1]
+    Abuf = _pack(A)
+    l = np.array([lam], dtype=np.float64)
+    dr = ctypes.c_int(int(direction))
+    stats = np.zeros(9)
+    st = _load().orc_gn_step_ls(ctypes.byref(_desc(dims, R)), _ptr(X), _ptr(Abuf), _ptr(l), ctypes.byref(dr),
+                                float(lam_lo), float(lam_hi), float(mu), float(eps_cg), int(maxit),
+                                int(bool(use_dt)), int(reg), int(bool(lam_fixed)), float(armijo_c),
+                                float(armijo_beta), int(armijo_max), _ptr(stats))
+    keys = ("grad_norm_sum", "update_norm_sum", "lam_used", "cg_iters", "cg_rnorm", "m_norm_sum", "step", "f0",
+            "trials")
+    s = dict(zip(keys, stats.tolist()))
+    s["cg_iters"], s["trials"] = int(s["cg_iters"]), int(s["trials"])
     return _unpack(Abuf, dims, R), float(l[0]), dr.value, s, st
 
 

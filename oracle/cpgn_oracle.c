@@ -485,6 +485,17 @@ void orc_lambda_next(double* lam, int* dir, double lo, double hi, double mu) {
 
 /* ------------------------------------------------------------------ GN step */
 
+static double sq_residual(const orc_desc* d, const double* X, const double* A, double* sq_x);
+
+/* Options of one GN iteration beyond Algorithm 1's plain loop body. */
+typedef struct {
+    double stop_ratio;   /* > 0: Algorithm 1's loop test at the entry point (see gn_iteration) */
+    int lam_fixed;       /* 1: lambda stays constant (constant regularisation, Section 5) */
+    double armijo_c;     /* > 0: step-size control by Armijo's condition (Section 5) */
+    double armijo_beta;  /* step reduction factor of the backtracking, 0 < beta < 1 */
+    int armijo_max;      /* reductions tried after the full step */
+} gn_opts;
+
 /* One iteration of CP-GN, Algorithm 1: M^(n) for all n, Gamma^(n,p), G^(n),
  * then Algorithm 1's loop test (stop_ratio > 0: if sum_n ||G^(n)||_F <=
  * stop_ratio sum_n ||M^(n)||_F -- the scale-free reading of the test on
@@ -494,7 +505,8 @@ void orc_lambda_next(double* lam, int* dir, double lo, double hi, double mu) {
  * stats as orc_gn_step. */
 static int gn_iteration(const orc_desc* d, const double* X, double* A, double* lam, int* dir, double lam_lo,
                         double lam_hi, double mu, double eps_cg, int maxit, int beta_kind, int use_dt, int reg,
-                        double stop_ratio, double* stats, int* stopped) {
+                        const gn_opts* o, double* stats, int* stopped) {
+    const double stop_ratio = o->stop_ratio;
     const int N = d->N, R = d->R;
     const int64_t len = factor_total(d);
     double* M = (double*)malloc(sizeof(double) * len);
@@ -515,11 +527,34 @@ static int gn_iteration(const orc_desc* d, const double* X, double* A, double* l
     const double lam_used = *lam;
     int status = ORC_OK;
     *stopped = stop_ratio > 0.0 && gsum <= stop_ratio * msum;
+    double step = 1.0, f0 = -1.0;
+    int trials = 0;
     if (!*stopped) {
         status = orc_pcg(d, A, Gam, G, lam_used, reg, eps_cg, maxit, beta_kind, V, &iters, &rnorm);
+        if ((status == ORC_OK || status == ORC_WARN_CG_MAXIT) && o->armijo_c > 0.0) {
+            /* Armijo's condition on f = 1/2 ||X - [[A]]||^2 along V: accept the first
+             * t in 1, beta, beta^2, ... with f(A + t V) <= f(A) + c t <grad f, V>
+             * (grad f = G, Eq. (2.3)); none accepted: no update (t = 0). */
+            double* At = (double*)malloc(sizeof(double) * len);
+            double unused;
+            f0 = 0.5 * sq_residual(d, X, A, &unused);
+            double slope = 0.0;
+            for (int64_t i = 0; i < len; ++i) slope += G[i] * V[i];
+            double t = 1.0;
+            step = 0.0;
+            for (int k = 0; k <= o->armijo_max; ++k, t *= o->armijo_beta) {
+                for (int64_t i = 0; i < len; ++i) At[i] = A[i] + t * V[i];
+                ++trials;
+                if (0.5 * sq_residual(d, X, At, &unused) <= f0 + o->armijo_c * t * slope) {
+                    step = t;
+                    break;
+                }
+            }
+            free(At);
+        }
         if (status == ORC_OK || status == ORC_WARN_CG_MAXIT) {
-            for (int64_t i = 0; i < len; ++i) A[i] += V[i];
-            orc_lambda_next(lam, dir, lam_lo, lam_hi, mu);
+            for (int64_t i = 0; i < len; ++i) A[i] += step * V[i];
+            if (!o->lam_fixed) orc_lambda_next(lam, dir, lam_lo, lam_hi, mu);
         }
     }
     stats[0] = gsum;
@@ -528,6 +563,9 @@ static int gn_iteration(const orc_desc* d, const double* X, double* A, double* l
     stats[3] = iters;
     stats[4] = rnorm;
     stats[5] = msum;
+    stats[6] = step;
+    stats[7] = f0;
+    stats[8] = trials;
     free(M); free(G); free(V); free(S); free(Gam);
     return status;
 }
@@ -544,8 +582,27 @@ int orc_gn_step(const orc_desc* d, const double* X, double* A, double* lam, int*
                 double lam_hi, double mu, double eps_cg, int maxit, int beta_kind, int use_dt, int reg,
                 double* stats) {
     int stopped = 0;
-    return gn_iteration(d, X, A, lam, dir, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind, use_dt, reg, 0.0, stats,
-                        &stopped);
+    const gn_opts o = {0.0, 0, 0.0, 0.5, 0};
+    double st[9];
+    const int status = gn_iteration(d, X, A, lam, dir, lam_lo, lam_hi, mu, eps_cg, maxit, beta_kind, use_dt, reg,
+                                    &o, st, &stopped);
+    for (int k = 0; k < 6; ++k) stats[k] = st[k];
+    return status;
+}
+
+/* One iteration of Algorithm 1 with the options of Section 5's experiments:
+ * a constant lambda (lam_fixed = 1) and step-size control by Armijo's
+ * condition (armijo_c > 0; backtracking by armijo_beta, at most armijo_max
+ * reductions).  stats[0..5] as orc_gn_step, stats[6] = the step length t
+ * applied (1 without the line search; 0 when no trial met the condition),
+ * stats[7] = f(A) = 1/2 ||X - [[A]]||_F^2 at the entry point (-1 without the
+ * line search), stats[8] = trial points evaluated. */
+int orc_gn_step_ls(const orc_desc* d, const double* X, double* A, double* lam, int* dir, double lam_lo,
+                   double lam_hi, double mu, double eps_cg, int maxit, int use_dt, int reg, int lam_fixed,
+                   double armijo_c, double armijo_beta, int armijo_max, double* stats) {
+    int stopped = 0;
+    const gn_opts o = {0.0, lam_fixed, armijo_c, armijo_beta, armijo_max};
+    return gn_iteration(d, X, A, lam, dir, lam_lo, lam_hi, mu, eps_cg, maxit, 0, use_dt, reg, &o, stats, &stopped);
 }
 
 /* Algorithm 1 to a target: GN iterations from A (in/out) with lambda starting
@@ -559,12 +616,13 @@ int orc_gn_step(const orc_desc* d, const double* X, double* A, double* lam, int*
 int orc_gn_solve(const orc_desc* d, const double* X, double* A, double lam0, double lam_lo, double lam_hi,
                  double mu, double eps_cg, int maxit, double target, int max_gn, int use_dt, int reg,
                  double* out) {
-    double lam = lam0, stats[6];
+    double lam = lam0, stats[9];
     int dir = 0, status = ORC_OK, updates = 0, cg = 0, stopped = 0;
     double ratio = 0.0;
+    const gn_opts o = {target, 0, 0.0, 0.5, 0};
     while (updates < max_gn) {
-        status = gn_iteration(d, X, A, &lam, &dir, lam_lo, lam_hi, mu, eps_cg, maxit, 0, use_dt, reg, target,
-                              stats, &stopped);
+        status = gn_iteration(d, X, A, &lam, &dir, lam_lo, lam_hi, mu, eps_cg, maxit, 0, use_dt, reg, &o, stats,
+                              &stopped);
         ratio = stats[5] > 0.0 ? stats[0] / stats[5] : 0.0;
         if (stopped) break;
         if (status != ORC_OK && status != ORC_WARN_CG_MAXIT) break;
@@ -595,6 +653,14 @@ void orc_set_threads(int n) {
  * reconstruction evaluated element by element from Section 2.2's CP model and
  * both squared sums accumulated with Kahan compensation. */
 double orc_residual(const orc_desc* d, const double* X, const double* A) {
+    double den = 0.0;
+    const double num = sq_residual(d, X, A, &den);
+    return sqrt(num) / sqrt(den);
+}
+
+/* ||X - [[A]]||_F^2, with *sq_x = ||X||_F^2: the reconstruction evaluated
+ * element by element, both sums with Kahan compensation. */
+static double sq_residual(const orc_desc* d, const double* X, const double* A, double* sq_x) {
     const int N = d->N, R = d->R;
     const int64_t total = tensor_size(d);
     double num = 0.0, den = 0.0;
@@ -620,7 +686,8 @@ double orc_residual(const orc_desc* d, const double* X, const double* A) {
 #pragma omp critical
         { num += s_num; den += s_den; }
     }
-    return sqrt(num) / sqrt(den);
+    *sq_x = den;
+    return num;
 }
 
 /* The residual tensor E = X - [[A]] element by element (Section 2.2's CP

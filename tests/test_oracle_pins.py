@@ -611,3 +611,63 @@ def test_residual_tensor_definition(orc):
         r = orc.residual(X, A)
         assert abs(np.sum(E * E) / np.sum(X * X) - r * r) <= 1e-13 * r * r
         assert np.abs(orc.residual_tensor(cpref.reconstruct(A), A)).max() <= 1e-13
+
+
+def _armijo_case(orc):
+    """A 6x5x7 random tensor, R = 4, after two plain GN steps at a constant
+    lambda = 1e-4: the full third step raises the objective (84.75 -> 121.76)."""
+    rng = np.random.default_rng(0)
+    dims, R = (6, 5, 7), 4
+    X = rng.standard_normal(dims)
+    A = [rng.standard_normal((s, R)) for s in dims]
+    for _ in range(2):
+        A, _, _, _, _ = orc.gn_step_ls(X, A, 1e-4, 0, 1e-9, 1.0, 2.0, 1e-10, 60, lam_fixed=True)
+    return X, A
+
+
+def test_armijo_condition_at_the_accepted_step(orc):
+    """Section 5's step-size control by Armijo's condition: the step taken is
+    the first t in 1, 1/2, 1/4, ... with f(A + tV) <= f(A) + c t <grad f, V>,
+    checked with numpy's objective (tests/cpref.py) and the oracle's pinned
+    gradient; the trial before it fails the condition; f decreases."""
+    from tests import cpref
+
+    X, A = _armijo_case(orc)
+    c = 1e-4
+    A_full, _, _, _, _ = orc.gn_step_ls(X, A, 1e-4, 0, 1e-9, 1.0, 2.0, 1e-10, 60, lam_fixed=True)
+    A_ls, lam, _, s, st = orc.gn_step_ls(X, A, 1e-4, 0, 1e-9, 1.0, 2.0, 1e-10, 60, lam_fixed=True, armijo_c=c)
+    assert st in (orc.OK, orc.WARN_CG_MAXIT) and lam == 1e-4  # constant lambda
+    V = [af - a for af, a in zip(A_full, A)]  # the full GN direction
+    G, _ = orc.gradient(A, orc.gamma(orc.gram(A)), orc.mttkrp(X, A))
+    slope = sum(float(np.sum(g * v)) for g, v in zip(G, V))
+    f0 = cpref.objective(X, A)
+    assert abs(s["f0"] - f0) <= 1e-12 * f0 and slope < 0
+    t = s["step"]
+    assert t == 0.5 and s["trials"] == 2
+    for a_ls, a, v in zip(A_ls, A, V):
+        np.testing.assert_allclose(a_ls, a + t * v, rtol=0, atol=1e-12)
+    assert cpref.objective(X, A_ls) <= f0 + c * t * slope
+    assert cpref.objective(X, [a + 2 * t * v for a, v in zip(A, V)]) > f0 + c * 2 * t * slope
+    assert cpref.objective(X, A_ls) < f0
+
+
+def test_armijo_full_step_near_exact_decomposition(orc):
+    """Close to an exact decomposition the GN step is nearly a Newton step and
+    the full step meets Armijo's condition at once."""
+    from paper_1910_12331_gb300 import datagen
+
+    p = datagen.workload("exact20", seed=0)
+    rng = np.random.default_rng(5)
+    A = [a + 1e-4 * rng.standard_normal(a.shape) for a in p["truth"]]
+    _, _, _, s, st = orc.gn_step_ls(p["X"], A, 1e-6, 0, 1e-9, 1.0, 2.0, 1e-10, 100, lam_fixed=True, armijo_c=1e-4)
+    assert st in (orc.OK, orc.WARN_CG_MAXIT) and s["step"] == 1.0 and s["trials"] == 1
+
+
+def test_armijo_off_is_the_plain_step(orc):
+    """armijo_c = 0 and a varying lambda: bit for bit the plain GN step."""
+    X, A = _armijo_case(orc)
+    A1, l1, d1, s1, st1 = orc.gn_step(X, A, 0.3, 0, 1e-3, 1.0, 2.0, 1e-3, 50)
+    A2, l2, d2, s2, st2 = orc.gn_step_ls(X, A, 0.3, 0, 1e-3, 1.0, 2.0, 1e-3, 50)
+    assert st1 == st2 and l1 == l2 and d1 == d2 and s2["step"] == 1.0
+    for a, b in zip(A1, A2):
+        assert np.array_equal(a, b)
