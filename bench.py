@@ -335,10 +335,25 @@ def batched_timing(dev, count=512):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    threads = plan.threads
+    threads, order = plan.threads, plan.order
     plan.close()
     h.close()
     conv = sum(r["converged"] for r in res)
+    # the same batch with step-size control by Armijo's condition (one-shot call, untimed beside the graph)
+    b_ls = []
+    for q, a0 in zip(b, init):
+        q2 = dict(q, A=[a.clone() for a in a0], armijo_c=1e-4, armijo_beta=0.5, armijo_max=10)
+        b_ls.append(q2)
+    t1 = time.perf_counter()
+    res_ls = api.cp_gn_solve_batched(h, b_ls, EPS_CG, CG_MAX, 200, 1e-6)
+    t_ls = time.perf_counter() - t1
+    armijo = {"converged": sum(r["converged"] for r in res_ls), "wall_s": t_ls,
+              "gn_iters_mean": float(np.mean([r["iters"] for r in res_ls])),
+              "backtracks": sum(r["ls_backtracks"] for r in res_ls),
+              "status_counts": {str(k): sum(1 for r in res_ls if r["status"] == k)
+                                for k in sorted({r["status"] for r in res_ls})},
+              "not_converged": [{"problem": i, "status": r["status"], "iters": r["iters"],
+                                 "rel_residual": r["rel_residual"]} for i, r in enumerate(res_ls) if not r["converged"]]}
     return {"workload": f"{count} order-3 FP32 problems, sides U{{16..96}}, ranks U{{4..24}}, N(0,1) factors, "
                         "1e-8 noise; target r <= 1e-6 or 200 GN iterations",
             "ms": ms, "problems_per_s": count / (ms / 1e3), "converged": conv,
@@ -347,7 +362,8 @@ def batched_timing(dev, count=512):
             "cg_breakdowns": sum(r["cg_breakdowns"] for r in res),
             "status_counts": {str(k): sum(1 for r in res if r["status"] == k) for k in sorted({r["status"] for r in res})},
             "launches": 1, "graph": "one captured plan launch, replayed", "threads_per_cta": threads,
-            "autotune_s": tune_s}
+            "problem_order": ["given", "largest work first"][order], "autotune_s": tune_s,
+            "with_armijo": armijo}
 
 
 def run_kernel(which):

@@ -120,6 +120,15 @@ typedef struct {
     double stop_stationarity; /* > 0: if sum||G||/sum||M|| <= this at the entry point, apply no
                                  update and report stats.stopped = 1 (Algorithm 1's loop test) */
     int64_t spin_limit;   /* grid-barrier spin limit in polls; 0 selects the default (~seconds) */
+    /* Step-size control by Armijo's condition (Section 5, the matrix-multiplication
+     * experiments): armijo_c > 0 takes the first t in 1, beta, beta^2, ..., beta^armijo_max
+     * with f(A + t V) <= f(A) + armijo_c t <G, V> + 2 R 2^-53 ||X||^2 (the last term: the
+     * accuracy of f = 1/2 ||X - [[A]]||_F^2 evaluated by the direct FP64 reconstruction, as
+     * cp_residual), <G, V> summed in a fixed order; A += t V, or no update (t = 0) if no
+     * trial meets it.  armijo_c = 0: the full step. */
+    double armijo_c;      /* 0 <= c < 1 (paper: unspecified; 1e-4 is usual) */
+    double armijo_beta;   /* 0 < beta < 1 when armijo_c > 0 */
+    int armijo_max;       /* >= 0 reductions after the full step */
 } cp_gn_params;
 
 typedef struct {
@@ -139,6 +148,9 @@ typedef struct {
     double step_ms;          /* device time of the whole step */
     int kernel_launches;     /* kernels this step launched */
     int cg_blocks;           /* blocks of the persistent CG kernel's launch (0 if it did not run) */
+    double step;             /* step length t applied (1 without the line search, 0: rejected) */
+    double f_entry;          /* f = 1/2 ||X - [[A]]||_F^2 at the entry point (line search), or -1 */
+    int ls_trials;           /* trial points the line search evaluated */
 } cp_gn_stats;
 
 /* Human-readable name of a status code (static storage; unknown codes give
@@ -212,7 +224,9 @@ cp_status cp_gn_matvec(cp_handle h, const cp_desc* desc, const double* const* A,
  * preconditioner (Gamma^(n,n) + lambda D)^{-1} with D = I or diag(Gamma^(n,n))
  * by params->reg (Cholesky then explicit inverse, Section 3.3), CP-CG
  * (Algorithm 2, standard PCG beta) as one persistent device kernel, then
- * A^(n) += V^(n) in place, then lambda advances (unless lam_fixed).  A is
+ * A^(n) += t V^(n) in place (t = 1, or chosen by Armijo's condition when
+ * params->armijo_c > 0; the line search synchronises once per trial), then
+ * lambda advances (unless lam_fixed).  A is
  * in/out.  Synchronises; fills *stats (host, may be NULL).  Returns the step's
  * status: CP_OK, CP_WARN_CG_MAXIT (update applied), or an error (A unchanged
  * for CP_ERR_NOT_SPD, CP_ERR_NONFINITE, CP_ERR_UNSUPPORTED; unspecified for
@@ -322,6 +336,13 @@ typedef struct {
     const float* X;        /* device, FP32, C-contiguous s_1 x s_2 x s_3 (caller-owned) */
     double* A[3];          /* device, FP64 row-major s_n x R, in/out (caller-owned) */
     double lam, lam_lo, lam_hi, mu;  /* regularisation of Section 3.2 */
+    int reg;               /* cp_reg: damping lam I (0) or lam diag(J^T J) (1) */
+    int lam_fixed;         /* 1: lambda stays lam (constant regularisation) */
+    double armijo_c;       /* > 0: step-size control by Armijo's condition (as cp_gn_params, with
+                              f the residual of the stop test, relaxed by its FP32 accuracy
+                              2 R 2^-24 ||X||^2, and <G, V> from the CG recurrences); 0: full steps */
+    double armijo_beta;    /* step reduction factor, 0 < beta < 1 when armijo_c > 0 */
+    int armijo_max;        /* reductions after the full step (>= 0) */
 } cp_batch_problem;
 
 typedef struct {
@@ -333,6 +354,7 @@ typedef struct {
                               positive (the update found so far is applied) */
     double rel_residual;   /* last residual evaluated (FP32 reconstruction, FP64 sums) */
     double lam;            /* lambda of the last iteration */
+    int ls_backtracks;     /* step reductions the line search took in all */
 } cp_batch_result;
 
 /* Many small order-3 problems, each by Algorithm 1 with CP-CG (Algorithm 2)
@@ -341,7 +363,9 @@ typedef struct {
  * problem needs, 8 (R^2 + R + 96) + 4 (6 (s_1 + s_2 + s_3) R + 21 R^2) bytes,
  * must not exceed 220 KB (CP_ERR_UNSUPPORTED).  Synchronises.
  * Errors: CP_ERR_ARG (null pointers, sizes out of range, mu <= 1, lam < 0,
- * lam_hi < lam_lo), CP_ERR_UNSUPPORTED, CP_ERR_NOMEM, CP_ERR_CUDA; per-problem
+ * lam_hi < lam_lo, unknown reg, armijo_c outside [0, 1), armijo_beta outside
+ * (0, 1) or armijo_max < 0 with armijo_c > 0), CP_ERR_UNSUPPORTED,
+ * CP_ERR_NOMEM, CP_ERR_CUDA; per-problem
  * device errors go to results[i].status. */
 cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* problems, double eps_cg,
                               int cg_max_iter, int max_iters, double target_residual, cp_batch_result* results);
@@ -349,9 +373,11 @@ cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* pr
 /* The same batched solve as a reusable plan: cp_batch_plan_create checks the
  * problems (same rules and errors as cp_gn_solve_batched), copies their
  * descriptors to the device, allocates the results and, if `autotune` is
- * nonzero, times the kernel's block sizes (128, 256 and 384 threads) on a
- * device copy of the factors of at most 64 of the problems -- the caller's
- * factors are not modified -- and keeps the fastest (otherwise 256).
+ * nonzero, times the kernel's block sizes (128, 256 and 384 threads), each with
+ * the problems taken in the given order and largest work first (s_1 s_2 s_3 R,
+ * the persistent CTAs' longest-processing-time order), on a device copy of the
+ * factors of at most 64 of the problems -- the caller's factors are not
+ * modified -- and keeps the fastest (otherwise 256 threads, given order).
  * Synchronises.  The plan keeps the device pointers of the problems: X and A
  * must stay allocated while the plan is used.
  *
@@ -362,7 +388,8 @@ cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* pr
  * Launches of one plan must not overlap on the GPU (they share the counter
  * and the results).  cp_batch_plan_results copies the results of the last
  * completed launch to `results` (host, nprob entries); synchronises.
- * cp_batch_plan_threads returns the block size in use.  cp_batch_plan_destroy
+ * cp_batch_plan_threads returns the block size in use, cp_batch_plan_order the
+ * problem order (0: as given, 1: largest work first).  cp_batch_plan_destroy
  * frees the plan's device memory (after its launches have finished; the
  * caller's current device is kept) and the plan.  Errors: CP_ERR_ARG,
  * CP_ERR_UNSUPPORTED, CP_ERR_NOMEM, CP_ERR_CUDA. */
@@ -373,6 +400,7 @@ cp_status cp_batch_plan_create(cp_handle h, int nprob, const cp_batch_problem* p
 cp_status cp_batch_plan_launch(cp_handle h, cp_batch_plan plan);
 cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result* results);
 cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads);
+cp_status cp_batch_plan_order(cp_batch_plan plan, int* order);
 cp_status cp_batch_plan_destroy(cp_batch_plan plan);
 
 /* ---------------------------------------------------------------------------

@@ -534,10 +534,14 @@ static int gn_iteration(const orc_desc* d, const double* X, double* A, double* l
         if ((status == ORC_OK || status == ORC_WARN_CG_MAXIT) && o->armijo_c > 0.0) {
             /* Armijo's condition on f = 1/2 ||X - [[A]]||^2 along V: accept the first
              * t in 1, beta, beta^2, ... with f(A + t V) <= f(A) + c t <grad f, V>
-             * (grad f = G, Eq. (2.3)); none accepted: no update (t = 0). */
+             * (grad f = G, Eq. (2.3)) up to the evaluation accuracy of f; none
+             * accepted: no update (t = 0). */
             double* At = (double*)malloc(sizeof(double) * len);
-            double unused;
-            f0 = 0.5 * sq_residual(d, X, A, &unused);
+            double unused, xx;
+            f0 = 0.5 * sq_residual(d, X, A, &xx);
+            /* the condition is relaxed by the accuracy of the FP64 evaluation of f,
+             * 2 R 2^-53 ||X||^2, so that steps below it are not rejected on rounding */
+            const double tol_f = 2.0 * R * 0x1p-53 * xx;
             double slope = 0.0;
             for (int64_t i = 0; i < len; ++i) slope += G[i] * V[i];
             double t = 1.0;
@@ -545,7 +549,7 @@ static int gn_iteration(const orc_desc* d, const double* X, double* A, double* l
             for (int k = 0; k <= o->armijo_max; ++k, t *= o->armijo_beta) {
                 for (int64_t i = 0; i < len; ++i) At[i] = A[i] + t * V[i];
                 ++trials;
-                if (0.5 * sq_residual(d, X, At, &unused) <= f0 + o->armijo_c * t * slope) {
+                if (0.5 * sq_residual(d, X, At, &unused) <= f0 + o->armijo_c * t * slope + tol_f) {
                     step = t;
                     break;
                 }

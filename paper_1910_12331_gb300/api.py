@@ -30,7 +30,7 @@ REG = {"identity": CP_REG_IDENTITY, "diag": CP_REG_DIAG}
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
            "cp_residual", "cp_residual_sums", "cp_residual_tensor", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
-           "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads",
+           "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads", "cp_batch_plan_order",
            "cp_batch_plan_destroy", "cp_probe_grid_barrier", "cp_probe_fp64_fma")
 
 
@@ -44,7 +44,8 @@ class cp_gn_params(ctypes.Structure):
                 ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double), ("mu", ctypes.c_double),
                 ("lam_dir", ctypes.c_int), ("lam_fixed", ctypes.c_int), ("reg", ctypes.c_int), ("prec", ctypes.c_int),
                 ("cg_fp32", ctypes.c_int), ("want_residual", ctypes.c_int),
-                ("stop_stationarity", ctypes.c_double), ("spin_limit", ctypes.c_int64)]
+                ("stop_stationarity", ctypes.c_double), ("spin_limit", ctypes.c_int64),
+                ("armijo_c", ctypes.c_double), ("armijo_beta", ctypes.c_double), ("armijo_max", ctypes.c_int)]
 
 
 class cp_gn_stats(ctypes.Structure):
@@ -53,7 +54,8 @@ class cp_gn_stats(ctypes.Structure):
                 ("update_norm_sum", ctypes.c_double), ("factor_norm_sum", ctypes.c_double),
                 ("lam_used", ctypes.c_double), ("cg_rnorm", ctypes.c_double), ("rel_residual", ctypes.c_double),
                 ("entry_residual", ctypes.c_double), ("mttkrp_ms", ctypes.c_double), ("pcg_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int), ("cg_blocks", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("cg_blocks", ctypes.c_int), ("step", ctypes.c_double),
+                ("f_entry", ctypes.c_double), ("ls_trials", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,13 +85,15 @@ _lib = None
 class cp_batch_problem(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int64 * 3), ("rank", ctypes.c_int), ("X", ctypes.c_void_p),
                 ("A", ctypes.c_void_p * 3), ("lam", ctypes.c_double), ("lam_lo", ctypes.c_double),
-                ("lam_hi", ctypes.c_double), ("mu", ctypes.c_double)]
+                ("lam_hi", ctypes.c_double), ("mu", ctypes.c_double), ("reg", ctypes.c_int),
+                ("lam_fixed", ctypes.c_int), ("armijo_c", ctypes.c_double), ("armijo_beta", ctypes.c_double),
+                ("armijo_max", ctypes.c_int)]
 
 
 class cp_batch_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cg_iters_total", ctypes.c_int),
                 ("converged", ctypes.c_int), ("cg_breakdowns", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("lam", ctypes.c_double)]
+                ("lam", ctypes.c_double), ("ls_backtracks", ctypes.c_int)]
 
 
 class CPError(RuntimeError):
@@ -140,6 +144,7 @@ def load(build_if_missing: bool = False):
         L.cp_batch_plan_launch.argtypes = [vp, vp]
         L.cp_batch_plan_results.argtypes = [vp, vp, ctypes.POINTER(cp_batch_result)]
         L.cp_batch_plan_threads.argtypes = [vp, ctypes.POINTER(i)]
+        L.cp_batch_plan_order.argtypes = [vp, ctypes.POINTER(i)]
         L.cp_batch_plan_destroy.argtypes = [vp]
         L.cp_probe_grid_barrier.argtypes = [i, i, i, i, ctypes.POINTER(d)]
         L.cp_probe_fp64_fma.argtypes = [i, ctypes.POINTER(d)]
@@ -355,9 +360,10 @@ def cp_gn_matvec(h: Handle, A, W, lam, Q=None, grams=None, reg="identity", prec=
 
 def gn_params(lam, lam_lo, lam_hi, mu=2.0, eps_cg=1e-3, cg_max_iter=250, prec="fp64", cg_fp32=None,
               lam_dir=0, lam_fixed=False, want_residual=False, stop_stationarity=0.0, spin_limit=0,
-              reg="identity"):
+              reg="identity", armijo_c=0.0, armijo_beta=0.5, armijo_max=10):
     """reg: "identity" damps by lam I, "diag" by lam diag(J^T J) (then lam is
-    dimensionless)."""
+    dimensionless); armijo_c > 0 turns on step-size control by Armijo's
+    condition (backtracking by armijo_beta, at most armijo_max reductions)."""
     p = cp_gn_params()
     p.eps_cg, p.cg_max_iter = float(eps_cg), int(cg_max_iter)
     p.lam, p.lam_lo, p.lam_hi, p.mu = float(lam), float(lam_lo), float(lam_hi), float(mu)
@@ -368,6 +374,7 @@ def gn_params(lam, lam_lo, lam_hi, mu=2.0, eps_cg=1e-3, cg_max_iter=250, prec="f
     p.want_residual = int(bool(want_residual))
     p.stop_stationarity = float(stop_stationarity)
     p.spin_limit = int(spin_limit)
+    p.armijo_c, p.armijo_beta, p.armijo_max = float(armijo_c), float(armijo_beta), int(armijo_max)
     return p
 
 
@@ -472,16 +479,23 @@ def _batch_array(problems, device: int):
         arr[k].X = X.data_ptr()
         arr[k].A = (ctypes.c_void_p * 3)(*[a.data_ptr() for a in A])
         arr[k].lam, arr[k].lam_lo, arr[k].lam_hi, arr[k].mu = q["lam"], q["lam_lo"], q["lam_hi"], q.get("mu", 2.0)
+        arr[k].reg = REG[q.get("reg", "identity")]
+        arr[k].lam_fixed = int(bool(q.get("lam_fixed", False)))
+        arr[k].armijo_c = float(q.get("armijo_c", 0.0))
+        arr[k].armijo_beta = float(q.get("armijo_beta", 0.5))
+        arr[k].armijo_max = int(q.get("armijo_max", 10))
     return arr
 
 
-_BATCH_KEYS = ("status", "iters", "cg_iters_total", "converged", "cg_breakdowns", "rel_residual", "lam")
+_BATCH_KEYS = ("status", "iters", "cg_iters_total", "converged", "cg_breakdowns", "rel_residual", "lam",
+               "ls_backtracks")
 
 
 def cp_gn_solve_batched(h: Handle, problems, eps_cg=1e-3, cg_max_iter=250, max_iters=200, target_residual=1e-6):
     """Solve many small order-3 problems in one persistent launch.  problems: list of
     dicts with X (float32 CUDA, 3-D), A (three float64 CUDA (s_n, R) tensors, updated in
-    place), lam, lam_lo, lam_hi, mu.  Returns a list of result dicts."""
+    place), lam, lam_lo, lam_hi, mu, and optionally reg ("identity" / "diag"),
+    lam_fixed, armijo_c, armijo_beta, armijo_max.  Returns a list of result dicts."""
     n = len(problems)
     arr = _batch_array(problems, h.device)
     res = (cp_batch_result * max(n, 1))()
@@ -512,6 +526,13 @@ class BatchPlan:
         t = ctypes.c_int()
         _check(load().cp_batch_plan_threads(self.p, ctypes.byref(t)), "cp_batch_plan_threads")
         return t.value
+
+    @property
+    def order(self):
+        """0: problems taken in the given order, 1: largest work first."""
+        o = ctypes.c_int()
+        _check(load().cp_batch_plan_order(self.p, ctypes.byref(o)), "cp_batch_plan_order")
+        return o.value
 
     def launch(self):
         """Enqueue one solve of every problem on torch's current stream (no synchronisation)."""

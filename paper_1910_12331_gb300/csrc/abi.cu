@@ -55,8 +55,9 @@ struct cp_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch, grad_part;
-    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf;
+    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf, Atrial, stats2;
     DevStats* h_stats = nullptr;  // pinned
+    DevStats* h_stats2 = nullptr; // pinned: line-search trials
     SplitCache split;             // bf16 planes of X (tensor-core path)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
     int launches = 0;             // kernels launched by the current call
@@ -266,10 +267,11 @@ cp_status cp_destroy(cp_handle h) {
         cudaStreamSynchronize(h->stream);
         DevBuf* bufs[] = {&h->gram_part, &h->grad_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
                           &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
-                          &h->stats, &h->Y, &h->resid_planes, &h->Adf};
+                          &h->stats, &h->Y, &h->resid_planes, &h->Adf, &h->Atrial, &h->stats2};
         for (DevBuf* b : bufs)
             if (b->p) cudaFree(b->p);
         if (h->h_stats) cudaFreeHost(h->h_stats);
+        if (h->h_stats2) cudaFreeHost(h->h_stats2);
         for (auto& e : h->ev)
             if (e) cudaEventDestroy(e);
         split_cache_free(h->split);
@@ -484,12 +486,65 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
     else
         CP_TRY(gn_pcg<double>(h, s, Ac, &q));
     h->launches += 2;  // pack + persistent CG
-    // A^(n) += V^(n)
+    // Step-size control by Armijo's condition (Section 5): t in 1, beta, beta^2, ...
+    double t_step = 1.0, f0 = -1.0;
+    int trials = 0;
+    bool search = p->armijo_c > 0.0;
+    if (search) {  // only after a CG solve that succeeded
+        CP_TRY(sync_stats(h));
+        const int cs = h->h_stats->status;
+        search = (cs == CP_OK || cs == CP_WARN_CG_MAXIT) && !h->h_stats->stopped;
+    }
+    if (search) {
+        const int64_t len = (int64_t)s.roff[s.N] * s.R;
+        CP_TRY(grow(h->Atrial, (size_t)len * sizeof(double)));
+        CP_TRY(grow(h->stats2, sizeof(DevStats)));
+        if (!h->h_stats2) CUDA_TRY(cudaMallocHost((void**)&h->h_stats2, sizeof(DevStats)));
+        DevStats* d2 = (DevStats*)h->stats2.p;
+        if (p->cg_fp32)
+            launch_dot_gv<float>(len, (const double*)h->Gp.p, (const float*)h->vec.p, d2->dot_part, &d2->slope,
+                                 h->stream);
+        else
+            launch_dot_gv<double>(len, (const double*)h->Gp.p, (const double*)h->vec.p, d2->dot_part, &d2->slope,
+                                  h->stream);
+        CUDA_TRY(cudaMemsetAsync(&d2->res_num, 0, 2 * sizeof(double), h->stream));
+        launch_residual_f64(s, d->x_dtype, X, Ac, d2, h->stream);
+        h->launches += 3;
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(h->h_stats2, d2, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        f0 = 0.5 * h->h_stats2->res_num;
+        const double slope = h->h_stats2->slope;
+        // relaxed by the accuracy of the FP64 evaluation of f (2 R 2^-53 ||X||^2)
+        const double tol_f = 2.0 * s.R * 0x1p-53 * h->h_stats2->res_den;
+        double t = 1.0;
+        t_step = 0.0;
+        double* At = (double*)h->Atrial.p;
+        for (int k = 0; k <= p->armijo_max; ++k, t *= p->armijo_beta) {
+            if (p->cg_fp32)
+                launch_trial_factors<float>(s, Ac, (const float*)h->vec.p, t, At, h->stream);
+            else
+                launch_trial_factors<double>(s, Ac, (const double*)h->vec.p, t, At, h->stream);
+            CUDA_TRY(cudaMemsetAsync(&d2->res_num, 0, 2 * sizeof(double), h->stream));
+            launch_residual_f64(s, d->x_dtype, X, as_const(packed_ptrs(At, s)), d2, h->stream);
+            h->launches += 2;
+            ++trials;
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(cudaMemcpyAsync(&h->h_stats2->res_num, &d2->res_num, sizeof(double), cudaMemcpyDeviceToHost,
+                                     h->stream));
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+            if (0.5 * h->h_stats2->res_num <= f0 + p->armijo_c * t * slope + tol_f) {
+                t_step = t;
+                break;
+            }
+        }
+    }
+    // A^(n) += t V^(n)
     Ptrs<double> Am = ptrs_of(A, s.N);
     if (p->cg_fp32)
-        launch_update<float>(s, Am, (const float*)h->vec.p, ds, h->stream);
+        launch_update<float>(s, Am, (const float*)h->vec.p, ds, h->stream, t_step);
     else
-        launch_update<double>(s, Am, (const double*)h->vec.p, ds, h->stream);
+        launch_update<double>(s, Am, (const double*)h->vec.p, ds, h->stream, t_step);
     h->launches += 1;
     if (p->want_residual) {
         launch_residual_f64(s, d->x_dtype, X, as_const(Am), ds, h->stream);
@@ -525,6 +580,9 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
         st->step_ms = t03;
         st->kernel_launches = h->launches;
         st->cg_blocks = h->cg_blocks;
+        st->step = t_step;
+        st->f_entry = f0;
+        st->ls_trials = trials;
     }
     if ((status == CP_OK || status == CP_WARN_CG_MAXIT) && !hs.stopped) lambda_advance(p);
     return status;
@@ -537,6 +595,8 @@ static cp_status check_params(const cp_gn_params* p) {
     if (p->reg != CP_REG_IDENTITY && p->reg != CP_REG_DIAG) return CP_ERR_ARG;
     if (!p->lam_fixed && !(p->mu > 1.0 && p->lam_lo > 0.0 && p->lam_hi >= p->lam_lo)) return CP_ERR_ARG;
     if (p->prec != CP_PREC_FP64 && p->prec != CP_PREC_BF16X3 && p->prec != CP_PREC_RESIDUAL) return CP_ERR_ARG;
+    if (!(p->armijo_c >= 0.0 && p->armijo_c < 1.0)) return CP_ERR_ARG;
+    if (p->armijo_c > 0.0 && (!(p->armijo_beta > 0.0 && p->armijo_beta < 1.0) || p->armijo_max < 0)) return CP_ERR_ARG;
     return CP_OK;
 }
 
@@ -715,6 +775,12 @@ cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result
 cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads) {
     if (!plan || !threads) return CP_ERR_ARG;
     *threads = batch_plan_threads(plan->p);
+    return CP_OK;
+}
+
+cp_status cp_batch_plan_order(cp_batch_plan plan, int* order) {
+    if (!plan || !order) return CP_ERR_ARG;
+    *order = batch_plan_order(plan->p);
     return CP_OK;
 }
 

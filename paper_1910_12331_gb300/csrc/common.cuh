@@ -39,6 +39,8 @@ struct DevStats {
     double eres_num;        // sum (x - x~)^2 at the entry point (residual gradient)
     double eres_den;
     double cg_rnorm;        // final sum_n ||R^(n)||_F
+    double slope;           // <G, V> (Armijo line search)
+    double dot_part[64];    // its block partials
     int cg_iters;
     int status;             // cp_status raised on the device
     int stopped;            // stationarity test held: no CG iteration, V = 0

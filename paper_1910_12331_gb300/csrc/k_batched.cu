@@ -39,10 +39,13 @@ struct BProb {
     const float* X;
     double* A[3];
     double lam, lam_lo, lam_hi, mu;
+    int reg, lam_fixed;        // damping lam diag(J^T J) (1) or lam I (0); constant lambda
+    double armijo_c, armijo_beta;
+    int armijo_max, pad;
 };
 
 struct BRes {
-    int status, iters, cg_iters, converged, breakdowns, pad;
+    int status, iters, cg_iters, converged, breakdowns, backtracks;
     double rel_residual, lam;
 };
 
@@ -51,6 +54,7 @@ struct BArgs {
     BRes* res;
     int nprob;
     int* counter;
+    const int* order;  // the order in which the CTAs take the problems
     double eps_cg;
     int cg_max;
     int max_iters;
@@ -244,10 +248,10 @@ __device__ __forceinline__ void apply_pinv(const Smem& m, const float* in, float
     __syncthreads();
 }
 
-// Q = (J^T J + lam I) W via Y^(p) = A^(p)^T W^(p), T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p),
-// Q^(n) = lam W^(n) + W^(n) Gamma^(n,n) + A^(n) T^(n)^T.
+// Q = (J^T J + lam D) W via Y^(p) = A^(p)^T W^(p), T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p),
+// Q^(n) = lam W^(n) D^(n) + W^(n) Gamma^(n,n) + A^(n) T^(n)^T, D^(n) = I or diag(Gamma^(n,n)).
 template <int BT>
-__device__ __forceinline__ void matvec(const Smem& m, float lam) {
+__device__ __forceinline__ void matvec(const Smem& m, float lam, bool diag) {
     const int R = m.R, RR = R * R, SR = m.S * R;
     for (int e = threadIdx.x; e < 3 * RR; e += BT) {
         const int p = e / RR, r = (e % RR) / R, z = e % R;
@@ -273,7 +277,7 @@ __device__ __forceinline__ void matvec(const Smem& m, float lam) {
         const float* T = m.Tb + n * RR;
         const float* w = m.W + row * R;
         const float* a = m.A + row * R;
-        float acc = lam * w[z];
+        float acc = (diag ? lam * G[z * R + z] : lam) * w[z];
         for (int r = 0; r < R; ++r) {
             acc = fmaf(w[r], G[r * R + z], acc);
             acc = fmaf(a[r], T[z * R + r], acc);
@@ -283,10 +287,10 @@ __device__ __forceinline__ void matvec(const Smem& m, float lam) {
     __syncthreads();
 }
 
-// P_inv^(n) = (Gamma^(n,n) + lam I)^{-1}, Gauss-Jordan in FP64 (pivots = squared Cholesky
-// diagonals); returns false if a pivot is not positive.
+// P_inv^(n) = (Gamma^(n,n) + lam D^(n))^{-1}, D^(n) = I or diag(Gamma^(n,n)), Gauss-Jordan in
+// FP64 (pivots = squared Cholesky diagonals); returns false if a pivot is not positive.
 template <int BT>
-__device__ __forceinline__ bool precond(const Smem& m, double lam) {
+__device__ __forceinline__ bool precond(const Smem& m, double lam, bool diag) {
     const int R = m.R, RR = R * R;
     __shared__ int bad;
     __shared__ double inv_s;
@@ -295,7 +299,8 @@ __device__ __forceinline__ bool precond(const Smem& m, double lam) {
         const float* G = m.Gm + (n * 3 + n) * RR;
         double* B = m.gj;
         double* f = m.gj + RR;
-        for (int e = threadIdx.x; e < RR; e += BT) B[e] = (double)G[e] + ((e / R) == (e % R) ? lam : 0.0);
+        for (int e = threadIdx.x; e < RR; e += BT)
+            B[e] = (double)G[e] + ((e / R) == (e % R) ? lam * (diag ? (double)G[e] : 1.0) : 0.0);
         __syncthreads();
         for (int j = 0; j < R; ++j) {
             if (threadIdx.x == 0) {
@@ -331,8 +336,8 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
         __syncthreads();
         if (threadIdx.x == 0) prob_s = atomicAdd(args.counter, 1);
         __syncthreads();
-        const int pi = prob_s;
-        if (pi >= args.nprob) break;
+        if (prob_s >= args.nprob) break;
+        const int pi = args.order[prob_s];
         const BProb pb = args.probs[pi];
         Smem m;
         carve(m, smem, pb);
@@ -353,18 +358,20 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
         }
         const double nx2 = bsum<BT>((double)xs, m.red);
         double lam = pb.lam;
-        int dir = 0, status = CP_OK, it = 0, cg_total = 0, converged = 0, breakdowns = 0;
+        const bool diag = pb.reg == CP_REG_DIAG;
+        int dir = 0, status = CP_OK, it = 0, cg_total = 0, converged = 0, breakdowns = 0, backtracks = 0;
         double rel = -1.0;
         for (;; ++it) {
             __syncthreads();
             gram_gamma<BT>(m);
-            rel = sqrt(fmax(resid2<BT>(m, X), 0.0) / nx2);
+            const double r2 = fmax(resid2<BT>(m, X), 0.0);  // ||X - [[A]]||^2 at the entry point
+            rel = sqrt(r2 / nx2);
             if (rel <= args.target) {
                 converged = 1;
                 break;
             }
             if (it >= args.max_iters) break;
-            if (it > 0) {  // varying lambda (Section 3.2), thresholds inclusive
+            if (it > 0 && !pb.lam_fixed) {  // varying lambda (Section 3.2), thresholds inclusive
                 if (dir == 0) {
                     if (lam / pb.mu < pb.lam_lo) {
                         dir = 1;
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                 status = CP_ERR_NONFINITE;
                 break;
             }
-            if (!precond<BT>(m, lam)) {
+            if (!precond<BT>(m, lam, diag)) {
                 status = CP_ERR_NOT_SPD;
                 break;
             }
@@ -417,9 +424,10 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
             }
             double rz = bsum<BT>((double)rzp, m.red);
             double rnorm = gsum;
+            double arz = 0.0;  // sum_k alpha_k <R_k, Z_k> = <-G, V> (PCG from V = 0)
             int k = 0;
             for (; k < args.cg_max && rnorm > args.eps_cg * gsum; ++k) {
-                matvec<BT>(m, (float)lam);
+                matvec<BT>(m, (float)lam, diag);
                 float wqp = 0.f;
                 for (int e = threadIdx.x; e < SR; e += BT) wqp = fmaf(m.W[e], m.Q[e], wqp);
                 const double wq = bsum<BT>((double)wqp, m.red);
@@ -428,6 +436,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                     break;
                 }
                 const float alpha = (float)(rz / wq);
+                arz += (double)alpha * rz;
                 for (int e = threadIdx.x; e < SR; e += BT) {
                     m.V[e] = fmaf(alpha, m.W[e], m.V[e]);
                     m.Rv[e] = fmaf(-alpha, m.Q[e], m.Rv[e]);
@@ -454,12 +463,36 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
             }
             cg_total += k;
             if (status != CP_OK) break;
-            // A += V (FP64 master, FP32 copy)
+            // Step-size control by Armijo's condition (Section 5): the first t in 1, beta,
+            // beta^2, ... with f(A + t V) <= f(A) + c t <G, V>, f = 1/2 ||X - [[A]]||^2 (the
+            // residual of the stop test), <G, V> from the CG recurrences; none: no update.
+            double step = 1.0;
+            if (pb.armijo_c > 0.0) {
+                // relaxed by the accuracy of the FP32 evaluation of f (2 R 2^-24 ||X||^2), below
+                // which a trial cannot be told from the entry point
+                const double f0 = 0.5 * r2, slope = -arz, tol_f = 2.0 * R * 0x1p-24 * nx2;
+                double t = 1.0;
+                step = 0.0;
+                for (int kk = 0; kk <= pb.armijo_max; ++kk, t *= pb.armijo_beta) {
+                    for (int e = threadIdx.x; e < SR; e += BT) {
+                        const int row = e / R, r = e % R;
+                        const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
+                        m.A[e] = (float)(pb.A[n][(row - m.roff[n]) * R + r] + t * (double)m.V[e]);
+                    }
+                    __syncthreads();
+                    if (0.5 * fmax(resid2<BT>(m, X), 0.0) <= f0 + pb.armijo_c * t * slope + tol_f) {
+                        step = t;
+                        break;
+                    }
+                    ++backtracks;
+                }
+            }
+            // A += t V (FP64 master, FP32 copy)
             for (int e = threadIdx.x; e < SR; e += BT) {
                 const int row = e / R, r = e % R;
                 const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
                 double* a = pb.A[n] + (row - m.roff[n]) * R + r;
-                const double v = *a + (double)m.V[e];
+                const double v = *a + step * (double)m.V[e];
                 *a = v;
                 m.A[e] = (float)v;
             }
@@ -471,6 +504,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
             out.cg_iters = cg_total;
             out.converged = converged;
             out.breakdowns = breakdowns;
+            out.backtracks = backtracks;
             out.rel_residual = rel;
             out.lam = lam;
             args.res[pi] = out;
@@ -497,6 +531,8 @@ struct BatchPlan {
     BProb* dp = nullptr;
     BRes* dr = nullptr;
     int* dc = nullptr;
+    int* dorder = nullptr;  // [2][nprob]: the given order, then largest work first
+    int order = 0;          // which of the two the launches use
     std::vector<BProb> hp;
     double eps_cg = 0.0, target = 0.0;
     int cg_max = 0, max_iters = 0;
@@ -550,6 +586,9 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
         if (!q.X || !q.A[0] || !q.A[1] || !q.A[2] || q.rank < 1 || q.rank > CP_BATCH_MAX_RANK || !(q.mu > 1.0) ||
             !(q.lam >= 0.0) || !(q.lam_lo >= 0.0) || !(q.lam_hi >= q.lam_lo))
             return CP_ERR_ARG;
+        if ((q.reg != CP_REG_IDENTITY && q.reg != CP_REG_DIAG) || !(q.armijo_c >= 0.0 && q.armijo_c < 1.0) ||
+            (q.armijo_c > 0.0 && (!(q.armijo_beta > 0.0 && q.armijo_beta < 1.0) || q.armijo_max < 0)))
+            return CP_ERR_ARG;
         int S = 0;
         for (int n = 0; n < 3; ++n) {
             if (q.dims[n] < 1 || q.dims[n] > CP_BATCH_MAX_SIDE) return CP_ERR_ARG;
@@ -563,6 +602,12 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
         hp[i].lam_lo = q.lam_lo;
         hp[i].lam_hi = q.lam_hi;
         hp[i].mu = q.mu;
+        hp[i].reg = q.reg;
+        hp[i].lam_fixed = q.lam_fixed ? 1 : 0;
+        hp[i].armijo_c = q.armijo_c;
+        hp[i].armijo_beta = q.armijo_beta;
+        hp[i].armijo_max = q.armijo_max;
+        hp[i].pad = 0;
         need = std::max(need, smem_bytes(S, q.rank));
     }
     if (need > kBatchSmemMax) return CP_ERR_UNSUPPORTED;
@@ -584,31 +629,48 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
         if (pl->dp) cudaFree(pl->dp);
         if (pl->dr) cudaFree(pl->dr);
         if (pl->dc) cudaFree(pl->dc);
+        if (pl->dorder) cudaFree(pl->dorder);
         delete pl;
         return st;
     };
+    // the two problem orders: as given, and largest work s_1 s_2 s_3 R first (ties by index)
+    std::vector<int> orders(2 * (size_t)nprob);
+    for (int i = 0; i < nprob; ++i) orders[i] = orders[nprob + i] = i;
+    auto work = [&](int i) { return (double)hp[i].s[0] * hp[i].s[1] * hp[i].s[2] * hp[i].R; };
+    std::stable_sort(orders.begin() + nprob, orders.end(), [&](int a, int b) { return work(a) > work(b); });
     if (cudaMalloc(&pl->dp, sizeof(BProb) * nprob) != cudaSuccess || cudaMalloc(&pl->dr, sizeof(BRes) * nprob) != cudaSuccess ||
-        cudaMalloc(&pl->dc, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&pl->dc, sizeof(int)) != cudaSuccess || cudaMalloc(&pl->dorder, sizeof(int) * 2 * nprob) != cudaSuccess)
         return fail(CP_ERR_NOMEM);
-    if (cudaMemcpyAsync(pl->dp, hp.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    if (cudaMemcpyAsync(pl->dp, hp.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(pl->dorder, orders.data(), sizeof(int) * 2 * nprob, cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess)
         return fail(CP_ERR_CUDA);
     pl->threads = 256;
     pl->grid = grid_of(device, 256, need, nprob);
     if (autotune) {
-        // Autotuner: time each block size on a scratch copy of (at most 64 of) the
-        // problems' factors -- the caller's factors are not touched -- and keep the fastest.
+        // Autotuner: time each block size and each problem order on a scratch copy of
+        // (at most 64 of) the problems' factors -- the caller's factors are not
+        // touched -- and keep the fastest.  The sample is the first 64 problems of
+        // the largest-work order when the batch is larger (it sets the tail).
         const int nt = std::min(nprob, 64);
-        std::vector<BProb> tp(hp.begin(), hp.begin() + nt);
+        std::vector<BProb> tp(nt);
+        std::vector<int> src(nt), torders(2 * (size_t)nt);
+        for (int i = 0; i < nt; ++i) src[i] = nprob > nt ? orders[nprob + i] : i;
+        for (int i = 0; i < nt; ++i) tp[i] = hp[src[i]];
+        for (int i = 0; i < nt; ++i) torders[i] = torders[nt + i] = i;
+        std::stable_sort(torders.begin() + nt, torders.end(), [&](int a, int b) { return work(src[a]) > work(src[b]); });
         size_t words = 0;
         for (const BProb& b : tp) words += (size_t)(b.s[0] + b.s[1] + b.s[2]) * b.R;
         double* scratch = nullptr;
         BProb* dtp = nullptr;
         BRes* dtr = nullptr;
         int* dtc = nullptr;
+        int* dto = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         bool ok = cudaMalloc(&scratch, words * sizeof(double)) == cudaSuccess &&
                   cudaMalloc(&dtp, sizeof(BProb) * nt) == cudaSuccess && cudaMalloc(&dtr, sizeof(BRes) * nt) == cudaSuccess &&
-                  cudaMalloc(&dtc, sizeof(int)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+                  cudaMalloc(&dtc, sizeof(int)) == cudaSuccess && cudaMalloc(&dto, sizeof(int) * 2 * nt) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess &&
                   cudaEventCreate(&e1) == cudaSuccess;
         if (ok) {
             size_t off = 0;
@@ -618,27 +680,32 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
                     off += (size_t)b.s[n] * b.R;
                     b.A[n] = dst;
                 }
-            ok = cudaMemcpyAsync(dtp, tp.data(), sizeof(BProb) * nt, cudaMemcpyHostToDevice, stream) == cudaSuccess;
+            ok = cudaMemcpyAsync(dtp, tp.data(), sizeof(BProb) * nt, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+                 cudaMemcpyAsync(dto, torders.data(), sizeof(int) * 2 * nt, cudaMemcpyHostToDevice, stream) ==
+                     cudaSuccess;
         }
         float best = 0.f;
-        for (int v = 0; ok && v < 3; ++v) {
-            const int th = kVariants[v];
+        for (int v = 0; ok && v < 6; ++v) {
+            const int th = kVariants[v >> 1], ord = v & 1;
             const int g = grid_of(device, th, need, nt);
             if (g < 1) continue;
             for (int rep = 0; ok && rep < 2; ++rep) {  // the first run of a variant includes its module load
                 for (int i = 0; i < nt && ok; ++i)
                     for (int n = 0; n < 3; ++n)
-                        ok = ok && cudaMemcpyAsync(tp[i].A[n], hp[i].A[n], (size_t)hp[i].s[n] * hp[i].R * sizeof(double),
+                        ok = ok && cudaMemcpyAsync(tp[i].A[n], hp[src[i]].A[n],
+                                                   (size_t)tp[i].s[n] * tp[i].R * sizeof(double),
                                                    cudaMemcpyDeviceToDevice, stream) == cudaSuccess;
                 ok = ok && cudaMemsetAsync(dtc, 0, sizeof(int), stream) == cudaSuccess;
                 ok = ok && cudaEventRecord(e0, stream) == cudaSuccess;
-                launch(th, g, need, stream, BArgs{dtp, dtr, nt, dtc, eps_cg, cg_max_iter, max_iters, target_residual});
+                launch(th, g, need, stream,
+                       BArgs{dtp, dtr, nt, dtc, dto + (size_t)ord * nt, eps_cg, cg_max_iter, max_iters, target_residual});
                 ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(e1, stream) == cudaSuccess &&
                      cudaEventSynchronize(e1) == cudaSuccess;
                 float ms = 0.f;
                 if (ok && rep == 1 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best == 0.f || ms < best)) {
                     best = ms;
                     pl->threads = th;
+                    pl->order = ord;
                     pl->grid = grid_of(device, th, need, nprob);
                 }
             }
@@ -650,6 +717,7 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
         if (dtp) cudaFree(dtp);
         if (dtr) cudaFree(dtr);
         if (dtc) cudaFree(dtc);
+        if (dto) cudaFree(dto);
         if (!ok) return fail(CP_ERR_CUDA);
     }
     if (pl->grid < 1) return fail(CP_ERR_UNSUPPORTED);
@@ -664,7 +732,8 @@ cp_status batch_plan_launch(BatchPlan* pl, cudaStream_t stream) {
         return CP_ERR_CUDA;
     }
     launch(pl->threads, pl->grid, pl->smem, stream,
-           BArgs{pl->dp, pl->dr, pl->nprob, pl->dc, pl->eps_cg, pl->cg_max, pl->max_iters, pl->target});
+           BArgs{pl->dp, pl->dr, pl->nprob, pl->dc, pl->dorder + (size_t)pl->order * pl->nprob, pl->eps_cg, pl->cg_max,
+                 pl->max_iters, pl->target});
     if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
     return CP_OK;
 }
@@ -684,11 +753,13 @@ cp_status batch_plan_results(BatchPlan* pl, cudaStream_t stream, cp_batch_result
         results[i].cg_breakdowns = hr[i].breakdowns;
         results[i].rel_residual = hr[i].rel_residual;
         results[i].lam = hr[i].lam;
+        results[i].ls_backtracks = hr[i].backtracks;
     }
     return CP_OK;
 }
 
 int batch_plan_threads(const BatchPlan* pl) { return pl->threads; }
+int batch_plan_order(const BatchPlan* pl) { return pl->order; }
 
 void batch_plan_destroy(BatchPlan* pl) {
     if (!pl) return;
@@ -696,6 +767,7 @@ void batch_plan_destroy(BatchPlan* pl) {
     if (pl->dp) cudaFree(pl->dp);
     if (pl->dr) cudaFree(pl->dr);
     if (pl->dc) cudaFree(pl->dc);
+    if (pl->dorder) cudaFree(pl->dorder);
     cudaGetLastError();
     delete pl;
 }

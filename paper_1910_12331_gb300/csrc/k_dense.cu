@@ -408,14 +408,17 @@ template void launch_pack<double>(const Shape&, Ptrs<const double>, double*, cud
 template void launch_pack<float>(const Shape&, Ptrs<const double>, float*, cudaStream_t);
 
 template <typename T>
-__global__ void update_kernel(Shape s, Ptrs<double> A, const T* V, DevStats* stats) {
+__global__ void update_kernel(Shape s, Ptrs<double> A, const T* V, double t, DevStats* stats) {
     __shared__ double red[32];
+    // a step that failed on the device (non-SPD, non-finite, breakdown, timeout) leaves A unchanged
+    const int st = ldcg(&stats->status);
+    if (st != CP_OK && st != CP_WARN_CG_MAXIT) return;
     const int n = blockIdx.y;
     const int64_t len = s.dims[n] * s.R;
     double v2 = 0.0, a2 = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)V[s.roff[n] * s.R + e];
+        const double v = t * (double)V[s.roff[n] * s.R + e];
         const double a = A.p[n][e] + v;
         A.p[n][e] = a;
         v2 += v * v;
@@ -430,12 +433,58 @@ __global__ void update_kernel(Shape s, Ptrs<double> A, const T* V, DevStats* sta
 }
 
 template <typename T>
-void launch_update(const Shape& s, Ptrs<double> A, const T* V, DevStats* stats, cudaStream_t st) {
+void launch_update(const Shape& s, Ptrs<double> A, const T* V, DevStats* stats, cudaStream_t st, double t) {
     dim3 grid(32, s.N);
-    update_kernel<T><<<grid, 256, 0, st>>>(s, A, V, stats);
+    update_kernel<T><<<grid, 256, 0, st>>>(s, A, V, t, stats);
 }
-template void launch_update<double>(const Shape&, Ptrs<double>, const double*, DevStats*, cudaStream_t);
-template void launch_update<float>(const Shape&, Ptrs<double>, const float*, DevStats*, cudaStream_t);
+template void launch_update<double>(const Shape&, Ptrs<double>, const double*, DevStats*, cudaStream_t, double);
+template void launch_update<float>(const Shape&, Ptrs<double>, const float*, DevStats*, cudaStream_t, double);
+
+// ------------------------------------------------------ Armijo line search
+// Trial factors At = A + t V (packed FP64; A in the caller's per-mode pointers).
+template <typename T>
+__global__ void trial_factors_kernel(Shape s, Ptrs<const double> A, const T* V, double t, double* At) {
+    const int n = blockIdx.y;
+    const int64_t len = s.dims[n] * s.R, off = s.roff[n] * s.R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+        At[off + e] = A.p[n][e] + t * (double)V[off + e];
+}
+template <typename T>
+void launch_trial_factors(const Shape& s, Ptrs<const double> A, const T* V, double t, double* At, cudaStream_t st) {
+    trial_factors_kernel<T><<<dim3(32, s.N), 256, 0, st>>>(s, A, V, t, At);
+}
+template void launch_trial_factors<double>(const Shape&, Ptrs<const double>, const double*, double, double*,
+                                           cudaStream_t);
+template void launch_trial_factors<float>(const Shape&, Ptrs<const double>, const float*, double, double*,
+                                          cudaStream_t);
+
+// <G, V> over the packed vectors, in a fixed order: kDotBlocks block partials
+// (each a fixed stride of the vector, a fixed tree inside the block), then one
+// block sums the partials in order into *out.
+constexpr int kDotBlocks = 64;
+template <typename T>
+__global__ void dot_partial_kernel(int64_t len, const double* G, const T* V, double* part) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(G[e], (double)V[e], acc);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+__global__ void dot_finish_kernel(const double* part, int n, double* out) {
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += part[k];
+        *out = acc;
+    }
+}
+template <typename T>
+void launch_dot_gv(int64_t len, const double* G, const T* V, double* part, double* out, cudaStream_t st) {
+    dot_partial_kernel<T><<<kDotBlocks, 256, 0, st>>>(len, G, V, part);
+    dot_finish_kernel<<<1, 32, 0, st>>>(part, kDotBlocks, out);
+}
+template void launch_dot_gv<double>(int64_t, const double*, const double*, double*, double*, cudaStream_t);
+template void launch_dot_gv<float>(int64_t, const double*, const float*, double*, double*, cudaStream_t);
 
 __global__ void als_solve_kernel(int64_t rows, int R, const double* Mn, const double* P, double* An) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -37,9 +37,15 @@ size_t precond_scratch_doubles(const Shape& s);
 // Packed copy of the factors in T.
 template <typename T>
 void launch_pack(const Shape& s, Ptrs<const double> A, T* Ap, cudaStream_t st);
-// A^(n) += V^(n) (V packed in T); ||V^(n)||^2 and ||A^(n)||^2 into stats.
+// A^(n) += t V^(n) (V packed in T); ||t V^(n)||^2 and ||A^(n)||^2 into stats.
 template <typename T>
-void launch_update(const Shape& s, Ptrs<double> A, const T* V, DevStats* stats, cudaStream_t st);
+void launch_update(const Shape& s, Ptrs<double> A, const T* V, DevStats* stats, cudaStream_t st, double t = 1.0);
+// Armijo line search: trial factors At = A + t V (packed FP64), and <G, V>
+// (packed, G FP64) summed in a fixed order into *out (part: 64 doubles).
+template <typename T>
+void launch_trial_factors(const Shape& s, Ptrs<const double> A, const T* V, double t, double* At, cudaStream_t st);
+template <typename T>
+void launch_dot_gv(int64_t len, const double* G, const T* V, double* part, double* out, cudaStream_t st);
 // ALS mode update: A^(n) = M^(n) Pinv^(n) (M packed rows of mode n).
 void launch_als_solve(const Shape& s, int n, const double* Mn, const double* Pinv_n, double* An, cudaStream_t st);
 // Copy packed rows of mode n to a caller pointer set (FP64).
@@ -121,6 +127,7 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
 cp_status batch_plan_launch(BatchPlan* pl, cudaStream_t stream);
 cp_status batch_plan_results(BatchPlan* pl, cudaStream_t stream, cp_batch_result* results);
 int batch_plan_threads(const BatchPlan* pl);
+int batch_plan_order(const BatchPlan* pl);
 void batch_plan_destroy(BatchPlan* pl);
 
 }  // namespace cpgn
