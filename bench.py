@@ -337,7 +337,6 @@ def batched_timing(dev, count=512):
     ms = e0.elapsed_time(e1)
     threads, order = plan.threads, plan.order
     plan.close()
-    h.close()
     conv = sum(r["converged"] for r in res)
     # the same batch with step-size control by Armijo's condition (one-shot call, untimed beside the graph)
     b_ls = []
@@ -354,6 +353,7 @@ def batched_timing(dev, count=512):
                                 for k in sorted({r["status"] for r in res_ls})},
               "not_converged": [{"problem": i, "status": r["status"], "iters": r["iters"],
                                  "rel_residual": r["rel_residual"]} for i, r in enumerate(res_ls) if not r["converged"]]}
+    h.close()
     return {"workload": f"{count} order-3 FP32 problems, sides U{{16..96}}, ranks U{{4..24}}, N(0,1) factors, "
                         "1e-8 noise; target r <= 1e-6 or 200 GN iterations",
             "ms": ms, "problems_per_s": count / (ms / 1e3), "converged": conv,
@@ -364,6 +364,202 @@ def batched_timing(dev, count=512):
             "launches": 1, "graph": "one captured plan launch, replayed", "threads_per_cta": threads,
             "problem_order": ["given", "largest work first"][order], "autotune_s": tune_s,
             "with_armijo": armijo}
+
+
+def c1_timing(dev, seeds=range(10)):
+    """The exact 20^3 rank-5 Gaussian tensors (FP64, no noise), seeds 0..9: time
+    to r <= 1e-10 from the seeded N(0,1) start, Gauss-Newton (Algorithm 1, FP64)
+    and ALS (Section 2.2, FP64), on the GPU through the C ABI, and the FP64
+    oracle on the host cores doing the same."""
+    import torch
+
+    import oracle
+    from paper_1910_12331_gb300 import api, datagen
+
+    h = api.Handle(dev)
+    out = {"gn": [], "als": [], "oracle_gn": [], "oracle_als": []}
+    for seed in seeds:
+        p = datagen.workload("exact20", seed=seed)
+        hi, lo = lam_thresholds(p["init"])
+        X = torch.from_numpy(p["X"]).to(dev)
+        A = [torch.from_numpy(a.copy()).to(dev) for a in p["init"]]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, res = api.cp_gn_solve(h, X, A, api.gn_params(hi, lo, hi, MU, EPS_CG, CG_MAX),
+                                 api.solve_opts(max_iters=100, target_residual=1e-10))
+        out["gn"].append((time.perf_counter() - t0, res["iters"], bool(res["converged"])))
+        A = [torch.from_numpy(a.copy()).to(dev) for a in p["init"]]
+        t0 = time.perf_counter()
+        it, r = 0, 1.0
+        while it < 1000 and r > 1e-10:
+            r = api.cp_als_sweep(h, X, A, 0.0, "fp64")
+            it += 1
+        out["als"].append((time.perf_counter() - t0, it, r <= 1e-10))
+        # the oracle on the host cores (baseline)
+        Ao, lam, d = [a.copy() for a in p["init"]], hi, 0
+        t0 = time.perf_counter()
+        it, r = 0, 1.0
+        while it < 100 and r > 1e-10:
+            Ao, lam, d, _, _ = oracle.gn_step(p["X"], Ao, lam, d, lo, hi, MU, EPS_CG, CG_MAX)
+            r = oracle.residual(p["X"], Ao)
+            it += 1
+        out["oracle_gn"].append((time.perf_counter() - t0, it, r <= 1e-10))
+        Ao = [a.copy() for a in p["init"]]
+        t0 = time.perf_counter()
+        it, r = 0, 1.0
+        while it < 1000 and r > 1e-10:
+            Ao, _ = oracle.als_sweep(p["X"], Ao)
+            r = oracle.residual(p["X"], Ao)
+            it += 1
+        out["oracle_als"].append((time.perf_counter() - t0, it, r <= 1e-10))
+    h.close()
+
+    def summ(v):
+        return {"median_s": statistics.median(x[0] for x in v), "iters": [x[1] for x in v],
+                "converged": sum(x[2] for x in v)}
+
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"workload": "exact20: 20x20x20 FP64 = [[A*]], rank-5 N(0,1) factors, no noise; R=5; seeds 0..9",
+            "target": "relative residual <= 1e-10", "unit": "s (wall time per solve, median over seeds)",
+            "gn": summ(out["gn"]), "als": summ(out["als"]),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "gn": summ(out["oracle_gn"]),
+                             "als": summ(out["oracle_als"]), "sample": "the same ten solves on the host cores"}}
+
+
+def c3_timing(dev, max_gn=60, max_als=400):
+    """The order-4 120^4 FP32 workload (rank-40 U(0,1) factors, 1e-4 noise; R=40):
+    Gauss-Newton (mixed path: residual-form gradient, FP32 CG vectors) against
+    ALS (bf16x3 tensor-core MTTKRP mode by mode), both from the seeded start, to
+    the relative residual 1.00001 r(A*) (A* the generating factors, so the
+    optimum lies below it), the residual evaluated after every iteration by the
+    tensor-core reconstruction (cp_residual_tensor, sums only)."""
+    import torch
+
+    from paper_1910_12331_gb300 import api, datagen
+
+    p = datagen.workload("uniform120x4", seed=0)
+    X = torch.from_numpy(p["X"]).to(dev)
+    h = api.Handle(dev)
+
+    def resid(A):
+        _, e, x = api.cp_residual_tensor(h, X, A, sums_only=True)
+        return float(np.sqrt(e / x))
+
+    target = 1.00001 * resid([torch.from_numpy(a).to(dev) for a in p["truth"]])
+    hi, lo = lam_thresholds(p["init"])
+    runs = {}
+    for method in ("gn", "als"):
+        A = [torch.from_numpy(a.copy()).to(dev) for a in p["init"]]
+        h.bump_version(X)
+        params = api.gn_params(hi, lo, hi, MU, EPS_CG, CG_MAX, prec="residual", cg_fp32=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, r, cg = 0, 1.0, 0
+        while r > target and it < (max_gn if method == "gn" else max_als):
+            if method == "gn":
+                _, st = api.cp_gn_step(h, X, A, params)
+                cg += st["cg_iters"]
+            else:
+                api.cp_als_sweep(h, X, A, 0.0, "bf16x3", want_residual=False)
+            r = resid(A)
+            it += 1
+        torch.cuda.synchronize()
+        runs[method] = {"time_s": time.perf_counter() - t0, "iters": it, "rel_residual": r,
+                        "converged": r <= target, **({"cg_iters": cg} if method == "gn" else {})}
+    h.close()
+    return {"workload": "uniform120x4: 120x120x120x120 FP32, rank-40 U(0,1) factors, 1e-4 relative noise; R=40",
+            "target": f"relative residual <= 1.00001 r(A*) = {target:.6g}", "gn": runs["gn"], "als": runs["als"],
+            "gn_speedup_over_als": runs["als"]["time_s"] / runs["gn"]["time_s"]}
+
+
+def c3_cpu_sample():
+    """One GN iteration and one ALS sweep of the FP64 oracle on the order-4
+    workload, timed on the host cores (bounded sample; unit: s per iteration)."""
+    import oracle
+    from paper_1910_12331_gb300 import datagen
+
+    p = datagen.workload("uniform120x4", seed=0)
+    hi, lo = lam_thresholds(p["init"])
+    t0 = time.perf_counter()
+    oracle.gn_step(p["X"], [a.copy() for a in p["init"]], hi, 0, lo, hi, MU, EPS_CG, CG_MAX, 0, True)
+    t_gn = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.als_sweep(p["X"], [a.copy() for a in p["init"]])
+    t_als = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+            "unit": "s per iteration", "gn_iteration_s": t_gn, "als_sweep_s": t_als,
+            "sample": "one GN iteration (dimension-tree MTTKRP, CG to 1e-3) and one ALS sweep from the start"}
+
+
+def likelihood_study(dev, n_problems=100, starts=5):
+    """Section 5's convergence-likelihood study: for R = 3..9, n_problems exact
+    rank-R 4x4x4 tensors from U(-1,1) factors, `starts` U(-1,1) starting points
+    each; Gauss-Newton with the varying lambda run to r < 5e-5 or 500
+    iterations, all problems in one batched launch."""
+    import torch
+
+    from paper_1910_12331_gb300 import api, datagen
+
+    probs = datagen.likelihood_problems(n_problems, range(3, 10), starts, 4, "uniform11", seed=0)
+    h = api.Handle(dev)
+    Xs = {}
+    batch = []
+    for q in probs:
+        key = (q["rank"], q["problem"])
+        if key not in Xs:
+            Xs[key] = torch.from_numpy(q["X"]).to(dev)
+        hi, lo = lam_thresholds(q["init"])
+        batch.append(dict(X=Xs[key], A=[torch.from_numpy(a.copy()).to(dev) for a in q["init"]], lam=hi,
+                          lam_lo=lo, lam_hi=hi, mu=MU))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = api.cp_gn_solve_batched(h, batch, EPS_CG, CG_MAX, 500, 5e-5)
+    wall = time.perf_counter() - t0
+    h.close()
+    per_rank = {}
+    for q, r in zip(probs, res):
+        d = per_rank.setdefault(q["rank"], {})
+        d.setdefault(q["problem"], []).append(bool(r["converged"]))
+    table = {str(R): {"problems_with_a_converged_start": sum(any(v) for v in d.values()),
+                      "mean_converged_starts": float(np.mean([sum(v) for v in d.values()]))}
+             for R, d in sorted(per_rank.items())}
+    return {"workload": f"{n_problems} exact rank-R 4x4x4 tensors per R = 3..9, U(-1,1) factors, {starts} U(-1,1) "
+                        "starts each; GN with varying lambda to r < 5e-5 or 500 iterations",
+            "problems": len(probs), "wall_s": wall, "launches": 1, "per_rank": table}
+
+
+def matmul_study(dev, inits=30):
+    """Section 5's matrix-multiplication tensor: the 2x2 product tensor (4x4x4,
+    rank 7), `inits` N(0,1) starts; ALS with lambda = 0.01 for 200 sweeps, then
+    Gauss-Newton with the constant lambda = 1e-3, with and without Armijo's
+    condition, to r <= 1e-8 or 300 iterations (FP64 path)."""
+    import torch
+
+    from paper_1910_12331_gb300 import api, datagen
+
+    T = datagen.matmul_tensor(2)
+    X = torch.from_numpy(T).to(dev)
+    h = api.Handle(dev)
+    rng = np.random.default_rng(0)
+    out = {"armijo": 0, "plain": 0}
+    t0 = time.perf_counter()
+    for k in range(inits):
+        A0 = [rng.standard_normal((4, 7)) for _ in range(3)]
+        A = [torch.from_numpy(a).to(dev) for a in A0]
+        for _ in range(200):
+            api.cp_als_sweep(h, X, A, 0.01, "fp64", want_residual=False)
+        warm = [a.clone() for a in A]
+        for name, c in (("armijo", 1e-4), ("plain", 0.0)):
+            B = [a.clone() for a in warm]
+            params = api.gn_params(1e-3, 1e-3, 1e-3, MU, EPS_CG, CG_MAX, lam_fixed=True, armijo_c=c)
+            _, res = api.cp_gn_solve(h, X, B, params, api.solve_opts(max_iters=300, target_residual=1e-8),
+                                     check=False)
+            out[name] += int(res["converged"] == 1)
+    wall = time.perf_counter() - t0
+    h.close()
+    return {"workload": "2x2 matrix-multiplication tensor (4x4x4), rank 7; N(0,1) starts; 200 ALS sweeps at "
+                        "lambda = 0.01, then GN at constant lambda = 1e-3", "inits": inits,
+            "converged_gn_armijo": out["armijo"], "converged_gn_plain": out["plain"], "wall_s": wall}
 
 
 def run_kernel(which):
@@ -526,6 +722,7 @@ def main():
     # ---- CP loss autograd Function (256^3 FP32, R=32): forward + fused-MTTKRP backward vs an einsum baseline
     loss_info = cp_loss_timing(dev)
     batch_info = batched_timing(dev)
+    c3_info = c3_timing(dev)
 
     if rank != 0:
         if pg:
@@ -571,8 +768,12 @@ def main():
                  "frac": mt_flops / t_mt64 / 1e12 / fp64_peak, "us": t_mt64 * 1e6,
                  "peak_source": "measured (cp_probe_fp64_fma)"}
     cpu = None
+    c1_info = c1_timing(dev)
+    like_info = likelihood_study(dev)
+    mm_info = matmul_study(dev)
     if not args.no_cpu_baseline:
         cpu = cpu_baseline_record(p, lam_hi, lam_lo)
+        c3_info["cpu_baseline"] = c3_cpu_sample()
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -592,6 +793,10 @@ def main():
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "cp_loss": loss_info,
         "batched": batch_info,
+        "c1_exact20": c1_info,
+        "c3_order4": c3_info,
+        "convergence_likelihood": like_info,
+        "matmul_tensor": mm_info,
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": clk.summary(i0, i1),
     }

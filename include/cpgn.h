@@ -305,14 +305,14 @@ cp_status cp_residual_sums(cp_handle h, const cp_desc* desc, const void* X, cons
  * objective of Eq. (2.3) times 2, and whose MTTKRP is the residual form of the
  * gradient, G^(n) = -E_(n) P^(n)), element by element, written in FP64 to E:
  * a DEVICE buffer of prod_n s_n doubles, C-contiguous like X (caller-owned,
- * overwritten).  E is formed by the reconstruction the residual-form gradient
+ * overwritten), or NULL for the two sums below alone.  E is formed by the reconstruction the residual-form gradient
  * uses: for R <= 64 on the tensor cores by error-free bf16 slice products
  * (error below 2^-38.5 R sigma tau per element, sigma and tau the powers of
  * two at or above max_r |a^(1)_ir w_m[r]| and max_r |a^(N)_kr|, w_m the
  * Hadamard product of the middle factors' rows), else on the CUDA cores in
  * extended FP32 arithmetic.  Also returns, in host memory, *sq_err = sum E^2
  * (of E rounded to FP32) and *sq_x = ||X||_F^2 (either may be NULL).
- * Synchronises.  Errors: CP_ERR_ARG (null or aliased pointers, bad
+ * Synchronises.  Errors: CP_ERR_ARG (null X or A, E aliasing an input, bad
  * descriptor), CP_ERR_NOMEM, CP_ERR_CUDA, CP_ERR_TIMEOUT. */
 cp_status cp_residual_tensor(cp_handle h, const cp_desc* desc, const void* X, const double* const* A, double* E,
                              double* sq_err, double* sq_x);

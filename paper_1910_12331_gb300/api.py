@@ -443,20 +443,25 @@ def cp_residual_sums(h: Handle, X, A):
     return e.value, x.value
 
 
-def cp_residual_tensor(h: Handle, X, A, E=None):
+def cp_residual_tensor(h: Handle, X, A, E=None, sums_only=False):
     """E = X - [[A]] in FP64 (a CUDA tensor shaped like X) by the residual-form
-    gradient's reconstruction; returns (E, sum E^2, ||X||^2)."""
+    gradient's reconstruction; returns (E, sum E^2, ||X||^2).  sums_only: no E
+    (returned as None), the two sums alone."""
     R = _factors(X, A)
-    if E is None:
-        E = torch.empty(X.shape, dtype=torch.float64, device=X.device)
-    if not (E.is_cuda and E.dtype == torch.float64 and E.is_contiguous() and E.shape == X.shape
-            and E.device == X.device):
-        raise ValueError("E: expected a contiguous CUDA float64 tensor shaped like X")
+    if sums_only:
+        E = None
+    else:
+        if E is None:
+            E = torch.empty(X.shape, dtype=torch.float64, device=X.device)
+        if not (E.is_cuda and E.dtype == torch.float64 and E.is_contiguous() and E.shape == X.shape
+                and E.device == X.device):
+            raise ValueError("E: expected a contiguous CUDA float64 tensor shaped like X")
     h._bind_stream()
     d = h.desc(X, R)
     e, x = ctypes.c_double(), ctypes.c_double()
-    _check(load().cp_residual_tensor(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A), E.data_ptr(),
-                                     ctypes.byref(e), ctypes.byref(x)), "cp_residual_tensor")
+    _check(load().cp_residual_tensor(h.h, ctypes.byref(d), X.data_ptr(), _ptr_array(A),
+                                     E.data_ptr() if E is not None else None, ctypes.byref(e), ctypes.byref(x)),
+           "cp_residual_tensor")
     return E, e.value, x.value
 
 

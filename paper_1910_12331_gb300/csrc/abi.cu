@@ -814,10 +814,10 @@ cp_status cp_residual_sums(cp_handle h, const cp_desc* d, const void* X, const d
 
 cp_status cp_residual_tensor(cp_handle h, const cp_desc* d, const void* X, const double* const* A, double* E,
                              double* sq_err, double* sq_x) {
-    if (!h || !X || !E) return CP_ERR_ARG;
+    if (!h || !X) return CP_ERR_ARG;
     CP_TRY(check_desc(d));
     CP_TRY(check_ptrs((const void* const*)A, d->order));
-    {
+    if (E) {
         const void* out[1] = {E};
         if (aliased(out, 1, (const void* const*)A, d->order, X)) return CP_ERR_ARG;
     }

@@ -118,3 +118,22 @@ def matmul_tensor(n: int) -> np.ndarray:
             for l in range(n):
                 T[i * n + j, i * n + l, l * n + j] = 1.0
     return T
+
+
+def likelihood_problems(n_problems=100, ranks=range(3, 10), starts=5, side=4, dist="uniform11", seed=0,
+                        dtype=np.float32):
+    """The convergence-likelihood study of Section 5: for every rank R, n_problems
+    exact rank-R order-3 tensors of side `side` from factors of `dist`, each with
+    `starts` starting points drawn from the same distribution.  Returns a list of
+    dicts (X, truth, init, rank, problem, start) in the order rank, problem, start."""
+    out = []
+    for R in ranks:
+        for q in range(n_problems):
+            rng_f = _rng(seed * 1000003 + R * 1009 + q, 11)
+            truth = [draw_factor(rng_f, side, int(R), dist) for _ in range(3)]
+            X = np.ascontiguousarray(full_tensor(truth).astype(dtype))
+            for st in range(starts):
+                rng_i = _rng(seed * 1000003 + R * 1009 + q, 100 + st)
+                init = [draw_factor(rng_i, side, int(R), dist) for _ in range(3)]
+                out.append({"X": X, "truth": truth, "init": init, "rank": int(R), "problem": q, "start": st})
+    return out

@@ -128,3 +128,42 @@ def test_argument_checks(env):
         ag.cp_loss(X, [torch.zeros(3, 2, device="cuda", dtype=torch.float32)] * 3, handle=h)
     with pytest.raises(ValueError):
         ag.cp_loss(X.cpu(), [torch.zeros(3, 2, dtype=torch.float64)] * 3, handle=h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_loss256_full_size(env, orc, prec):
+    """The loss workload at its stated size: 256^3 FP32 tensor from rank-32
+    N(0,1) factors, gradients at the (non-optimal) seeded start.  The forward
+    against the oracle's residual (1e-12); the backward against the oracle's
+    FP64 dimension-tree gradient 2 (A Gamma - M) (1e-12 of ||M^(n)|| in FP64,
+    2e-5 with the bf16x3 MTTKRP) and against central differences of the FP64
+    loss along random directions (relative 1e-6: truncation h^2 |f'''| and the
+    cancellation 1e-16 |f| / h are both far below that at h = 1e-3)."""
+    torch, ag, h = env
+    from paper_1910_12331_gb300 import datagen
+
+    p = datagen.workload("loss256", seed=0)
+    X, A = p["X"], p["init"]
+    Xd = torch.from_numpy(X).cuda()
+    Ad = [torch.from_numpy(a.copy()).cuda().requires_grad_() for a in A]
+    loss = ag.cp_loss(Xd, Ad, prec=prec, handle=h)
+    X64 = X.astype(np.float64)
+    r = orc.residual(X64, A)
+    ref = r * r * float(np.sum(X64 * X64))
+    assert abs(loss.item() - ref) <= 1e-12 * ref
+    loss.backward()
+    M = orc.mttkrp(X64, A, "dt")
+    G, _ = orc.gradient(A, orc.gamma(orc.gram(A)), M)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    for a, g, m in zip(Ad, G, M):
+        assert np.linalg.norm(a.grad.cpu().numpy() - 2.0 * g) <= tol * 2.0 * np.linalg.norm(m)
+    if prec == "fp64":
+        rng = np.random.default_rng(9)
+        eps = 1e-3
+        for _ in range(2):
+            D = [rng.standard_normal(a.shape) for a in A]
+            fp = orc.residual(X64, [a + eps * d for a, d in zip(A, D)]) ** 2 * float(np.sum(X64 * X64))
+            fm = orc.residual(X64, [a - eps * d for a, d in zip(A, D)]) ** 2 * float(np.sum(X64 * X64))
+            fd = (fp - fm) / (2 * eps)
+            an = sum(float((a.grad.cpu().numpy() * d).sum()) for a, d in zip(Ad, D))
+            assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
