@@ -36,6 +36,10 @@ __device__ __forceinline__ double fmadd(double a, double b, double c) { return _
 // Up to 8 partials per lane are loaded before any is consumed, so one L2
 // round trip serves a whole gather (at most 256 blocks).
 constexpr int kGatherPerLane = 8;
+// Entries of T^(n) per thread whose loads go out together (FP32: R x R <= 8 x 512
+// in one round; FP64, twice the registers per value: four).
+template <typename T>
+constexpr int kTQ = sizeof(T) == 4 ? 8 : 4;
 
 // Error-free sum s + e = a + b (Knuth two-sum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -280,18 +284,22 @@ struct V4<double> {
     }
 };
 
-// Tile shape of the row products: FP32 uses 2 x 4 register tiles (fewer
-// shared-memory loads per FMA); FP64 is DFMA-bound, so one output per thread
-// spreads the work over all four sub-partitions of the SM.
+// Tile shapes of the row products.  FP32: 2 x 4 register tiles (fewer
+// shared-memory loads per FMA: 1 x 4 tiles, or a tile's sum split over two
+// lanes, give more threads work but measured 1.3-1.6x slower).  FP64 is
+// DFMA-bound: one output per thread spreads the work over all four
+// sub-partitions of the SM.
 template <typename T>
 struct Tile;
 template <>
 struct Tile<float> {
-    static constexpr int TR = 2, TC = 4;
+    static constexpr int TR = 2, TC = 4;   // rows_mm
+    static constexpr int YR = 2, YC = 4;   // y_tiles
 };
 template <>
 struct Tile<double> {
     static constexpr int TR = 1, TC = 1;
+    static constexpr int YR = 1, YC = 1;
 };
 
 template <typename T, int TC>
@@ -366,7 +374,7 @@ __device__ __forceinline__ void rows_mm(const T* X, const T* M1, const T* Yr, co
 // Yp row stride R.
 template <typename T>
 __device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int rows, int R, int Rp) {
-    constexpr int TR = Tile<T>::TR, TC = Tile<T>::TC;
+    constexpr int TR = Tile<T>::YR, TC = Tile<T>::YC;
     const int tc_n = Rp / TC, tr_n = (R + TR - 1) / TR;
     for (int t = threadIdx.x; t < tr_n * tc_n; t += blockDim.x) {
         const int tr = t / tc_n, tc = t - tr * tc_n;
@@ -406,7 +414,7 @@ __device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int row
 // Shared memory holds the block's Gamma^(n,p) (all p), P_inv^(n), T^(n) and
 // its rows of A, V, R, Z, W, Q, every matrix with row stride Rp (zero padded).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_mats) {
+__global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stage_mats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Shape& s = a.s;
     const int R = s.R, RR = R * R, N = s.N;
@@ -525,18 +533,18 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(PcgArgs<T> a, int stage_m
         }
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         // ---- T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed (Tt[z][r] = T[r][z]);
-        // every thread issues its loads of Y for all modes before using them
-        for (int q0 = threadIdx.x; q0 < RR; q0 += 4 * blockDim.x) {
-            T y[4][kMaxN];
+        // every thread issues its loads of Y (up to kTQ entries, the modes but n) before using them
+        for (int q0 = threadIdx.x; q0 < RR; q0 += kTQ<T> * blockDim.x) {
+            T y[kTQ<T>][kMaxN];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kTQ<T>; ++u) {
                 const int q = q0 + u * blockDim.x;
 #pragma unroll
                 for (int pp = 0; pp < kMaxN; ++pp)
                     y[u][pp] = (pp < N && pp != n && q < RR) ? ldcg(&a.Yfull[(size_t)pp * RR + q]) : (T)0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kTQ<T>; ++u) {
                 const int q = q0 + u * blockDim.x;
                 if (q >= RR) break;
                 const int r = q / R, z = q - r * R;
