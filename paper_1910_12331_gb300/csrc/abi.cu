@@ -208,7 +208,7 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
             h->launches += 2;
         }
         CP_TRY(tc_mttkrp_planes(h->split, h->resid_planes.p, s, A, M, &ds->status, h->stream));
-        h->launches += (s.R + 63) / 64 * 3;
+        h->launches += (s.R + 63) / 64 * 4;
     } else {
         return CP_ERR_ARG;
     }

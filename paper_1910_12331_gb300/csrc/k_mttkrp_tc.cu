@@ -28,17 +28,19 @@
 // of steps in (b, g, m) order (m fastest).
 //   warp 0      producer: the step's X chunk tiles (128 i x 64 k, both planes,
 //               32 KB each, stored pre-swizzled so that linear bulk copies land
-//               them) into one of two step slots; the w_m rows a few steps
-//               ahead; at each run start the group's B_Y = [hi; lo] a^(N)^T
-//               (2 x 16 KB by TMA, resident for the run).
+//               them) into one of two step slots, and the step's B_Z =
+//               split(a^(1)(block b) * w_m)^T (32 KB, built for every (b, m)
+//               by bz_prep_kernel in the same pre-swizzled form) into one of
+//               two B_Z buffers; the w_m rows a few steps ahead; at each run
+//               start the group's B_Y = [hi; lo] a^(N)^T (2 x 16 KB by TMA,
+//               resident for the run).
 //   warp 1      TMEM allocator and GEMM-Y issuer (one thread).
 //   warp 2      GEMM-Z issuer (one thread).
 //   warp 3      idle.
-//   warps 4-11  workers, two per TMEM lane quadrant: build B_Z =
-//               split(a^(1)(block b) * w_m)^T (K-major, double-buffered) one
-//               step ahead, then drain D_Y (double-buffered in TMEM) into
-//               M^(1) and c_m, and D_Z at segment end.  One code path per
-//               sub-partition keeps the hot instruction footprint small.
+//   warps 4-11  workers, two per TMEM lane quadrant: drain D_Y
+//               (double-buffered in TMEM) into M^(1) and c_m, and D_Z at
+//               segment end.  One code path per sub-partition keeps the hot
+//               instruction footprint small.
 // Partials go to workspace in FP32 and a finalize kernel reduces them in a
 // fixed order into the FP64 outputs (no atomics, deterministic).
 // Every mbarrier wait is bounded: on expiry the CTA records CP_ERR_TIMEOUT,
@@ -63,7 +65,6 @@ constexpr int kWQ = 2;                   // worker warps per TMEM lane quadrant
 constexpr int kWork = 128 * kWQ;         // worker threads
 constexpr int kThreads = 128 + kWork;    // four role warps + the workers
 constexpr int kWCols = 64 / kWQ;         // rank columns of D_Y / D_Z per worker warp
-constexpr int kBRanks = 64 / (kWork / 64);  // B_Z rank columns per builder thread
 constexpr int kStages = 4;               // X chunk tiles in flight
 constexpr int kBI = 128;                 // rows of an i-block (M of GEMM-Y, K of GEMM-Z)
 constexpr int kKC = 64;                  // columns of a chunk
@@ -93,6 +94,7 @@ struct Params {
     int64_t middim[kMaxN];  // s_q of the middle modes (index q)
     const float* A1f;   // [s1][64] rows of A^(1) (rank tile), FP32, zero padded
     const float* W;     // [mid][64] w_m (rank tile), FP32, zero padded
+    const unsigned char* BZ;  // [nib][mid] B_Z tiles of the rank tile (kBZBytes each, pre-swizzled)
     float* P_Y1;        // [slot][128 i][64 r]        M^(1) partial of a run (when seg[slot].y)
     float* P_Z;         // [slot][2 chunks][64 r][64 k]  M^(N) partial of a segment
     float* P_c;         // [nib][ngr][mid][64]        c_m partial of a step
@@ -195,7 +197,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t s_stage0 = sbase;
     const uint32_t s_by = sbase + kStages * kTile;
     const uint32_t s_bz0 = s_by + kBYBytes;
-    unsigned char* bz_gen0 = base + kStages * kTile + kBYBytes;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Rows of the last i-block beyond its tile's rows are never copied in; they
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&C.drain[s]), 1);
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&C.bz_full[s]), kWork);
+            mbar_init(smem_u32(&C.bz_full[s]), 1);
             mbar_init(smem_u32(&C.bz_empty[s]), 1);
             mbar_init(smem_u32(&C.dy_full[s]), 1);
             mbar_init(smem_u32(&C.dy_empty[s]), kWork);
@@ -283,11 +284,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     bulk_load(dst, src, pbytes, fb);
                     bulk_load(dst + kXPlane, src + pbytes, pbytes, fb);
                 }
+                // the step's B_Z, once the GEMM-Z MMAs two steps back have released its buffer
+                if (!(ok = mbar_wait(smem_u32(&C.bz_empty[slot]), (uint32_t)(((it >> 1) & 1) ^ 1), abort_s,
+                                     p.status)))
+                    break;
+                const uint32_t fz = smem_u32(&C.bz_full[slot]);
+                mbar_expect_tx(fz, kBZBytes);
+                bulk_load(s_bz0 + slot * kBZBytes, p.BZ + ((size_t)sp.b * p.mid + sp.m) * kBZBytes, kBZBytes, fz);
                 ++it;
             }
             // every issued copy must have landed before the CTA may exit
-            for (int64_t k = (it > 2 ? it - 2 : 0); k < it; ++k)
+            for (int64_t k = (it > 2 ? it - 2 : 0); k < it; ++k) {
                 mbar_drain(smem_u32(&C.full[k & 1]), (uint32_t)((k >> 1) & 1), p.status);
+                mbar_drain(smem_u32(&C.bz_full[k & 1]), (uint32_t)((k >> 1) & 1), p.status);
+            }
             for (int64_t k = (wl > kWRing ? wl - kWRing : 0); k < wl; ++k)
                 mbar_drain(smem_u32(&C.w_full[k % kWRing]), (uint32_t)((k / kWRing) & 1), p.status);
             if (yg >= 0) mbar_drain(smem_u32(&C.by_full), (uint32_t)(yg & 1), p.status);
@@ -389,17 +399,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp >= 4) {
         // ------------------------------------------------------------ workers
-        // Warps 4-11, two per TMEM lane quadrant.  Step t of the loop first
-        // builds B_Z of step t + 1, then drains D_Y of step t:
-        //   B_Z build: thread = rows i0, i0 + 1 of the i-block and 16 rank
-        //   columns; B_Z row 2r holds the hi part of column r, row 2r + 1 the lo part.
-        //   D_Y drain: thread = TMEM lane (row i) and 32 rank columns (warp half).
+        // Warps 4-11, two per TMEM lane quadrant.  Step t of the loop drains
+        // D_Y of step t: thread = TMEM lane (row i) and 32 rank columns (warp half).
         const int wk = warp - 4;
         const int q = warp & 3;                  // TMEM lane quadrant of this warp
         const int cb = kWCols * (wk >> 2);       // first rank column of this warp's D_Y / D_Z share
         const int row = q * 32 + lane;           // lane of D_Y (row i) and of D_Z (row rho)
         const int et = wk * 32 + lane;           // 0 .. kWork - 1
-        const int i0 = 2 * (et & 63), rq = kBRanks * (et >> 6);  // B_Z rows and first rank column
         auto grp_wait = [&](uint32_t bar, uint32_t parity) -> bool {
             mbar_wait(bar, parity, abort_s, p.status);
             named_sync(2, kWork);
@@ -407,59 +413,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             named_sync(2, kWork);
             return C.dec[1] == 0;
         };
-        // byte address of B_Z element (row, i0) in buffer 0 is rowbase[row & 7] + (row - 2 rq) * 128
-        unsigned char* rowbase[8];
-        {
-            const int ii = i0 & 63;
-            unsigned char* sub = bz_gen0 + (i0 >> 6) * kOpSub + 2 * rq * 128;
-#pragma unroll
-            for (int x = 0; x < 8; ++x) rowbase[x] = sub + ((((ii >> 3) ^ x) & 7) << 4) + (ii & 7) * 2;
-        }
-        float b0[kBRanks], b1[kBRanks];  // A^(1) rows i0, i0 + 1 (columns rq ..) of the block being built
         float a1r[kWCols], m1acc[kWCols];  // A^(1) row `row` (columns cb ..) and the M^(1) partial
-        int bb = -1, pb = -1;
-        // B_Z of step `st` (relative index tb) into buffer tb & 1
-        auto build = [&](const StepId& st, int64_t tb) -> bool {
-            if (st.b != bb) {
-                bb = st.b;
-                const int64_t g0 = (int64_t)st.b * kBI + i0;
-#pragma unroll
-                for (int r = 0; r < kBRanks; ++r) {
-                    b0[r] = g0 < p.s1 ? p.A1f[g0 * kRT + rq + r] : 0.0f;
-                    b1[r] = g0 + 1 < p.s1 ? p.A1f[(g0 + 1) * kRT + rq + r] : 0.0f;
-                }
-            }
-            const int db = (int)(tb & 1), ws = (int)(tb % kWRing);
-            if (!grp_wait(smem_u32(&C.bz_empty[db]), (uint32_t)(((tb >> 1) & 1) ^ 1))) return false;
-            if (!grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tb / kWRing) & 1))) return false;
-            const uint32_t boff = db * kBZBytes;
-            const float4* wv = reinterpret_cast<const float4*>(&C.wring[ws][rq]);
-#pragma unroll
-            for (int r4 = 0; r4 < kBRanks; r4 += 4) {
-                const float4 w4 = wv[r4 >> 2];
-                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int r = r4 + u;
-                    const float p0 = b0[r] * w[u], p1 = b1[r] * w[u];
-                    const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
-                    const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - __low2float(hi), p1 - __high2float(hi));
-                    *reinterpret_cast<__nv_bfloat162*>(rowbase[(2 * r) & 7] + boff + (2 * r) * 128) = hi;
-                    *reinterpret_cast<__nv_bfloat162*>(rowbase[(2 * r + 1) & 7] + boff + (2 * r + 1) * 128) = lo;
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(smem_u32(&C.bz_full[db]));
-            return true;
-        };
-        StepId sp = step_of(p, T0), nx = sp;
+        int pb = -1;
+        StepId sp = step_of(p, T0);
         SegTrack seg;
         int done = 0;
-        bool ok = T0 >= T1 || build(sp, 0);
+        bool ok = true;
         int64_t tt = 0;
         for (int64_t t = T0; t < T1 && ok; ++t, ++tt, sp.next(p)) {
-            nx.next(p);
-            if (t + 1 < T1 && !(ok = build(nx, tt + 1))) break;
             bool run_start, seg_start;
             seg.enter(t, T0, sp.m, run_start, seg_start);
             if (run_start) {
@@ -474,6 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int db = (int)(tt & 1);
             const int ws = (int)(tt % kWRing);
+            if (!(ok = grp_wait(smem_u32(&C.w_full[ws]), (uint32_t)((tt / kWRing) & 1)))) break;
             if (!(ok = grp_wait(smem_u32(&C.dy_full[db]), (uint32_t)((tt >> 1) & 1)))) break;
             tc_fence_after();
             const uint32_t ta = t_dy0 + db * 128 + cb + ((uint32_t)(q * 32) << 16);
@@ -652,13 +614,52 @@ __global__ void prep_kernel(Shape s, Ptrs<const double> A, int r0, int64_t pitch
     }
 }
 
+// B_Z of every (i-block b, slice m) of the rank tile: rows 2r and 2r + 1 hold
+// the bf16 hi and lo parts of a^(1)_{ir} w_m[r] (FP32 product) for the 128 rows i
+// of the block (K = i, two 64-column sub-tiles), in the 128-byte-swizzled
+// K-major byte image the GEMM-Z MMAs read; rows i >= s_1 are zero.  A block
+// stages the rows of A^(1) of its i-block transposed in shared memory
+// (coalesced loads once) and writes the tiles of kBzSlices consecutive slices
+// m; thread = one column pair (i, i + 1) of 16 ranks (4-byte stores that
+// cover whole 128-byte rows per warp).
+constexpr int kBzSlices = 4;
+__global__ void __launch_bounds__(256) bz_prep_kernel(const float* __restrict__ A1f, const float* __restrict__ W,
+                                                      int64_t s1, int64_t mid, int nib, unsigned char* __restrict__ BZ) {
+    __shared__ __align__(16) float a1t[kRT][kBI];  // a1t[r][i] = a^(1)_{b*128+i, r}
+    const int et = threadIdx.x;
+    const int64_t mchunks = (mid + kBzSlices - 1) / kBzSlices;
+    const int64_t b = blockIdx.x / mchunks, mc = blockIdx.x - b * mchunks;
+    for (int e = et; e < kBI * kRT; e += 256) {
+        const int i = e / kRT, r = e - i * kRT;
+        const int64_t gi = b * kBI + i;
+        a1t[r][i] = gi < s1 ? A1f[gi * kRT + r] : 0.0f;
+    }
+    __syncthreads();
+    const int i0 = 2 * (et & 63), rq = 16 * (et >> 6), ii = i0 & 63;
+    for (int64_t m = mc * kBzSlices; m < mid && m < (mc + 1) * kBzSlices; ++m) {
+        unsigned char* out = BZ + (b * mid + m) * kBZBytes + (i0 >> 6) * kOpSub;
+#pragma unroll 4
+        for (int r = rq; r < rq + 16; ++r) {
+            const float w = __ldg(W + m * kRT + r);
+            const float2 a = *reinterpret_cast<const float2*>(&a1t[r][i0]);
+            const float p0 = a.x * w, p1 = a.y * w;
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - __low2float(hi), p1 - __high2float(hi));
+            const int rh = 2 * r, rl = 2 * r + 1;
+            *reinterpret_cast<__nv_bfloat162*>(out + rh * 128 + ((((ii >> 3) ^ (rh & 7)) & 7) << 4) + (ii & 7) * 2) = hi;
+            *reinterpret_cast<__nv_bfloat162*>(out + rl * 128 + ((((ii >> 3) ^ (rl & 7)) & 7) << 4) + (ii & 7) * 2) = lo;
+        }
+    }
+}
+
 // Reduce the partials into the FP64 outputs in a fixed order, columns r0 .. r0+Rt-1.
 // grid.y = mode.  Mode 1: block = 8 rows i of one i-block x 32 threads (two
-// columns each).  Mode N: block = 64 columns k of one chunk x 4 ranks, one
-// output per thread.  Both list the slots of their i-block (chunk's group) in
-// increasing order, kFinList at a time (the slot records are staged in shared
-// memory by all threads, then compacted by one warp), and sum the listed
-// partials with sixteen independent loads in flight.  Middle modes: block = 8
+// columns each).  Mode N: block = 64 columns k of one chunk for one rank, four
+// threads per output, each summing an interleaved quarter of the slots, the
+// quarters then added in a fixed order.  Both list the slots of their i-block
+// (chunk's group) in increasing order, kFinList at a time (the slot records
+// are staged in shared memory by all threads, then compacted by one warp), and
+// sum the listed partials with sixteen independent loads in flight.  Middle modes: block = 8
 // rows x 32 threads, summing the per-step column sums c_m times the other
 // middle factors.
 constexpr int kFinRows = 8;
@@ -695,9 +696,13 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
     const int n = blockIdx.y;
     if (!(mode_mask & (1u << n))) return;
     if (n == N - 1) {
-        const int c = blockIdx.x >> 4, rq = blockIdx.x & 15;  // chunk, group of 4 ranks
+        // block = one rank r of one chunk c; thread = column k of the chunk and one
+        // of four interleaved quarters of the slot list; the quarters are added in
+        // a fixed order
+        __shared__ double qsum[4][kKC];
+        const int c = blockIdx.x >> 6, r = blockIdx.x & 63;
         if (c >= p.nch) return;  // uniform over the block
-        const int kk = threadIdx.x & 63, r = rq * 4 + (threadIdx.x >> 6);
+        const int kk = threadIdx.x & 63, qt = threadIdx.x >> 6;
         const int64_t k = (int64_t)c * kKC + kk;
         const int g = c / kGroup, cc = c % kGroup;
         const float* src = p.P_Z + ((int64_t)cc * kRT + r) * kKC + kk;
@@ -705,16 +710,19 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
         double acc = 0.0;
         for (int e0 = 0; e0 < nslots; e0 += kFinList) {
             const int cnt = fin_list(p, e0, min(nslots, e0 + kFinList), 1, g, list, stage);
-            for (int j = 0; j < cnt; j += 16) {
+            for (int j = qt; j < cnt; j += 4 * 16) {
                 float v[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = j + u < cnt ? src[(int64_t)list[j + u] * sstride] : 0.0f;
+                for (int u = 0; u < 16; ++u) v[u] = j + 4 * u < cnt ? src[(int64_t)list[j + 4 * u] * sstride] : 0.0f;
 #pragma unroll
                 for (int u = 0; u < 16; ++u) acc += v[u];
             }
             __syncthreads();
         }
-        if (k < p.sN && r < Rt) M.p[n][k * R + r0 + r] = acc;
+        qsum[qt][kk] = acc;
+        __syncthreads();
+        if (qt == 0 && k < p.sN && r < Rt)
+            M.p[n][k * R + r0 + r] = (qsum[0][kk] + qsum[1][kk]) + (qsum[2][kk] + qsum[3][kk]);
         return;
     }
     const int64_t sn = n == 0 ? p.s1 : p.middim[n];
@@ -805,7 +813,7 @@ int tc_launch_count(const SplitCache& c, const cp_desc* d, const Shape& s) {
     const bool hit = c.planes && c.key_ptr != nullptr && c.key_version == d->x_version && c.key_total == s.total &&
                      c.key_dtype == (int)d->x_dtype;
     const int tiles = (s.R + kRT - 1) / kRT;
-    return (hit ? 0 : 1) + tiles * 3;  // per rank tile: prep, main, finalize
+    return (hit ? 0 : 1) + tiles * 4;  // per rank tile: prep, B_Z prep, main, finalize
 }
 
 void split_cache_free(SplitCache& c) {
@@ -860,7 +868,8 @@ size_t tc_workspace_bytes(const Shape& s, int sms) {
     return al((size_t)2 * kRT * pitch * sizeof(__nv_bfloat16)) + al((size_t)s.dims[0] * kRT * sizeof(float)) +
            al((size_t)s.mid * kRT * sizeof(float)) + al(nslots * kBI * kRT * sizeof(float)) +
            al(nslots * kGroup * kRT * kKC * sizeof(float)) +
-           al((size_t)g.nib * g.ngr * s.mid * kRT * sizeof(float)) + al(nslots * sizeof(int4));
+           al((size_t)g.nib * g.ngr * s.mid * kRT * sizeof(float)) + al(nslots * sizeof(int4)) +
+           al((size_t)g.nib * s.mid * kBZBytes);
 }
 
 // bf16 planes of X, cached by pointer / size / version.
@@ -928,7 +937,9 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
     const size_t pz_b = al((size_t)nslots * kGroup * kRT * kKC * sizeof(float));
     const size_t pc_b = al((size_t)g.nib * g.ngr * mid * kRT * sizeof(float));
     const size_t sg_b = al((size_t)nslots * sizeof(int4));
-    if (ensure_buf(c.fac, c.fac_bytes, by_b + a1_b + w_b + py_b + pz_b + pc_b + sg_b) != CP_OK) return CP_ERR_NOMEM;
+    const size_t bz_b = al((size_t)g.nib * mid * kBZBytes);
+    if (ensure_buf(c.fac, c.fac_bytes, by_b + a1_b + w_b + py_b + pz_b + pc_b + sg_b + bz_b) != CP_OK)
+        return CP_ERR_NOMEM;
     unsigned char* wb = (unsigned char*)c.fac;
     __nv_bfloat16* BY = (__nv_bfloat16*)wb;
     p.A1f = (const float*)(wb += by_b);
@@ -937,6 +948,8 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
     p.P_Z = (float*)(wb += py_b);
     p.P_c = (float*)(wb += pz_b);
     p.seg = (int4*)(wb += pc_b);
+    unsigned char* BZ = (wb += sg_b);
+    p.BZ = BZ;
     p.status = status;
     // ---- tensor map of the B_Y planes (rows of s_N elements; the pitch padding reads as zero)
     CUtensorMap tmBY;
@@ -960,12 +973,14 @@ static cp_status tc_main(SplitCache& c, const void* planes, const Shape& s, Ptrs
     }
     int64_t rows = s1;
     for (int q = 1; q + 1 < N; ++q) rows = std::max<int64_t>(rows, s.dims[q]);
-    const int64_t fx = std::max<int64_t>((rows + kFinRows - 1) / kFinRows, (int64_t)g.nch * 16);
+    const int64_t fx = std::max<int64_t>((rows + kFinRows - 1) / kFinRows, (int64_t)g.nch * kRT);
     const dim3 fgrid((unsigned)fx, (unsigned)N);
     for (int r0 = 0; r0 < R; r0 += kRT) {
         const int Rt = std::min(kRT, R - r0);
         p.R = Rt;
         prep_kernel<<<dim3(sms, 3), 256, 0, st>>>(s, A, r0, pitch, BY, (float*)p.A1f, (float*)p.W);
+        bz_prep_kernel<<<(unsigned)((int64_t)g.nib * ((mid + kBzSlices - 1) / kBzSlices)), 256, 0, st>>>(
+            p.A1f, p.W, s1, mid, g.nib, BZ);
         mttkrp_tc_kernel<<<g.grid, kThreads, kDynSmem, st>>>(tmBY, p);
         if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
         finalize_kernel<<<fgrid, 256, 0, st>>>(p, M, A, R, r0, Rt, nslots, mode_mask);
