@@ -562,6 +562,42 @@ def matmul_study(dev, inits=30):
             "converged_gn_armijo": out["armijo"], "converged_gn_plain": out["plain"], "wall_s": wall}
 
 
+def large_r_mttkrp(dev, reps=3):
+    """The large-rank MTTKRP regime of Section 5 (s = R = 500, the exact-CP
+    study; s = R = 800, the parallel-performance study): all-mode bf16x3 MTTKRP
+    of U(0,1) FP32 tensors at rank R = s, where the contraction is
+    compute-bound (R flop per byte of X); useful flops 4 prod(s) R per call."""
+    import torch
+
+    from paper_1910_12331_gb300 import api
+
+    out = {}
+    h = api.Handle(dev)
+    for s_ in (500, 800):
+        g = torch.Generator(device=dev).manual_seed(s_)
+        X = torch.rand((s_, s_, s_), generator=g, device=dev, dtype=torch.float32)
+        A = [torch.rand((s_, s_), generator=g, device=dev, dtype=torch.float64) for _ in range(3)]
+        M = [torch.empty_like(a) for a in A]
+        api.cp_mttkrp_all(h, X, A, M, prec="bf16x3")  # split of X cached, workspace grown
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            api.cp_mttkrp_all(h, X, A, M, prec="bf16x3")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        flops = 4.0 * s_ ** 3 * s_
+        out[f"s=R={s_}"] = {"ms": t * 1e3, "tflops_useful": flops / t / 1e12, "rank_tiles": (s_ + 63) // 64,
+                            "x_bytes": 4 * s_ ** 3}
+        del X, A, M
+        torch.cuda.empty_cache()
+    h.close()
+    return {"workload": "U(0,1) FP32 s x s x s tensors, rank R = s; all-mode MTTKRP (bf16x3, tensor cores)",
+            **out}
+
+
 def run_kernel(which):
     """A few launches of one kernel on the workload (for ncu captures): the
     first mixed-path GN step (pcg: one persistent CP-CG launch per step), the
@@ -580,6 +616,13 @@ def run_kernel(which):
         M = [torch.empty_like(a) for a in init]
         for _ in range(3):
             api.cp_mttkrp_all(h, X, init, M, prec="bf16x3")
+    elif which == "mttkrp500":
+        g = torch.Generator(device=dev).manual_seed(500)
+        X5 = torch.rand((500, 500, 500), generator=g, device=dev, dtype=torch.float32)
+        A5 = [torch.rand((500, 500), generator=g, device=dev, dtype=torch.float64) for _ in range(3)]
+        M5 = [torch.empty_like(a) for a in A5]
+        for _ in range(2):
+            api.cp_mttkrp_all(h, X5, A5, M5, prec="bf16x3")
     elif which == "resid":
         for _ in range(3):
             api.cp_gradient(h, X, init, prec="residual")
@@ -600,7 +643,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["pcg", "mttkrp", "resid"], default=None,
+    ap.add_argument("--kernel", choices=["pcg", "mttkrp", "mttkrp500", "resid"], default=None,
                     help="profiling aid: only run a few launches of one kernel on the workload, print nothing")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -723,6 +766,7 @@ def main():
     loss_info = cp_loss_timing(dev)
     batch_info = batched_timing(dev)
     c3_info = c3_timing(dev)
+    larger_info = large_r_mttkrp(dev)
 
     if rank != 0:
         if pg:
@@ -795,6 +839,7 @@ def main():
         "batched": batch_info,
         "c1_exact20": c1_info,
         "c3_order4": c3_info,
+        "mttkrp_large_rank": larger_info,
         "convergence_likelihood": like_info,
         "matmul_tensor": mm_info,
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),

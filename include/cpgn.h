@@ -60,9 +60,17 @@ typedef enum { CP_F32 = 0, CP_F64 = 1 } cp_dtype;
  *  CP_PREC_FP64    FP64 everywhere (the plain path);
  *  CP_PREC_BF16X3  MTTKRP on tcgen05 tensor cores with each operand split into
  *                  bf16 high/low parts (hi*hi + hi*lo + lo*hi, FP32
- *                  accumulation); CG vectors and matvec in FP32; Gram, Gamma,
- *                  gradient, preconditioner, dot products, norms, alpha/beta
- *                  and the residual stay FP64. */
+ *                  accumulation); CG vectors and matvec in FP32.  Gram, Gamma
+ *                  and the gradient stay FP64; the preconditioner inverse is
+ *                  formed in double-float (relative error ~2^-44) and applied
+ *                  in FP32; the CG dot products <R,Z> and <W,Q> are summed
+ *                  error-free per thread and across each block as double-float
+ *                  pairs of FP32 (relative error ~2^-44 of the sum of the
+ *                  magnitudes of their terms), then across blocks and into
+ *                  alpha and beta in FP64; the per-mode norms of R for the CG
+ *                  stop test are FP32 sums (relative error ~2^-24 n, which
+ *                  moves the stop by at most an iteration); the residual is
+ *                  FP64. */
 /*  CP_PREC_RESIDUAL (gradient only: cp_gradient, cp_gn_step, cp_gn_solve)
  *                  G^(n) = -E_(n) P^(n) with E = X - [[A]] the residual tensor
  *                  (Eq. (2.3) in residual form), split into bf16 planes and
@@ -114,8 +122,9 @@ typedef struct {
     int reg;              /* cp_reg: damping lam I (0, default) or lam diag(J^T J) (1); other
                              values are CP_ERR_ARG */
     cp_precision prec;    /* MTTKRP arithmetic */
-    int cg_fp32;          /* 1: CG vectors and the matvec in FP32 (dot products, norms, alpha,
-                             beta stay FP64); 0: FP64 */
+    int cg_fp32;          /* 1: CG vectors and the matvec in FP32 (dot products in double-float,
+                             alpha and beta in FP64, the stop-test norms in FP32; see
+                             CP_PREC_BF16X3); 0: FP64 */
     int want_residual;    /* 1: also return the direct FP64 relative residual after the update */
     double stop_stationarity; /* > 0: if sum||G||/sum||M|| <= this at the entry point, apply no
                                  update and report stats.stopped = 1 (Algorithm 1's loop test) */

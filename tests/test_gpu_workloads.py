@@ -288,3 +288,23 @@ def test_bench_solve_end_state(env, orc):
     rel = np.sqrt(_model_diff2(ends["mixed"], ends["fp64"])) / np.linalg.norm(X64)
     print("model difference mixed vs fp64", rel)
     assert rel <= 1e-6
+
+
+def test_mttkrp_bf16x3_large_rank(env, orc):
+    """The large-rank regime (s = R = 500, Section 5's exact-CP study): eight
+    64-column rank tiles; rows of every mode against the oracle's rows of the
+    definition, at the bf16x3 tolerance."""
+    torch, api, h = env
+    rng = np.random.default_rng(500)
+    s_, R = 500, 500
+    X = rng.uniform(0.0, 1.0, (s_, s_, s_)).astype(np.float32)
+    A = [rng.uniform(0.0, 1.0, (s_, R)) for _ in range(3)]
+    Xd = torch.from_numpy(X).cuda()
+    M = [m.cpu().numpy() for m in api.cp_mttkrp_all(h, Xd, _dev(torch, A), prec="bf16x3")]
+    X64 = X.astype(np.float64)
+    for n in range(3):
+        rows = [0, 77, 250, 499]
+        ref = np.stack([orc.mttkrp_row(X64, A, n, i) for i in rows])
+        assert _relerr(M[n][rows], ref) <= TOL_BF16X3, n
+    del Xd
+    torch.cuda.empty_cache()
