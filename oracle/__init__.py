@@ -30,6 +30,11 @@ Parity status of each routine (pins live in ``tests/test_oracle_pins.py``):
                         fails at the one before, monotone objective, the full
                         step is taken near an exact decomposition, constant lambda)
   residual              pinned (numpy reconstruction, zero at exact factors)
+  unfold_gram / sym_eig / mode_product_t / hosvd
+                        pinned (numpy products and eigenvalues, eigen-equation and
+                        orthonormality, exact recovery of a tensor of low
+                        multilinear rank, the HoSVD error bounds, the split of
+                        the CP error of an expanded core)
   residual_tensor       pinned (numpy reconstruction, zero at exact factors, its
                         squared sum is the residual's numerator)
   als_sweep             pinned (monotone objective, zero mode gradient)
@@ -110,6 +115,13 @@ def _load():
             lib.orc_set_threads.restype = None
             lib.orc_residual.argtypes = [d, dp, dp]
             lib.orc_residual_tensor.argtypes = [d, dp, dp, dp]
+            lib.orc_unfold_gram.argtypes = [d, dp, ctypes.c_int, dp]
+            lib.orc_unfold_gram.restype = None
+            lib.orc_sym_eig.argtypes = [ctypes.c_int, dp, dp, dp]
+            lib.orc_sym_eig.restype = None
+            lib.orc_mode_product_t.argtypes = [ctypes.c_int, P(ctypes.c_int64), dp, ctypes.c_int, ctypes.c_int, dp,
+                                               dp]
+            lib.orc_mode_product_t.restype = None
             lib.orc_residual_tensor.restype = None
             lib.orc_residual.restype = ctypes.c_double
             lib.orc_als_sweep.argtypes = [d, dp, dp, ctypes.c_double]
@@ -304,6 +316,54 @@ def residual_tensor(X, A):
     E = np.empty(X.shape, dtype=np.float64)
     _load().orc_residual_tensor(ctypes.byref(_desc(dims, R)), _ptr(X), _ptr(_pack(A)), _ptr(E))
     return E
+
+
+def unfold_gram(X, n):
+    """S = X_(n) X_(n)^T (FP64)."""
+    X = _x64(X)
+    dims = list(X.shape)
+    S = np.empty((dims[n], dims[n]))
+    _load().orc_unfold_gram(ctypes.byref(_desc(dims, 1)), _ptr(X), int(n), _ptr(S))
+    return S
+
+
+def sym_eig(S):
+    """Cyclic Jacobi eigen-decomposition: (w decreasing, V with eigenvector columns)."""
+    s = S.shape[0]
+    A = np.ascontiguousarray(S, dtype=np.float64).copy()
+    w, V = np.empty(s), np.empty((s, s))
+    _load().orc_sym_eig(int(s), _ptr(A), _ptr(w), _ptr(V))
+    return w, V
+
+
+def mode_product_t(T, n, U):
+    """T x_n U^T (U: s_n x r)."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    dims = list(T.shape)
+    r = U.shape[1]
+    out = list(dims)
+    out[n] = r
+    Y = np.empty(out)
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    _load().orc_mode_product_t(len(dims), d, _ptr(T), int(n), int(r), _ptr(np.ascontiguousarray(U, np.float64)),
+                               _ptr(Y))
+    return Y
+
+
+def hosvd(X, ranks):
+    """Truncated higher-order SVD (Tucker compression): U_n = the eigenvectors of
+    X_(n) X_(n)^T of the ranks[n] largest eigenvalues; core = X x_1 U_1^T ... x_N U_N^T.
+    Returns (U list, core, eigenvalue lists)."""
+    X = _x64(X)
+    U, W = [], []
+    for n in range(X.ndim):
+        w, V = sym_eig(unfold_gram(X, n))
+        U.append(np.ascontiguousarray(V[:, :ranks[n]]))
+        W.append(w)
+    core = X
+    for n in range(X.ndim):
+        core = mode_product_t(core, n, U[n])
+    return U, core, W
 
 
 def als_sweep(X, A, lam=0.0):

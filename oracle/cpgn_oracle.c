@@ -754,3 +754,104 @@ int orc_als_sweep(const orc_desc* d, const double* X, double* A, double lam) {
     free(S); free(Gam); free(Pinv); free(Mrow);
     return status;
 }
+
+/* ----------------------------------------------------------------- Tucker / HoSVD */
+
+/* S = X_(n) X_(n)^T (s_n x s_n), the Gram matrix of the mode-n unfolding, by
+ * its definition: S[j][j'] = sum over all indices but the n-th of
+ * x[.., j, ..] x[.., j', ..]. */
+void orc_unfold_gram(const orc_desc* d, const double* X, int n, double* S) {
+    const int N = d->N;
+    int64_t L = 1, Rr = 1;
+    for (int m = 0; m < n; ++m) L *= d->dims[m];
+    for (int m = n + 1; m < N; ++m) Rr *= d->dims[m];
+    const int64_t sn = d->dims[n];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < sn; ++j)
+        for (int64_t jj = 0; jj < sn; ++jj) {
+            double acc = 0.0;
+            for (int64_t l = 0; l < L; ++l) {
+                const double* a = X + (l * sn + j) * Rr;
+                const double* b = X + (l * sn + jj) * Rr;
+                for (int64_t c = 0; c < Rr; ++c) acc += a[c] * b[c];
+            }
+            S[j * sn + jj] = acc;
+        }
+}
+
+/* Eigen-decomposition of a symmetric s x s matrix S by the cyclic Jacobi
+ * method (plane rotations annihilating S[p][q] in row order, sweeps until the
+ * off-diagonal mass is below 1e-30 of the total or 100 sweeps): on return
+ * w holds the eigenvalues in decreasing order and column i of V (row-major
+ * s x s) the unit eigenvector of w[i].  S is overwritten. */
+void orc_sym_eig(int s, double* S, double* w, double* V) {
+    for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) V[i * s + j] = i == j ? 1.0 : 0.0;
+    double tot = 0.0;
+    for (int i = 0; i < s * s; ++i) tot += S[i] * S[i];
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < s; ++p)
+            for (int q = p + 1; q < s; ++q) off += 2.0 * S[p * s + q] * S[p * s + q];
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < s; ++p)
+            for (int q = p + 1; q < s; ++q) {
+                const double apq = S[p * s + q];
+                if (apq == 0.0) continue;
+                const double app = S[p * s + p], aqq = S[q * s + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < s; ++k) {  /* columns p, q */
+                    const double skp = S[k * s + p], skq = S[k * s + q];
+                    S[k * s + p] = c * skp - sn * skq;
+                    S[k * s + q] = sn * skp + c * skq;
+                }
+                for (int k = 0; k < s; ++k) {  /* rows p, q */
+                    const double spk = S[p * s + k], sqk = S[q * s + k];
+                    S[p * s + k] = c * spk - sn * sqk;
+                    S[q * s + k] = sn * spk + c * sqk;
+                }
+                for (int k = 0; k < s; ++k) {
+                    const double vkp = V[k * s + p], vkq = V[k * s + q];
+                    V[k * s + p] = c * vkp - sn * vkq;
+                    V[k * s + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < s; ++i) w[i] = S[i * s + i];
+    /* decreasing order (selection sort, columns of V moved along) */
+    for (int i = 0; i < s; ++i) {
+        int b = i;
+        for (int j = i + 1; j < s; ++j)
+            if (w[j] > w[b]) b = j;
+        if (b != i) {
+            const double t = w[i];
+            w[i] = w[b];
+            w[b] = t;
+            for (int k = 0; k < s; ++k) {
+                const double x = V[k * s + i];
+                V[k * s + i] = V[k * s + b];
+                V[k * s + b] = x;
+            }
+        }
+    }
+}
+
+/* Y = T x_n U^T: the mode-n product of a dense tensor T (dims `dims`, order N)
+ * with U^T, U an s_n x r matrix (row-major): Y has r in place of s_n,
+ * Y[.., a, ..] = sum_j U[j][a] T[.., j, ..]. */
+void orc_mode_product_t(int N, const int64_t* dims, const double* T, int n, int r, const double* U, double* Y) {
+    int64_t L = 1, Rr = 1;
+    for (int m = 0; m < n; ++m) L *= dims[m];
+    for (int m = n + 1; m < N; ++m) Rr *= dims[m];
+    const int64_t sn = dims[n];
+#pragma omp parallel for schedule(static)
+    for (int64_t l = 0; l < L; ++l)
+        for (int a = 0; a < r; ++a)
+            for (int64_t c = 0; c < Rr; ++c) {
+                double acc = 0.0;
+                for (int64_t j = 0; j < sn; ++j) acc += U[j * r + a] * T[(l * sn + j) * Rr + c];
+                Y[(l * r + a) * Rr + c] = acc;
+            }
+}

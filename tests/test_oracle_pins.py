@@ -671,3 +671,86 @@ def test_armijo_off_is_the_plain_step(orc):
     assert st1 == st2 and l1 == l2 and d1 == d2 and s2["step"] == 1.0
     for a, b in zip(A1, A2):
         assert np.array_equal(a, b)
+
+
+# ------------------------------------------------ Tucker / HoSVD (compression ahead of CP, for R < s)
+
+def _tucker_tensor(dims, ranks, seed, noise=0.0):
+    """X = G x_1 Q_1 ... x_N Q_N with orthonormal Q_n (s_n x r_n) and a random core:
+    a tensor of exact multilinear rank `ranks` (plus optional noise)."""
+    rng = np.random.default_rng(seed)
+    Q = [np.linalg.qr(rng.standard_normal((s, r)))[0] for s, r in zip(dims, ranks)]
+    X = rng.standard_normal(ranks)
+    for n, q in enumerate(Q):
+        X = np.moveaxis(np.tensordot(q, X, axes=(1, n)), 0, n)
+    if noise:
+        X = X + noise * rng.standard_normal(dims)
+    return X, Q
+
+
+def test_unfold_gram_and_jacobi_eigen(orc):
+    rng = np.random.default_rng(80)
+    X = rng.standard_normal((5, 6, 7, 4))
+    for n in range(4):
+        Xn = np.moveaxis(X, n, 0).reshape(X.shape[n], -1)
+        S = orc.unfold_gram(X, n)
+        np.testing.assert_allclose(S, Xn @ Xn.T, rtol=0, atol=1e-12 * np.abs(S).max())
+        w, V = orc.sym_eig(S)
+        np.testing.assert_allclose(w, np.sort(np.linalg.eigvalsh(S))[::-1], rtol=0, atol=1e-12 * w[0])
+        np.testing.assert_allclose(V.T @ V, np.eye(len(w)), atol=1e-13)
+        np.testing.assert_allclose(S @ V, V * w, atol=1e-12 * w[0])
+
+
+def test_mode_product_definition(orc):
+    rng = np.random.default_rng(81)
+    T = rng.standard_normal((4, 5, 6))
+    U = rng.standard_normal((5, 3))
+    np.testing.assert_allclose(orc.mode_product_t(T, 1, U), np.einsum("ijk,ja->iak", T, U), atol=1e-13)
+
+
+def test_hosvd_exact_multilinear_rank(orc):
+    """A tensor of multilinear rank (3, 4, 2) is reproduced exactly by its
+    truncated HoSVD, and the U_n span the generating subspaces."""
+    X, Q = _tucker_tensor((9, 8, 7), (3, 4, 2), 82)
+    U, core, _ = orc.hosvd(X, (3, 4, 2))
+    Xh = core
+    for n, u in enumerate(U):
+        Xh = orc.mode_product_t(Xh, n, u.T)  # x_n U_n
+    np.testing.assert_allclose(Xh, X, atol=1e-12 * np.abs(X).max())
+    for u, q in zip(U, Q):
+        np.testing.assert_allclose(u @ u.T, q @ q.T, atol=1e-12)
+
+
+def test_hosvd_error_bounds(orc):
+    """De Lathauwer, De Moor and Vandewalle (2000): the truncated HoSVD error
+    satisfies max_n sum_{i > r_n} lambda_i^(n) <= ||X - X^||^2 <=
+    sum_n sum_{i > r_n} lambda_i^(n), lambda^(n) the eigenvalues of X_(n) X_(n)^T."""
+    X, _ = _tucker_tensor((8, 9, 10), (3, 3, 4), 83, noise=0.05)
+    ranks = (3, 3, 4)
+    U, core, W = orc.hosvd(X, ranks)
+    Xh = core
+    for n, u in enumerate(U):
+        Xh = orc.mode_product_t(Xh, n, u.T)
+    err = float(np.sum((X - Xh) ** 2))
+    tails = [float(np.sum(w[r:])) for w, r in zip(W, ranks)]
+    assert max(tails) * (1 - 1e-10) <= err <= sum(tails) * (1 + 1e-10)
+
+
+def test_cp_of_the_core_splits_the_error(orc):
+    """With orthonormal U_n, a CP model B of the core expanded to A_n = U_n B_n
+    has ||X - [[A]]||^2 = ||X - X^||^2 + ||core - [[B]]||^2 (Pythagoras in the
+    subspace), which is what makes CP on the compressed core exact."""
+    from tests import cpref
+
+    X, _ = _tucker_tensor((9, 8, 7), (4, 4, 3), 84, noise=0.1)
+    ranks = (4, 4, 3)
+    U, core, _ = orc.hosvd(X, ranks)
+    Xh = core
+    for n, u in enumerate(U):
+        Xh = orc.mode_product_t(Xh, n, u.T)
+    rng = np.random.default_rng(85)
+    B = [rng.standard_normal((r, 3)) for r in ranks]
+    A = [u @ b for u, b in zip(U, B)]
+    lhs = 2 * cpref.objective(X, A)
+    rhs = float(np.sum((X - Xh) ** 2)) + 2 * cpref.objective(core, B)
+    assert abs(lhs - rhs) <= 1e-12 * lhs
