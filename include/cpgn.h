@@ -327,6 +327,34 @@ cp_status cp_residual_tensor(cp_handle h, const cp_desc* desc, const void* X, co
                              double* sq_err, double* sq_x);
 
 /* ---------------------------------------------------------------------------
+ * Tucker compression ahead of CP for ranks below the sides (Section 1; the
+ * complexity comparison of Section 3.5 assumes it).
+ *
+ * cp_hosvd: the truncated higher-order SVD of X with multilinear ranks
+ * ranks[n] (1 <= ranks[n] <= s_n; desc->rank is not used but must be valid):
+ * U[n] (host array of N DEVICE pointers, each s_n x ranks[n] row-major FP64,
+ * overwritten) receives an orthonormal basis of the dominant ranks[n]-
+ * dimensional eigenspace of X_(n) X_(n)^T (Gram matrix formed in FP64,
+ * orthogonal iteration with Cholesky QR until ||S V - V V^T S V||_F <= 1e-12
+ * ||S V||_F, at most 300 steps), and core (DEVICE, prod_n ranks[n] doubles,
+ * C-contiguous, overwritten) the projection X x_1 U_1^T ... x_N U_N^T in FP64.
+ * The basis is unique up to a rotation within the subspace (compare U U^T).
+ * iters (host, N ints, may be NULL) receives the iteration counts.  CP of the
+ * core with cp_gn_solve and cp_tucker_expand then give a CP model of X whose
+ * squared error is the compression error plus the core's CP error.
+ * Synchronises once per iteration step.  Errors: CP_ERR_ARG, CP_ERR_NOMEM,
+ * CP_ERR_CUDA, CP_ERR_NOT_SPD (ranks[n] above the rank of X_(n)).
+ *
+ * cp_tucker_expand: A[n] = U[n] B[n] for n < order (U[n] dims[n] x ranks[n],
+ * B[n] ranks[n] x R, A[n] dims[n] x R; host arrays of DEVICE pointers,
+ * row-major FP64; A overwritten, not aliasing U or B).  Asynchronous.
+ * Errors: CP_ERR_ARG, CP_ERR_CUDA. */
+cp_status cp_hosvd(cp_handle h, const cp_desc* desc, const void* X, const int* ranks, double* const* U, double* core,
+                   int* iters);
+cp_status cp_tucker_expand(cp_handle h, int order, const int64_t* dims, const int* ranks, int R,
+                           const double* const* U, const double* const* B, double* const* A);
+
+/* ---------------------------------------------------------------------------
  * Many small independent order-3 problems (Algorithm 1 with Algorithm 2 per
  * problem) solved by one persistent kernel launch: each CTA takes problems
  * from a work counter and runs the whole Gauss-Newton iteration of one problem

@@ -29,7 +29,7 @@ REG = {"identity": CP_REG_IDENTITY, "diag": CP_REG_DIAG}
 
 SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_workspace_size",
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
-           "cp_residual", "cp_residual_sums", "cp_residual_tensor", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
+           "cp_residual", "cp_residual_sums", "cp_residual_tensor", "cp_hosvd", "cp_tucker_expand", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
            "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads", "cp_batch_plan_order",
            "cp_batch_plan_destroy", "cp_probe_grid_barrier", "cp_probe_fp64_fma")
 
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = False):
         L.cp_residual.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d)]
         L.cp_residual_sums.argtypes = [vp, pd, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.cp_residual_tensor.argtypes = [vp, pd, vp, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.cp_hosvd.argtypes = [vp, pd, vp, ctypes.POINTER(i), vp, vp, ctypes.POINTER(i)]
+        L.cp_tucker_expand.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i), i, vp, vp, vp]
         L.cp_gn_matvec_noalloc.argtypes = [pd, vp, vp, d, vp, vp]
         L.cp_gn_solve_batched.argtypes = [vp, i, ctypes.POINTER(cp_batch_problem), d, i, i, d,
                                           ctypes.POINTER(cp_batch_result)]
@@ -463,6 +465,44 @@ def cp_residual_tensor(h: Handle, X, A, E=None, sums_only=False):
                                      E.data_ptr() if E is not None else None, ctypes.byref(e), ctypes.byref(x)),
            "cp_residual_tensor")
     return E, e.value, x.value
+
+
+def cp_hosvd(h: Handle, X, ranks):
+    """Truncated HoSVD (Tucker compression): returns (U list of (s_n, r_n)
+    float64 CUDA tensors with orthonormal columns, core float64 CUDA tensor of
+    shape ranks, iteration counts)."""
+    ranks = [int(r) for r in ranks]
+    if len(ranks) != X.dim():
+        raise ValueError("one rank per mode")
+    U = [torch.empty((s, r), dtype=torch.float64, device=X.device) for s, r in zip(X.shape, ranks)]
+    core = torch.empty(ranks, dtype=torch.float64, device=X.device)
+    h._bind_stream()
+    d = h.desc(X, 1)
+    rk = (ctypes.c_int * len(ranks))(*ranks)
+    it = (ctypes.c_int * len(ranks))()
+    _check(load().cp_hosvd(h.h, ctypes.byref(d), X.data_ptr(), rk, _ptr_array(U), core.data_ptr(), it), "cp_hosvd")
+    return U, core, list(it)
+
+
+def cp_tucker_expand(h: Handle, U, B):
+    """A_n = U_n B_n (float64 CUDA tensors): the CP factors of X from the CP
+    factors B of the Tucker core."""
+    if len(U) != len(B):
+        raise ValueError("one B per U")
+    R = B[0].shape[1]
+    for n, (u, b) in enumerate(zip(U, B)):
+        _check_factor(u, u.shape[0], u.shape[1], f"U[{n}]")
+        _check_factor(b, u.shape[1], R, f"B[{n}]")
+        if u.device.index != h.device or b.device.index != h.device:
+            raise ValueError("U and B must be on the handle's device")
+    A = [torch.empty((u.shape[0], R), dtype=torch.float64, device=u.device) for u in U]
+    h._bind_stream()
+    N = len(U)
+    dims = (ctypes.c_int64 * N)(*[u.shape[0] for u in U])
+    rk = (ctypes.c_int * N)(*[u.shape[1] for u in U])
+    _check(load().cp_tucker_expand(h.h, N, dims, rk, R, _ptr_array(U), _ptr_array(B), _ptr_array(A)),
+           "cp_tucker_expand")
+    return A
 
 
 def _batch_array(problems, device: int):

@@ -55,9 +55,10 @@ struct cp_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch, grad_part;
-    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf, Atrial, stats2;
+    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf, Atrial, stats2, tucker;
     DevStats* h_stats = nullptr;  // pinned
     DevStats* h_stats2 = nullptr; // pinned: line-search trials
+    double* h_tk = nullptr;       // pinned: HoSVD convergence checks
     SplitCache split;             // bf16 planes of X (tensor-core path)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
     int launches = 0;             // kernels launched by the current call
@@ -267,11 +268,12 @@ cp_status cp_destroy(cp_handle h) {
         cudaStreamSynchronize(h->stream);
         DevBuf* bufs[] = {&h->gram_part, &h->grad_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
                           &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
-                          &h->stats, &h->Y, &h->resid_planes, &h->Adf, &h->Atrial, &h->stats2};
+                          &h->stats, &h->Y, &h->resid_planes, &h->Adf, &h->Atrial, &h->stats2, &h->tucker};
         for (DevBuf* b : bufs)
             if (b->p) cudaFree(b->p);
         if (h->h_stats) cudaFreeHost(h->h_stats);
         if (h->h_stats2) cudaFreeHost(h->h_stats2);
+        if (h->h_tk) cudaFreeHost(h->h_tk);
         for (auto& e : h->ev)
             if (e) cudaEventDestroy(e);
         split_cache_free(h->split);
@@ -809,6 +811,45 @@ cp_status cp_residual_sums(cp_handle h, const cp_desc* d, const void* X, const d
     CP_TRY(sync_stats(h));
     if (sq_err) *sq_err = h->h_stats->res_num;
     if (sq_x) *sq_x = h->h_stats->res_den;
+    return CP_OK;
+}
+
+cp_status cp_hosvd(cp_handle h, const cp_desc* d, const void* X, const int* ranks, double* const* U, double* core,
+                   int* iters) {
+    if (!h || !X || !ranks || !core) return CP_ERR_ARG;
+    CP_TRY(check_desc(d));
+    CP_TRY(check_ptrs((const void* const*)U, d->order));
+    for (int n = 0; n < d->order; ++n)
+        if (ranks[n] < 1 || ranks[n] > d->dims[n] || ranks[n] > CP_MAX_RANK) return CP_ERR_ARG;
+    if (aliased((const void* const*)U, d->order, nullptr, 0, X) || core == X) return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    const Shape s = make_shape(d);
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int64_t smax = 1;
+    for (int n = 0; n < s.N; ++n) smax = std::max<int64_t>(smax, s.dims[n]);
+    const int64_t tiles = (smax + 31) / 32;
+    const int slabs = (int)std::max<int64_t>(1, std::min<int64_t>(64, (2 * sms + tiles * (tiles + 1) / 2 - 1) /
+                                                                          (tiles * (tiles + 1) / 2)));
+    CP_TRY(grow(h->tucker, hosvd_scratch_doubles(s, ranks, slabs) * sizeof(double)));
+    if (!h->h_tk) CUDA_TRY(cudaMallocHost((void**)&h->h_tk, 4 * sizeof(double)));
+    return launch_hosvd(s, d->x_dtype, X, ranks, U, core, iters, (double*)h->tucker.p, slabs, h->h_tk, h->stream);
+}
+
+cp_status cp_tucker_expand(cp_handle h, int order, const int64_t* dims, const int* ranks, int R,
+                           const double* const* U, const double* const* B, double* const* A) {
+    if (!h || !dims || !ranks || order < 1 || order > CP_MAX_ORDER || R < 1 || R > CP_MAX_RANK) return CP_ERR_ARG;
+    CP_TRY(check_ptrs((const void* const*)U, order));
+    CP_TRY(check_ptrs((const void* const*)B, order));
+    CP_TRY(check_ptrs((const void* const*)A, order));
+    for (int n = 0; n < order; ++n)
+        if (dims[n] < 1 || ranks[n] < 1 || ranks[n] > dims[n]) return CP_ERR_ARG;
+    if (aliased((const void* const*)A, order, (const void* const*)U, order, nullptr) ||
+        aliased((const void* const*)A, order, (const void* const*)B, order, nullptr))
+        return CP_ERR_ARG;
+    DeviceGuard g(h->device);
+    for (int n = 0; n < order; ++n) launch_tucker_expand(dims[n], ranks[n], R, U[n], B[n], A[n], h->stream);
+    CUDA_TRY(cudaGetLastError());
     return CP_OK;
 }
 

@@ -113,6 +113,18 @@ size_t resid_tc_scratch_bytes(const Shape& s);
 int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
                           double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st);
 
+// ---- truncated HoSVD / Tucker compression (k_tucker.cu) -----------------------------
+// FP64 scratch (doubles) of launch_hosvd with `slabs` contraction slabs for the Grams.
+size_t hosvd_scratch_doubles(const Shape& s, const int* ranks, int slabs);
+// U[n] (s_n x r_n, orthonormal columns spanning the dominant eigenspace of
+// X_(n) X_(n)^T) and the core (prod r_n, C-contiguous); iters[n] (host, may be
+// null) = orthogonal-iteration steps; hbuf: 4 pinned host doubles.
+// Synchronises once per orthogonal-iteration step.
+cp_status launch_hosvd(const Shape& s, cp_dtype xdt, const void* X, const int* ranks, double* const* U, double* core,
+                       int* iters, double* scratch, int slabs, double* hbuf, cudaStream_t st);
+// A (s x R) = U (s x r) B (r x R), row-major FP64.
+void launch_tucker_expand(int64_t s, int r, int R, const double* U, const double* B, double* A, cudaStream_t st);
+
 // ---- residual (k_residual.cu) ------------------------------------------------------
 void launch_residual_f64(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, DevStats* stats,
                          cudaStream_t st);

@@ -109,6 +109,20 @@ def batched_problems(count=512, side_range=(16, 96), rank_range=(4, 24), noise=1
     return probs
 
 
+def tucker_tensor(dims, ranks, noise=0.0, seed=0, dtype=np.float64):
+    """X = G x_1 Q_1 ... x_N Q_N with Q_n an orthonormal basis of an s_n x r_n
+    Gaussian draw and G an N(0,1) core: a tensor of exact multilinear rank
+    `ranks`, plus relative noise eta as in `add_noise`.  Returns (X, Q list)."""
+    rng = _rng(seed, 21)
+    Q = [np.linalg.qr(rng.standard_normal((int(s), int(r))))[0] for s, r in zip(dims, ranks)]
+    X = rng.standard_normal(tuple(int(r) for r in ranks))
+    for n, q in enumerate(Q):
+        X = np.moveaxis(np.tensordot(q, X, axes=(1, n)), 0, n)
+    if noise:
+        X = add_noise(rng, X, noise)
+    return np.ascontiguousarray(X.astype(dtype)), Q
+
+
 def matmul_tensor(n: int) -> np.ndarray:
     """Order-3 unfolding of t_{ijklmn} = delta_lm delta_ik delta_nj (Section 5):
     T[(i,j), (k,l), (m,n)] with pair index a*n + b; c_ij = sum T a_kl b_mn."""
