@@ -135,7 +135,7 @@ class ClockSampler:
                "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-               "--format=csv,noheader,nounits", "-lms", "200"]
+               "--format=csv,noheader,nounits", "-lms", "100"]
         try:
             self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
@@ -598,9 +598,55 @@ def large_r_mttkrp(dev, reps=3):
             **out}
 
 
+def tucker_study(dev, direct_residual):
+    """Tucker compression ahead of CP (Section 1; Section 3.5's complexity comparison assumes it) on the
+    timed workload: the truncated HoSVD of X to its multilinear rank (R, R, R), the GN solve of the R^3
+    core (plain FP64 path, seeded N(0,1) start -- distributed as the workload's start projected on the
+    bases -- to the same stationarity target on the core), and A_n = U_n B_n; the relative residual of
+    the expanded model against the direct solve's."""
+    import torch
+
+    from paper_1910_12331_gb300 import api, datagen
+
+    p = datagen.workload(WORKLOAD, seed=0)
+    X = torch.from_numpy(p["X"]).to(dev)
+    R = p["init"][0].shape[1]
+    ranks = (R,) * X.dim()
+    rng = datagen._rng(0, 31)
+    B0 = [datagen.draw_factor(rng, R, R) for _ in ranks]
+    hi, lo = lam_thresholds(B0)
+    h = api.Handle(dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    api.cp_hosvd(h, X, ranks)  # first call: module loads and workspace growth
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev[0].record(stream)
+    U, core, hos_it = api.cp_hosvd(h, X, ranks)
+    ev[1].record(stream)
+    B = [torch.from_numpy(b).to(dev) for b in B0]
+    params = api.gn_params(hi, lo, hi, MU, EPS_CG, CG_MAX, prec="fp64")
+    _, res = api.cp_gn_solve(h, core, B, params, api.solve_opts(max_iters=MAX_GN, target_stationarity=TARGET_STAT))
+    ev[2].record(stream)
+    A = api.cp_tucker_expand(h, U, B)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    e_full, x2 = api.cp_residual_sums(h, X, A)
+    g2 = float(torch.sum(core * core))
+    h.close()
+    return {"workload": f"{WORKLOAD}, compressed to its multilinear rank {ranks}",
+            "hosvd_ms": ev[0].elapsed_time(ev[1]), "hosvd_iterations": hos_it,
+            "core_solve_ms": ev[1].elapsed_time(ev[2]), "core_gn_iters": res["iters"],
+            "core_cg_iters": res["cg_iters_total"], "core_converged": bool(res["converged"]),
+            "expand_ms": ev[2].elapsed_time(ev[3]), "wall_s": wall,
+            "compression_rel_error": float(np.sqrt(max(x2 - g2, 0.0) / x2)),
+            "rel_residual_compressed": float(np.sqrt(e_full / x2)), "rel_residual_direct": direct_residual}
+
+
 def run_kernel(which):
     """A few launches of one kernel on the workload (for ncu captures): the
-    first mixed-path GN step (pcg: one persistent CP-CG launch per step), the
+    first twelve mixed-path GN steps (pcg: one persistent CP-CG launch per step), the
     bf16x3 all-mode MTTKRP (mttkrp), or the residual-form gradient (resid:
     tensor-core reconstruction of E, then the MTTKRP of E)."""
     import torch
@@ -629,9 +675,10 @@ def run_kernel(which):
     else:
         lam_hi, lam_lo = lam_thresholds(p["init"])
         params = api.gn_params(lam_hi, lam_lo, lam_hi, MU, EPS_CG, CG_MAX, **MIXED)
-        for _ in range(3):
-            _, st = api.cp_gn_step(h, X, [a.clone() for a in init], params, check=False)
-        print("pcg launch: %d CG iterations" % st["cg_iters"], flush=True)
+        A = [a.clone() for a in init]
+        for k in range(12):  # twelve GN steps of the solve: launches 11-12 run tens of CG iterations
+            _, st = api.cp_gn_step(h, X, A, params, check=False)
+            print("pcg launch %d: %d CG iterations" % (k + 1, st["cg_iters"]), flush=True)
     torch.cuda.synchronize()
     h.close()
 
@@ -767,6 +814,7 @@ def main():
     batch_info = batched_timing(dev)
     c3_info = c3_timing(dev)
     larger_info = large_r_mttkrp(dev)
+    tucker_info = tucker_study(dev, last["rel_residual"])
 
     if rank != 0:
         if pg:
@@ -842,6 +890,7 @@ def main():
         "mttkrp_large_rank": larger_info,
         "convergence_likelihood": like_info,
         "matmul_tensor": mm_info,
+        "tucker_compressed": tucker_info,
         "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
         "clocks": clk.summary(i0, i1),
     }
