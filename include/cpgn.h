@@ -240,10 +240,13 @@ cp_status cp_gn_matvec(cp_handle h, const cp_desc* desc, const double* const* A,
  * status: CP_OK, CP_WARN_CG_MAXIT (update applied), or an error (A unchanged
  * for CP_ERR_NOT_SPD, CP_ERR_NONFINITE, CP_ERR_UNSUPPORTED; unspecified for
  * CP_ERR_BREAKDOWN, CP_ERR_TIMEOUT).
- * Rank limit: the CG kernel keeps N + 2 R x R matrices (its mode's row of
- * Gamma, P_inv^(n), T^(n)) in shared memory, so R <= 69 at N = 3 and R <= 64
- * at N = 4 with FP64 CG vectors, R <= 100 and R <= 91 with FP32 ones
- * (cg_fp32 = 1); a larger R gives CP_ERR_UNSUPPORTED. */
+ * Ranks: the CG kernel keeps N + 2 R x R matrices (its mode's row of Gamma,
+ * P_inv^(n), T^(n)) and its rows of the CG vectors in shared memory up to
+ * R = 69 at N = 3 (R = 64 at N = 4) with FP64 CG vectors, R = 100 (91) with
+ * FP32 ones (cg_fp32 = 1); above that it keeps them in global memory (L2),
+ * one block per SM, up to CP_MAX_RANK.  The workspace then grows by about
+ * N (N + 1) R^2 + nblocks (R^2 + 6 (rows per block) R) elements of the CG's
+ * precision and nblocks R^2 for the partial products. */
 cp_status cp_gn_step(cp_handle h, const cp_desc* desc, const void* X, double* const* A,
                      cp_gn_params* params, cp_gn_stats* stats);
 

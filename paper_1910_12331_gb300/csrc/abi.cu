@@ -55,7 +55,7 @@ struct cp_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     DevBuf gram_part, S, Gam, GamF, Pinv, PinvF, precond_scratch, grad_part;
-    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf, Atrial, stats2, tucker;
+    DevBuf Mp, Gp, Ap, vec, Ypart, Tm, pcg_part, bar, stats, Y, resid_planes, Adf, Atrial, stats2, tucker, pcg_spill;
     DevStats* h_stats = nullptr;  // pinned
     DevStats* h_stats2 = nullptr; // pinned: line-search trials
     double* h_tk = nullptr;       // pinned: HoSVD convergence checks
@@ -268,7 +268,7 @@ cp_status cp_destroy(cp_handle h) {
         cudaStreamSynchronize(h->stream);
         DevBuf* bufs[] = {&h->gram_part, &h->grad_part, &h->S, &h->Gam, &h->GamF, &h->Pinv, &h->PinvF, &h->precond_scratch,
                           &h->Mp, &h->Gp, &h->Ap, &h->vec, &h->Ypart, &h->Tm, &h->pcg_part, &h->bar,
-                          &h->stats, &h->Y, &h->resid_planes, &h->Adf, &h->Atrial, &h->stats2, &h->tucker};
+                          &h->stats, &h->Y, &h->resid_planes, &h->Adf, &h->Atrial, &h->stats2, &h->tucker, &h->pcg_spill};
         for (DevBuf* b : bufs)
             if (b->p) cudaFree(b->p);
         if (h->h_stats) cudaFreeHost(h->h_stats);
@@ -300,6 +300,11 @@ cp_status cp_workspace_size(cp_handle h, const cp_desc* d, cp_precision prec, si
     b += rows * s.R * 8 * 2;                    // M, G
     b += rows * s.R * 8 * 7;                    // packed A and CG vectors (FP64 worst case)
     b += (size_t)4096 * RR * 8 + s.N * RR * 8;  // partial A^T W per block, T
+    {  // large R: the CG kernel's matrices and row blocks in global memory (FP64 worst case)
+        const size_t Rp = (size_t)((s.R + 3) & ~3);
+        if ((size_t)(s.N + 2) * s.R * Rp * 8 + 640 > 200 * 1024)
+            b += ((size_t)s.N * (s.N + 1) * s.R * Rp + 256 * (size_t)s.R * Rp + 6 * (rows + 256 * s.N) * Rp) * 8;
+    }
     if (prec != CP_PREC_FP64) {                 // tensor-core MTTKRP: partial sums and operand planes
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
@@ -416,10 +421,14 @@ static void lambda_advance(cp_gn_params* p) {
 template <typename T>
 static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller, const cp_gn_params* p) {
     const size_t RR = (size_t)s.R * s.R, len = (size_t)s.roff[s.N] * s.R;
+    int nblocks = 0;
+    size_t spill = 0;
+    CP_TRY(pcg_plan<T>(s, 0, &nblocks, &spill));
     CP_TRY(grow(h->Ap, len * sizeof(T)));
     CP_TRY(grow(h->vec, len * sizeof(T)));
-    CP_TRY(grow(h->Ypart, (size_t)256 * RR * sizeof(T)));  // per-block A^T Z (at most 256 blocks)
-    CP_TRY(grow(h->Tm, s.N * RR * sizeof(T)));               // Y^(p), reduced
+    CP_TRY(grow(h->Ypart, (size_t)nblocks * RR * sizeof(T)));  // per-block A^T Z
+    CP_TRY(grow(h->Tm, s.N * RR * sizeof(T)));                   // Y^(p), reduced
+    if (spill) CP_TRY(grow(h->pcg_spill, spill * sizeof(T)));    // large R: matrices and rows in global memory
     CP_TRY(grow(h->pcg_part, 3 * 4096 * sizeof(double)));
     CP_TRY(grow(h->bar, sizeof(GridBarrier)));
     launch_pack<T>(s, Acaller, (T*)h->Ap.p, h->stream);
@@ -439,6 +448,7 @@ static cp_status gn_pcg(cp_handle h, const Shape& s, Ptrs<const double> Acaller,
     a.Zpart = (T*)h->Ypart.p;
     a.Yfull = (T*)h->Tm.p;
     a.part = (double*)h->pcg_part.p;
+    a.spill = spill ? (T*)h->pcg_spill.p : nullptr;
     a.bar = (GridBarrier*)h->bar.p;
     a.stats = (DevStats*)h->stats.p;
     a.lam = p->lam;

@@ -11,7 +11,8 @@
 //
 // Persistent layout: every block owns a contiguous range of rows of ONE mode
 // and keeps its rows of A, V, R, Z, W, Q in shared memory for the whole
-// solve.  Only the R x R products A^(p)T W^(p) (accumulated with atomic adds
+// solve (for ranks whose R x R matrices do not fit there, in a global
+// region of its own, with its mode's matrices in global memory too).  Only the R x R products A^(p)T W^(p) (accumulated with atomic adds
 // into a double-buffered global accumulator) and scalar partials cross
 // blocks, with 3 bounded-spin grid barriers per CG iteration.  Scalar
 // reductions (dot products, norms) are FP64 and are summed by every block in
@@ -413,7 +414,7 @@ __device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int row
 // Every cross-block sum runs in a fixed order, so a solve is reproducible.
 // Shared memory holds the block's Gamma^(n,p) (all p), P_inv^(n), T^(n) and
 // its rows of A, V, R, Z, W, Q, every matrix with row stride Rp (zero padded).
-template <typename T>
+template <typename T, bool spill>
 __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stage_mats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Shape& s = a.s;
@@ -432,9 +433,18 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
 
     double* red = reinterpret_cast<double*>(smem_raw);
     double* bcast = red + 72;
-    T* p = reinterpret_cast<T*>(smem_raw + 80 * sizeof(double));
-    T* Gx = p; p += (size_t)N * RRp;   // Gamma^(n,p), p = 0..N-1
-    T* Pm = p; p += RRp;               // P_inv^(n)
+    T* Gx;  // Gamma^(n,p), p = 0..N-1
+    T* Pm;  // P_inv^(n)
+    T* p;
+    if constexpr (spill) {  // the mode's matrices, then the block's own region (T^(n), rows)
+        Gx = a.spill + (size_t)n * (N + 1) * RRp;
+        Pm = Gx + (size_t)N * RRp;
+        p = a.spill + (size_t)N * (N + 1) * RRp + (size_t)b * a.spill_stride;
+    } else {
+        p = reinterpret_cast<T*>(smem_raw + 80 * sizeof(double));
+        Gx = p; p += (size_t)N * RRp;
+        Pm = p; p += RRp;
+    }
     T* Tt = p; p += RRp;               // T^(n) transposed
     const T* Gm = Gx + (size_t)n * RRp;
     const int rl = a.rpb[n] * Rp;
@@ -453,15 +463,18 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
     const long long lim = a.spin_limit;
 
     // ---- set-up: stage the constant matrices and the block's rows, zero padded
-    for (int q = threadIdx.x; q < N * RRp; q += blockDim.x) {
+    // (in global memory the mode's blocks share the staging of its matrices)
+    const int q0 = spill ? j * blockDim.x + threadIdx.x : threadIdx.x;
+    const int qstep = spill ? (a.mode_blk0[n + 1] - a.mode_blk0[n]) * blockDim.x : blockDim.x;
+    for (int q = q0; q < N * RRp; q += qstep) {
         const int pp = q / RRp, e = q - pp * RRp, z = e / Rp, c = e - z * Rp;
         Gx[q] = c < R ? a.GamT[((size_t)n * N + pp) * RR + z * R + c] : (T)0;
     }
-    for (int e = threadIdx.x; e < RRp; e += blockDim.x) {
+    for (int e = q0; e < RRp; e += qstep) {
         const int z = e / Rp, c = e - z * Rp;
         Pm[e] = c < R ? a.PinvT[(size_t)n * RR + z * R + c] : (T)0;
-        Tt[e] = (T)0;
     }
+    for (int e = threadIdx.x; e < RRp; e += blockDim.x) Tt[e] = (T)0;
     for (int e = threadIdx.x; e < lenp; e += blockDim.x) {
         const int k = e / Rp, c = e - k * Rp;
         const bool in = c < R;
@@ -477,21 +490,25 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
     const double tol = a.eps_cg * gsum;
     // Algorithm 1's loop test, evaluated on the device: a stationary point gets no update.
     const bool stationary = a.stop_ratio > 0.0 && gsum <= a.stop_ratio * msum;
+    bool ok = true;
+    if constexpr (spill) ok = grid_sync(a.bar, status, nb, lim);  // the mode's matrices are complete
     __syncthreads();
-    rows_mm<T>(sR, Pm, nullptr, nullptr, (T)0, sZ, rows, R, Rp);
-    __syncthreads();
-    for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = sZ[e];
-    double rz_h, rz_l, rn_h, rn_l;
-    dot2_rows(sR, sZ, sR, sR, lenp, red, rz_h, rz_l, rn_h, rn_l);
-    if (threadIdx.x == 0) {
-        Slot<T>::put(part_rz + b, rz_h, rz_l);
-        Slot<T>::put(part_rn + b, rn_h, rn_l);
+    double rz_h = 0.0, rz_l = 0.0, rn_h = 0.0, rn_l = 0.0;
+    if (ok) {
+        rows_mm<T>(sR, Pm, nullptr, nullptr, (T)0, sZ, rows, R, Rp);
+        __syncthreads();
+        for (int e = threadIdx.x; e < lenp; e += blockDim.x) sW[e] = sZ[e];
+        dot2_rows(sR, sZ, sR, sR, lenp, red, rz_h, rz_l, rn_h, rn_l);
+        if (threadIdx.x == 0) {
+            Slot<T>::put(part_rz + b, rz_h, rz_l);
+            Slot<T>::put(part_rn + b, rn_h, rn_l);
+        }
+        y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
     }
-    y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
 
     int it = 0;
     double rsum = 0.0, rz = 0.0, beta = 0.0;
-    bool ok = grid_sync(a.bar, status, nb, lim);
+    ok = ok && grid_sync(a.bar, status, nb, lim);
     double ratio = 0.0;
     auto reduce_r = [&](double rz_old, double& rz_out, double& rsum_out) {
         gather_rz_rn<T>(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_old, rz_out, rsum_out, ratio);
@@ -617,6 +634,9 @@ struct PcgGeom {
     int64_t dims[kMaxN] = {};
     int nblocks = 0, mode_blk0[kMaxN + 1] = {}, rpb[kMaxN] = {};
     size_t bytes = 0;
+    bool spill = false;          // matrices and rows in global memory
+    int64_t spill_stride = 0;    // elements per block region
+    size_t spill_elems = 0;      // elements of the whole global region
     cp_status status = CP_OK;
 };
 
@@ -630,13 +650,14 @@ static PcgGeom pcg_geometry(const Shape& s, int want, int sms) {
     g.sms = sms;
     for (int n = 0; n < s.N; ++n) g.dims[n] = s.dims[n];
     const int64_t rows_total = s.roff[s.N];
-    int target = std::max(s.N, std::min<int>(want, (int)std::min<int64_t>(rows_total, 4096)));
     const size_t budget = 200 * 1024;
-    if ((size_t)(s.N + 2) * s.R * ((s.R + 3) & ~3) * sizeof(T) + 80 * sizeof(double) > budget) {
-        g.status = CP_ERR_UNSUPPORTED;  // the R x R matrices alone exceed shared memory (large R)
-        return g;
-    }
-    cudaFuncSetAttribute(pcg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
+    const int64_t Rp = (s.R + 3) & ~3;
+    // Large R: the N + 2 R x R matrices alone exceed shared memory.  They and the
+    // row blocks then live in global memory (L2), one block per SM, few rows each.
+    g.spill = (size_t)(s.N + 2) * s.R * Rp * sizeof(T) + 80 * sizeof(double) > budget;
+    if (g.spill) want = std::max(want, sms);
+    int target = std::max(s.N, std::min<int>(want, (int)std::min<int64_t>(rows_total, 4096)));
+    cudaFuncSetAttribute(pcg_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget);
     for (int attempt = 0; attempt < 64; ++attempt) {
         int total = 0, rpb_max = 1;
         for (int n = 0; n < s.N; ++n) {
@@ -651,7 +672,9 @@ static PcgGeom pcg_geometry(const Shape& s, int want, int sms) {
         }
         g.mode_blk0[s.N] = total;
         g.nblocks = total;
-        g.bytes = pcg_smem_bytes<T>(s.N, s.R, rpb_max, true);
+        g.bytes = g.spill ? 80 * sizeof(double) : pcg_smem_bytes<T>(s.N, s.R, rpb_max, true);
+        g.spill_stride = g.spill ? (int64_t)s.R * Rp + 6 * (int64_t)rpb_max * Rp : 0;
+        g.spill_elems = g.spill ? (size_t)s.N * (s.N + 1) * s.R * Rp + (size_t)total * g.spill_stride : 0;
         if (g.bytes > budget) {  // rows do not fit: more blocks
             target = target * 2;
             continue;
@@ -661,7 +684,10 @@ static PcgGeom pcg_geometry(const Shape& s, int want, int sms) {
             continue;
         }
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kThreads, g.bytes);
+        if (g.spill)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T, true>, kThreads, g.bytes);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T, false>, kThreads, g.bytes);
         if (per_sm < 1) {
             g.status = CP_ERR_UNSUPPORTED;
             return g;
@@ -682,8 +708,7 @@ static PcgGeom pcg_geometry(const Shape& s, int want, int sms) {
 }
 
 template <typename T>
-cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
-    const Shape& s = a.s;
+static const PcgGeom& geometry_for(const Shape& s, int max_blocks) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -699,15 +724,38 @@ cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
     for (int n = 0; hit && n < s.N; ++n) hit = g.dims[n] == s.dims[n];
     if (!hit) {
         g = pcg_geometry<T>(s, want, sms);
+        g.want = want;
         g.dev = dev;
     }
+    return g;
+}
+
+template <typename T>
+cp_status pcg_plan(const Shape& s, int max_blocks, int* nblocks, size_t* spill_elems) {
+    const PcgGeom& g = geometry_for<T>(s, max_blocks);
     if (g.status != CP_OK) return g.status;
+    *nblocks = g.nblocks;
+    *spill_elems = g.spill_elems;
+    return CP_OK;
+}
+template cp_status pcg_plan<double>(const Shape&, int, int*, size_t*);
+template cp_status pcg_plan<float>(const Shape&, int, int*, size_t*);
+
+template <typename T>
+cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st) {
+    const Shape& s = a.s;
+    const PcgGeom& g = geometry_for<T>(s, max_blocks);
+    if (g.status != CP_OK) return g.status;
+    if (g.spill && !a.spill) return CP_ERR_ARG;  // the caller did not provide the global region
+    if (!g.spill) a.spill = nullptr;
+    a.spill_stride = g.spill_stride;
     a.nblocks = g.nblocks;
     for (int n = 0; n <= s.N; ++n) a.mode_blk0[n] = g.mode_blk0[n];
     for (int n = 0; n < s.N; ++n) a.rpb[n] = g.rpb[n];
     int stage_i = 1;
     void* args[] = {(void*)&a, (void*)&stage_i};
-    cudaError_t e = cudaLaunchCooperativeKernel((void*)pcg_kernel<T>, dim3(g.nblocks), dim3(kThreads), args, g.bytes, st);
+    void* fn = g.spill ? (void*)pcg_kernel<T, true> : (void*)pcg_kernel<T, false>;
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g.nblocks), dim3(kThreads), args, g.bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return CP_ERR_CUDA;

@@ -68,7 +68,8 @@ struct PcgArgs {
     T* V;               // packed update (output)
     T* Zpart;           // [nblocks][R*R]: each block's A^T Z over its rows
     T* Yfull;           // [N][R*R]: Y^(p) = A^(p)T W^(p), reduced in a fixed order
-    T* Tm;              // N*R*R scratch for T^(n) when it does not fit in shared memory
+    T* spill;           // large R: the matrices and row blocks in global memory (null: shared memory)
+    int64_t spill_stride;  // elements of one block's region in `spill`
     double* part;       // [3][nblocks] per-block partial scalars
     GridBarrier* bar;
     DevStats* stats;
@@ -86,6 +87,11 @@ struct PcgArgs {
 };
 template <typename T>
 cp_status launch_pcg(PcgArgs<T>& a, int max_blocks, cudaStream_t st);
+// The CG kernel's geometry for a shape: its block count and the elements of T
+// of global memory it needs when the R x R matrices do not fit in shared
+// memory (0 otherwise).  Cached; launch_pcg uses the same geometry.
+template <typename T>
+cp_status pcg_plan(const Shape& s, int max_blocks, int* nblocks, size_t* spill_elems);
 // Plain (non-persistent) matvec used by cp_gn_matvec: Q = (J^T J + lam D) W,
 // D = I or (diag) diag(J^T J), in FP64 (T = double) or the mixed CG's FP32
 // arithmetic (T = float).  Y: N R^2 elements of T scratch.

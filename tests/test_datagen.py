@@ -98,3 +98,20 @@ def test_batched_problem_mix():
     again = datagen.batched_problems(count=4, seed=3)
     for p, q in zip(probs[:4], again):
         assert p["X"].tobytes() == q["X"].tobytes()
+
+
+def test_tucker_tensor_recipe():
+    """Exact multilinear rank: every unfolding has rank r_n, its column space is
+    spanned by the orthonormal Q_n; the noise is the stated relative level;
+    seeds reproduce the bytes."""
+    X, Q = datagen.tucker_tensor((9, 8, 7), (3, 4, 2), seed=5)
+    for n, (q, r) in enumerate(zip(Q, (3, 4, 2))):
+        np.testing.assert_allclose(q.T @ q, np.eye(r), atol=1e-14)
+        Xn = np.moveaxis(X, n, 0).reshape(X.shape[n], -1)
+        sv = np.linalg.svd(Xn, compute_uv=False)
+        assert sv[r - 1] > 1e-3 * sv[0] and (len(sv) == r or sv[r] < 1e-12 * sv[0])
+        np.testing.assert_allclose(q @ (q.T @ Xn), Xn, atol=1e-12 * np.abs(Xn).max())
+    Xe, _ = datagen.tucker_tensor((9, 8, 7), (3, 4, 2), noise=1e-3, seed=5)
+    assert abs(np.linalg.norm(Xe - X) / np.linalg.norm(X) - 1e-3) < 1e-12
+    X2, _ = datagen.tucker_tensor((9, 8, 7), (3, 4, 2), seed=5)
+    assert X.tobytes() == X2.tobytes()

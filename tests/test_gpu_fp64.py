@@ -266,21 +266,6 @@ def test_als_sweep_fp64(env, orc, dims, R, lam):
 
 # --------------------------------------------------------------- error paths
 
-def test_gn_step_rank_beyond_cg_shared_memory(env):
-    """R = 80 at order 3 needs 5 R^2 FP64 words of shared memory in the CG
-    kernel (256 KB > 200 KB): CP_ERR_UNSUPPORTED, the factors untouched."""
-    torch, api, h = env
-    dims, R = (30, 25, 20), 80
-    A = _factors(dims, R, 31)
-    Ad = _dev(torch, A)
-    params = api.gn_params(1.0, 1e-6, 1.0, eps_cg=0.0, cg_max_iter=2, cg_fp32=False)
-    s, _ = api.cp_gn_step(h, torch.from_numpy(_tensor(dims, 31)).cuda(), Ad, params, check=False)
-    assert s == api.CP_ERR_UNSUPPORTED
-    for a, a0 in zip(Ad, A):
-        np.testing.assert_array_equal(a.cpu().numpy(), a0)
-    assert params.lam == 1.0
-
-
 def test_nonfinite_reported(env):
     torch, api, h = env
     dims, R = (6, 5, 4), 2
