@@ -60,7 +60,10 @@ struct cp_handle_s {
     DevStats* h_stats2 = nullptr; // pinned: line-search trials
     double* h_tk = nullptr;       // pinned: HoSVD convergence checks
     SplitCache split;             // bf16 planes of X (tensor-core path)
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step timing
+    // step timing: start, gradient phase end, CG start, step end, gradient phase start
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t side = nullptr;  // the preconditioner beside the gradient phase
+    cudaEvent_t fork = nullptr, gam = nullptr, join = nullptr;
     int launches = 0;             // kernels launched by the current call
     int cg_blocks = 0;            // blocks of the last persistent CG launch
 };
@@ -71,6 +74,13 @@ static cp_status ensure_events(cp_handle h) {
             cudaGetLastError();
             return CP_ERR_CUDA;
         }
+    if ((!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) ||
+        (!h->fork && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) ||
+        (!h->gam && cudaEventCreateWithFlags(&h->gam, cudaEventDisableTiming) != cudaSuccess) ||
+        (!h->join && cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        return CP_ERR_CUDA;
+    }
     return CP_OK;
 }
 
@@ -184,7 +194,7 @@ static cp_status sync_stats(cp_handle h) {
 
 // M (caller or packed pointers) = all-mode MTTKRP of X at `prec`.
 static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, const void* X, Ptrs<const double> A,
-                             Ptrs<double> M, cp_precision prec) {
+                             Ptrs<double> M, cp_precision prec, int reserve_sms = 0) {
     for (int n = 0; n < s.N; ++n)
         CUDA_TRY(cudaMemsetAsync(M.p[n], 0, (size_t)s.dims[n] * s.R * sizeof(double), h->stream));
     if (prec == CP_PREC_FP64) {
@@ -202,7 +212,7 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
         if (resid_tc_supported(s)) {  // reconstruction on the tensor cores (R <= 64)
             CP_TRY(grow(h->Adf, resid_tc_scratch_bytes(s)));
             h->launches += launch_resid_split_tc(s, d->x_dtype, X, A, h->resid_planes.p, nullptr, h->Adf.p, ds,
-                                                 &ds->status, h->stream);
+                                                 &ds->status, h->stream, reserve_sms);
         } else {
             CP_TRY(grow(h->Adf, resid_scratch_bytes(s)));
             launch_resid_split(s, d->x_dtype, X, A, h->resid_planes.p, nullptr, h->Adf.p, ds, h->stream);
@@ -218,11 +228,10 @@ static cp_status mttkrp_into(cp_handle h, const cp_desc* d, const Shape& s, cons
 }
 
 // S, Gamma (FP64) and the float copy of Gamma.
-static cp_status gram_gamma(cp_handle h, const Shape& s, Ptrs<const double> A) {
+static cp_status gram_gamma(cp_handle h, const Shape& s, Ptrs<const double> A, cudaStream_t st) {
     const int chunks = gram_chunks(s);
-    launch_gram_partial(s, A, (double*)h->gram_part.p, chunks, h->stream);
-    launch_gamma(s, (const double*)h->gram_part.p, chunks, (double*)h->S.p, (double*)h->Gam.p, (float*)h->GamF.p,
-                 h->stream);
+    launch_gram_partial(s, A, (double*)h->gram_part.p, chunks, st);
+    launch_gamma(s, (const double*)h->gram_part.p, chunks, (double*)h->S.p, (double*)h->Gam.p, (float*)h->GamF.p, st);
     CUDA_TRY(cudaGetLastError());
     return CP_OK;
 }
@@ -276,6 +285,13 @@ cp_status cp_destroy(cp_handle h) {
         if (h->h_tk) cudaFreeHost(h->h_tk);
         for (auto& e : h->ev)
             if (e) cudaEventDestroy(e);
+        if (h->side) {
+            cudaStreamSynchronize(h->side);
+            cudaStreamDestroy(h->side);
+        }
+        if (h->fork) cudaEventDestroy(h->fork);
+        if (h->gam) cudaEventDestroy(h->gam);
+        if (h->join) cudaEventDestroy(h->join);
         split_cache_free(h->split);
         cudaGetLastError();
     }
@@ -348,7 +364,7 @@ cp_status cp_gradient(cp_handle h, const cp_desc* d, const void* X, const double
     const Ptrs<const double> Ap = ptrs_of(A, s.N);
     CUDA_TRY(cudaMemsetAsync(h->stats.p, 0, sizeof(DevStats), h->stream));
     CP_TRY(mttkrp_into(h, d, s, X, Ap, packed_ptrs((double*)h->Mp.p, s), prec));
-    CP_TRY(gram_gamma(h, s, Ap));
+    CP_TRY(gram_gamma(h, s, Ap, h->stream));
     launch_gradient(s, Ap, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
                     (double*)h->grad_part.p, (DevStats*)h->stats.p, h->stream, prec == CP_PREC_RESIDUAL);
     launch_unpack(s, (const double*)h->Gp.p, ptrs_of(G, s.N), h->stream);
@@ -382,7 +398,7 @@ cp_status cp_gn_matvec(cp_handle h, const cp_desc* d, const double* const* A, co
         launch_gamma(s, grams, 1, (double*)h->S.p, (double*)h->Gam.p, nullptr, h->stream);
         CUDA_TRY(cudaGetLastError());
     } else {
-        CP_TRY(gram_gamma(h, s, Ap));
+        CP_TRY(gram_gamma(h, s, Ap, h->stream));
     }
     const bool diag = reg == CP_REG_DIAG;
     if (prec == CP_PREC_FP64)
@@ -472,26 +488,49 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
     DevStats* ds = (DevStats*)h->stats.p;
     CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
     CUDA_TRY(cudaMemsetAsync(ds, 0, sizeof(DevStats), h->stream));
-    // Algorithm 1: MTTKRP, Gamma^(n,p), G^(n) = A^(n) Gamma^(n,n) - M^(n)
-    CP_TRY(mttkrp_into(h, d, s, X, Ac, packed_ptrs((double*)h->Mp.p, s), p->prec));
+    // Algorithm 1: MTTKRP, Gamma^(n,p), G^(n) = A^(n) Gamma^(n,n) - M^(n).
+    // With identity damping, Gamma and P_inv = (Gamma^(n,n) + lambda I)^{-1} (Algorithm 2)
+    // depend on A and lambda only: they run on a second stream beside the MTTKRP, whose
+    // persistent reconstruction leaves N SMs to them.  (The diagonal damping changes
+    // Gamma^(n,n) after the gradient has used it, so it keeps the serial order.)
+    cp_gn_params q = *p;
+    const bool beside = p->reg != CP_REG_DIAG;
+    if (beside) {
+        CUDA_TRY(cudaEventRecord(h->fork, h->stream));
+        CUDA_TRY(cudaStreamWaitEvent(h->side, h->fork, 0));
+        CP_TRY(gram_gamma(h, s, Ac, h->side));
+        CUDA_TRY(cudaEventRecord(h->gam, h->side));
+        launch_precond(s, (const double*)h->Gam.p, q.lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
+                       (double*)h->precond_scratch.p, ds, h->side, p->cg_fp32 != 0);
+        h->launches += 3;
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventRecord(h->join, h->side));
+    }
+    CUDA_TRY(cudaEventRecord(h->ev[4], h->stream));
+    CP_TRY(mttkrp_into(h, d, s, X, Ac, packed_ptrs((double*)h->Mp.p, s), p->prec, beside ? s.N : 0));
     CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
-    CP_TRY(gram_gamma(h, s, Ac));
-    h->launches += 2;
+    if (beside) {
+        CUDA_TRY(cudaStreamWaitEvent(h->stream, h->gam, 0));  // the gradient reads Gamma
+    } else {
+        CP_TRY(gram_gamma(h, s, Ac, h->stream));
+        h->launches += 2;
+    }
     launch_gradient(s, Ac, (const double*)h->Gam.p, (const double*)h->Mp.p, (double*)h->Gp.p,
                     (double*)h->grad_part.p, ds, h->stream, p->prec == CP_PREC_RESIDUAL);
-    h->launches += 1;  // the fixed-order norm reduction
-    // Damping lam diag(J^T J): fold it into the diagonals of Gamma^(n,n) (the
-    // gradient above used them undamped) and solve the system with lam = 0.
-    cp_gn_params q = *p;
-    if (p->reg == CP_REG_DIAG) {
+    h->launches += 2;  // the gradient and its fixed-order norm reduction
+    if (beside) {
+        CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join, 0));
+    } else {
+        // Damping lam diag(J^T J): fold it into the diagonals of Gamma^(n,n) (the
+        // gradient above used them undamped) and solve the system with lam = 0.
         launch_damp_diag(s, (double*)h->Gam.p, (float*)h->GamF.p, p->lam, h->stream);
         h->launches += 1;
         q.lam = 0.0;
+        // Algorithm 2: P_inv = (Gamma^(n,n) + lambda D)^{-1}, then CG
+        launch_precond(s, (const double*)h->Gam.p, q.lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
+                       (double*)h->precond_scratch.p, ds, h->stream, p->cg_fp32 != 0);
+        h->launches += 1;
     }
-    // Algorithm 2: P_inv = (Gamma^(n,n) + lambda I)^{-1}, then CG
-    launch_precond(s, (const double*)h->Gam.p, q.lam, (double*)h->Pinv.p, (float*)h->PinvF.p,
-                   (double*)h->precond_scratch.p, ds, h->stream, p->cg_fp32 != 0);
-    h->launches += 2;
     CUDA_TRY(cudaGetLastError());
     if (p->cg_fp32)
         CP_TRY(gn_pcg<float>(h, s, Ac, &q));
@@ -583,7 +622,7 @@ static cp_status gn_step_impl(cp_handle h, const cp_desc* d, const void* X, doub
         st->rel_residual = p->want_residual ? sqrt(hs.res_num) / sqrt(hs.res_den) : -1.0;
         st->entry_residual = p->prec == CP_PREC_RESIDUAL ? sqrt(hs.eres_num) / sqrt(hs.eres_den) : -1.0;
         float t01 = 0.f, t23 = 0.f, t03 = 0.f;
-        cudaEventElapsedTime(&t01, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&t01, h->ev[4], h->ev[1]);
         cudaEventElapsedTime(&t23, h->ev[2], h->ev[3]);
         cudaEventElapsedTime(&t03, h->ev[0], h->ev[3]);
         cudaGetLastError();
@@ -693,7 +732,7 @@ cp_status cp_als_sweep(cp_handle h, const cp_desc* d, const void* X, double* con
     const Ptrs<const double> Ac = ptrs_of((const double* const*)A, s.N);
     Ptrs<double> Mp = packed_ptrs((double*)h->Mp.p, s);
     for (int n = 0; n < s.N; ++n) {
-        CP_TRY(gram_gamma(h, s, Ac));
+        CP_TRY(gram_gamma(h, s, Ac, h->stream));
         CUDA_TRY(cudaMemsetAsync(Mp.p[n], 0, (size_t)s.dims[n] * s.R * sizeof(double), h->stream));
         if (prec == CP_PREC_FP64)
             launch_mttkrp_f64(s, d->x_dtype, X, Ac, Mp, 1u << n, h->stream);

@@ -78,8 +78,8 @@ __device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int* p, un
 // Grid-wide barrier for a co-resident (cooperatively launched) grid, on one
 // monotonic arrival counter (zeroed before the launch): the k-th barrier is
 // complete when the counter reaches k * nblocks.  Thread 0 of each block
-// publishes the block's writes (fence + release add) and polls with acquire
-// loads; the abort flag is read every 32nd poll, so that a poll costs one L2
+// publishes the block's writes (block barrier, fence, release add) and polls
+// with acquire loads; the abort flag is read every 32nd poll, so that a poll costs one L2
 // round trip.  Every wait is bounded by `limit` polls: on expiry the barrier
 // records CP_ERR_TIMEOUT, raises the abort flag and returns false; a block
 // waiting in any barrier sees the flag within 32 polls and returns false too,

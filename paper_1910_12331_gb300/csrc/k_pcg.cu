@@ -407,10 +407,11 @@ __device__ __forceinline__ void y_tiles(const T* A, const T* W, T* Yacc, int row
 }
 
 // Persistent CP-CG.  Per iteration, three grid barriers:
-//   (B1) Y^(p) = A^(p)T W^(p) complete: T^(n), Q rows, partial <W,Q>;
+//   (B1) Y^(p)(W) complete: T^(n), Q rows, partial <W,Q>;
 //   (B2) alpha, V/R update, Z = R P_inv, partial <R,Z>, |R^(n)|^2 and A^T Z;
-//   (B3) beta, W = Z + beta W, and Y = sum_blocks A^T Z + beta Y in a fixed
-//        order (the same as A^T W), split over all blocks.
+//   (B3) the scalar gather (beta, stop test) and, beside it, Y^(p)(W) =
+//        sum_blocks A^T Z (fixed order, split over all blocks) + beta Y^(p)(W);
+//        W = Z + beta W.
 // Every cross-block sum runs in a fixed order, so a solve is reproducible.
 // Shared memory holds the block's Gamma^(n,p) (all p), P_inv^(n), T^(n) and
 // its rows of A, V, R, Z, W, Q, every matrix with row stride Rp (zero padded).
@@ -510,10 +511,50 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
     double rsum = 0.0, rz = 0.0, beta = 0.0;
     ok = ok && grid_sync(a.bar, status, nb, lim);
     double ratio = 0.0;
-    auto reduce_r = [&](double rz_old, double& rz_out, double& rsum_out) {
-        gather_rz_rn<T>(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_old, rz_out, rsum_out, ratio);
+    // After the set-up and after every third barrier: Y^(p)(W) = Y^(p)(Z) + beta Y^(p)(W_old) (Y is
+    // linear in W and W = Z + beta W_old), Y^(p)(Z) the sum over the blocks of mode p of their A^T Z in a
+    // fixed order, spread over warps 1.. of all blocks, while warp 0 of every block gathers the scalar
+    // partials (rz = <R,Z>, the per-mode |R|, beta = rz / rz_old): both read only what the barrier
+    // completed, so their L2 round trips overlap; a thread's first entry waits for beta in registers.
+    const size_t ny = (size_t)N * RR;
+    auto sum_partials = [&](size_t e) -> T {
+        const int pp = (int)(e / RR), q = (int)(e - (size_t)pp * RR);
+        const int c0 = a.mode_blk0[pp], c1 = a.mode_blk0[pp + 1];
+        T acc = (T)0;
+        int c = c0;
+        for (; c + 16 <= c1; c += 16) {  // sixteen partials in flight per round
+            T v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc += v[u];
+        }
+        if (c < c1) {
+            T v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = c + u < c1 ? ldcg(&a.Zpart[(size_t)(c + u) * RR + q]) : (T)0;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc += v[u];
+        }
+        return acc;
     };
-    if (ok) reduce_r(0.0, rz, rsum);
+    auto gather = [&](double rz_old, bool first, double& rz_out, double& rsum_out) {
+        const size_t nw = blockDim.x - 32, estep = (size_t)nb * nw;
+        const size_t e0 = (size_t)b * nw + (threadIdx.x - 32);
+        const bool have0 = threadIdx.x >= 32 && e0 < ny;
+        T acc0 = (T)0, y0 = (T)0;
+        if (have0) {
+            if (!first) y0 = a.Yfull[e0];
+            acc0 = sum_partials(e0);
+        }
+        gather_rz_rn<T>(part_rz, part_rn, (int)nb, a.mode_blk0, N, bcast, rz_old, rz_out, rsum_out, ratio);
+        const T be = first ? (T)0 : (T)ratio;
+        if (have0) {
+            a.Yfull[e0] = fmadd(be, y0, acc0);
+            for (size_t e = e0 + estep; e < ny; e += estep) a.Yfull[e] = fmadd(be, a.Yfull[e], sum_partials(e));
+        }
+    };
+    if (ok) gather(0.0, true, rz, rsum);
     if (stationary) {
         ok = false;
         if (b == 0 && threadIdx.x == 0) a.stats->stopped = 1;
@@ -522,54 +563,30 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
         if (!(rsum > tol)) break;
         if (!isfinite(rsum) || !isfinite(rz)) { set_status(status, CP_ERR_NONFINITE); break; }
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
-        // ---- Y^(p) = sum over the blocks of mode p of A^T Z, + beta Y^(p): fixed order
-        {
-            const T be = (T)beta;
-            const size_t ny = (size_t)N * RR;
-            for (size_t e = (size_t)b * blockDim.x + threadIdx.x; e < ny; e += (size_t)nb * blockDim.x) {
-                const int pp = (int)(e / RR), q = (int)(e - (size_t)pp * RR);
-                const int c0 = a.mode_blk0[pp], c1 = a.mode_blk0[pp + 1];
-                T acc = it == 0 ? (T)0 : be * a.Yfull[e];
-                int c = c0;
-                for (; c + 16 <= c1; c += 16) {  // sixteen partials in flight per round
-                    T v[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) acc += v[u];
-                }
-                if (c < c1) {
-                    T v[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) v[u] = c + u < c1 ? ldcg(&a.Zpart[(size_t)(c + u) * RR + q]) : (T)0;
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) acc += v[u];
-                }
-                a.Yfull[e] = acc;
-            }
-        }
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
-        // ---- T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p), stored transposed (Tt[z][r] = T[r][z]);
+        // ---- T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p)(W), stored transposed (Tt[z][r] = T[r][z]);
         // every thread issues its loads of Y (up to kTQ entries, the modes but n) before using them
-        for (int q0 = threadIdx.x; q0 < RR; q0 += kTQ<T> * blockDim.x) {
-            T y[kTQ<T>][kMaxN];
+        {
+            for (int q0 = threadIdx.x; q0 < RR; q0 += kTQ<T> * blockDim.x) {
+                T y[kTQ<T>][kMaxN];
 #pragma unroll
-            for (int u = 0; u < kTQ<T>; ++u) {
-                const int q = q0 + u * blockDim.x;
+                for (int u = 0; u < kTQ<T>; ++u) {
+                    const int q = q0 + u * blockDim.x;
 #pragma unroll
-                for (int pp = 0; pp < kMaxN; ++pp)
-                    y[u][pp] = (pp < N && pp != n && q < RR) ? ldcg(&a.Yfull[(size_t)pp * RR + q]) : (T)0;
-            }
+                    for (int pp = 0; pp < kMaxN; ++pp)
+                        y[u][pp] = (pp < N && pp != n && q < RR) ? ldcg(&a.Yfull[(size_t)pp * RR + q]) : (T)0;
+                }
 #pragma unroll
-            for (int u = 0; u < kTQ<T>; ++u) {
-                const int q = q0 + u * blockDim.x;
-                if (q >= RR) break;
-                const int r = q / R, z = q - r * R;
-                T t = 0;
+                for (int u = 0; u < kTQ<T>; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q >= RR) break;
+                    const int r = q / R, z = q - r * R;
+                    T t = 0;
 #pragma unroll
-                for (int pp = 0; pp < kMaxN; ++pp)
-                    if (pp < N && pp != n) t = fmadd(Gx[(size_t)pp * RRp + r * Rp + z], y[u][pp], t);
-                Tt[z * Rp + r] = t;
+                    for (int pp = 0; pp < kMaxN; ++pp)
+                        if (pp < N && pp != n) t = fmadd(Gx[(size_t)pp * RRp + r * Rp + z], y[u][pp], t);
+                    Tt[z * Rp + r] = t;
+                }
             }
         }
         __syncthreads();
@@ -600,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
         y_tiles(sA, sZ, a.Zpart + (size_t)b * RR, rows, R, Rp);
         if (!(ok = grid_sync(a.bar, status, nb, lim))) break;
         double rz_new;
-        reduce_r(rz, rz_new, rsum);
+        gather(rz, false, rz_new, rsum);
         ++it;
         if (!(rsum > tol)) break;
         if (it >= a.maxit) { set_status(status, CP_WARN_CG_MAXIT); break; }
@@ -714,10 +731,10 @@ static const PcgGeom& geometry_for(const Shape& s, int max_blocks) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t rows_total = s.roff[s.N];
     // FP64 vectors: the work is DFMA-bound, spread it over every SM.  FP32
-    // vectors: the iteration is latency-bound, so use fewer, fatter blocks
-    // (about 32 rows each) to shorten the barriers and reductions.
+    // vectors: the iteration is latency-bound; about 16 rows per block (measured
+    // at 400^3, R = 50: 19.1 us per iteration at 75-150 blocks, 20.7 us at 36).
     int want = max_blocks > 0 ? max_blocks
-                              : (sizeof(T) == 8 ? sms : (int)std::min<int64_t>(sms, (rows_total + 31) / 32));
+                              : (sizeof(T) == 8 ? sms : (int)std::min<int64_t>(sms, (rows_total + 15) / 16));
     static thread_local PcgGeom cache[2];
     PcgGeom& g = cache[sizeof(T) == 8];
     bool hit = g.N == s.N && g.R == s.R && g.want == want && g.sms == sms && g.dev == dev;

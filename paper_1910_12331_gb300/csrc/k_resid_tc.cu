@@ -601,7 +601,8 @@ bool resid_tc_supported(const Shape& s) {
 size_t resid_tc_scratch_bytes(const Shape& s) { return rtc::layout_of(s).total; }
 
 int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                          double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st) {
+                          double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st,
+                          int reserve_sms) {
     using namespace rtc;
     static bool attr_set[64] = {};
     static int sms_of[64] = {};
@@ -664,7 +665,9 @@ int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<cons
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
-    const int grid = (int)std::min<int64_t>(sms, p.runs);
+    // one CTA per SM (a CTA's shared memory fills an SM), less the SMs reserved for work beside it:
+    // a CTA that had to wait for one of them would finish its static share of the runs late
+    const int grid = (int)std::min<int64_t>(std::max(1, sms - std::max(0, reserve_sms)), p.runs);
     recon_tc_kernel<<<grid, kThreads, kDynSmem, st>>>(tmX, p);
     return launched;
 }

@@ -116,8 +116,10 @@ size_t resid_scratch_bytes(const Shape& s);
 // error-free bf16 slice products; returns the number of kernels launched.
 bool resid_tc_supported(const Shape& s);
 size_t resid_tc_scratch_bytes(const Shape& s);
+// reserve_sms: SMs left free for work running beside it on another stream.
 int launch_resid_split_tc(const Shape& s, cp_dtype xdt, const void* X, Ptrs<const double> A, void* planes,
-                          double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st);
+                          double* E64, void* scratch, DevStats* stats, int* status, cudaStream_t st,
+                          int reserve_sms = 0);
 
 // ---- truncated HoSVD / Tucker compression (k_tucker.cu) -----------------------------
 // FP64 scratch (doubles) of launch_hosvd with `slabs` contraction slabs for the Grams.
