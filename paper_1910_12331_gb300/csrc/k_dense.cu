@@ -152,7 +152,9 @@ __global__ void gradient_kernel(Shape s, Ptrs<const double> A, const double* Gam
         const double* Gnn = Gam + ((int64_t)n * s.N + n) * R * R;
         const double* a = A.p[n] + i * R;
         double acc = 0.0;
-        for (int z = 0; z < R; ++z) acc += a[z] * Gnn[(int64_t)r * R + z];  // Gamma symmetric
+        // Gamma^(n,n) is symmetric bit for bit (its Grams sum the same products in the same
+        // order for (r, z) and (z, r)): read column r, contiguous across the warp's threads
+        for (int z = 0; z < R; ++z) acc += a[z] * Gnn[(int64_t)z * R + r];
         const double mv = M[s.roff[n] * R + e];
         // resid: mv = (E_(n) P^(n))_{ir}, G = -mv, M = A Gamma - G
         const double g = resid ? -mv : acc - mv;
