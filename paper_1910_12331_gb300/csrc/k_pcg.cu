@@ -522,19 +522,20 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
         const int c0 = a.mode_blk0[pp], c1 = a.mode_blk0[pp + 1];
         T acc = (T)0;
         int c = c0;
-        for (; c + 16 <= c1; c += 16) {  // sixteen partials in flight per round
-            T v[16];
+        constexpr int kIn = sizeof(T) == 4 ? 32 : 16;  // partials in flight per round
+        for (; c + kIn <= c1; c += kIn) {
+            T v[kIn];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
+            for (int u = 0; u < kIn; ++u) v[u] = ldcg(&a.Zpart[(size_t)(c + u) * RR + q]);
 #pragma unroll
-            for (int u = 0; u < 16; ++u) acc += v[u];
+            for (int u = 0; u < kIn; ++u) acc += v[u];
         }
         if (c < c1) {
-            T v[16];
+            T v[kIn];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) v[u] = c + u < c1 ? ldcg(&a.Zpart[(size_t)(c + u) * RR + q]) : (T)0;
+            for (int u = 0; u < kIn; ++u) v[u] = c + u < c1 ? ldcg(&a.Zpart[(size_t)(c + u) * RR + q]) : (T)0;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) acc += v[u];
+            for (int u = 0; u < kIn; ++u) acc += v[u];
         }
         return acc;
     };
