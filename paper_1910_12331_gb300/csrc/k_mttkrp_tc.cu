@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(Params p, Ptrs<double> M,
         // a fixed order
         __shared__ double qsum[4][kKC];
         const int c = blockIdx.x >> 6, r = blockIdx.x & 63;
-        if (c >= p.nch) return;  // uniform over the block
+        if (c >= p.nch || r >= Rt) return;  // uniform over the block (ranks past the tile's own: nothing to write)
         const int kk = threadIdx.x & 63, qt = threadIdx.x >> 6;
         const int64_t k = (int64_t)c * kKC + kk;
         const int g = c / kGroup, cc = c % kGroup;

@@ -551,7 +551,9 @@ __global__ void recon_prep_v(Shape s, const double* AN, int nck, unsigned char* 
         double x = v[h] * __longlong_as_double((2046LL << 52) - __double_as_longlong(t));  // 1 / t, t = 2^k
 #pragma unroll
         for (int sl = 1; sl <= kSlices; ++sl) {
-            const double g = ldexp(1.0, 8 * sl), gi = ldexp(1.0, -8 * sl);
+            // 2^(8 sl) and 2^(-8 sl) from their bit patterns
+            const double g = __longlong_as_double((long long)(1023 + 8 * sl) << 52);
+            const double gi = __longlong_as_double((long long)(1023 - 8 * sl) << 52);
             const double pc = rint(x * g) * gi;
             x -= pc;
             *reinterpret_cast<__nv_bfloat16*>(img + (size_t)(sl - 1) * kBSlice + sw128(kk, r)) =
