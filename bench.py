@@ -354,9 +354,27 @@ def batched_timing(dev, count=512):
               "not_converged": [{"problem": i, "status": r["status"], "iters": r["iters"],
                                  "rel_residual": r["rel_residual"]} for i, r in enumerate(res_ls) if not r["converged"]]}
     h.close()
+    # Algorithmic work of the timed solve, per problem (order 3, Pi = s1 s2 s3, S = s1 + s2 + s3): per GN
+    # iteration 6 Pi R flops (the all-mode MTTKRP by the dimension tree, 4 Pi R, and the stop test's
+    # reconstruction, 2 Pi R) plus 6 S R^2 (Grams, gradient, update); per CG iteration 16 S R^2 (the implicit
+    # matvec's three R x R products per row and the preconditioner's one).  Against the FP32 FMA peak of the
+    # GPU at 2070 MHz (SMs x 128 lanes x 2 flops): the kernel runs this arithmetic in FP32 on the CUDA cores.
+    work = []
+    for p, r in zip(probs, res):
+        d3, R = p["X"].shape, p["truth"][0].shape[1]
+        Pi, S = float(np.prod(d3)), float(sum(d3))
+        work.append(r["iters"] * (6.0 * Pi * R + 6.0 * S * R * R) + r["cg_iters_total"] * 16.0 * S * R * R)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    achieved = float(np.sum(work)) / (ms / 1e3) / 1e12
+    imax = int(np.argmax(work))
+    roof = {"bound": "latency (one CTA per problem, every step a block-level reduction)", "gflop": float(np.sum(work)) / 1e9,
+            "achieved_tflops": achieved, "fp32_peak_tflops": fp32_peak, "frac": achieved / fp32_peak,
+            "largest_problem": {"problem": imax, "gflop": work[imax] / 1e9, "gn_iters": res[imax]["iters"],
+                                "cg_iters": res[imax]["cg_iters_total"], "share_of_work": work[imax] / float(np.sum(work))}}
     return {"workload": f"{count} order-3 FP32 problems, sides U{{16..96}}, ranks U{{4..24}}, N(0,1) factors, "
                         "1e-8 noise; target r <= 1e-6 or 200 GN iterations",
-            "ms": ms, "problems_per_s": count / (ms / 1e3), "converged": conv,
+            "ms": ms, "problems_per_s": count / (ms / 1e3), "converged": conv, "roofline": roof,
             "gn_iters_mean": float(np.mean([r["iters"] for r in res])),
             "cg_iters_mean": float(np.mean([r["cg_iters_total"] for r in res])),
             "cg_breakdowns": sum(r["cg_breakdowns"] for r in res),
@@ -489,6 +507,24 @@ def c3_cpu_sample():
     return {"kind": "oracle", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
             "unit": "s per iteration", "gn_iteration_s": t_gn, "als_sweep_s": t_als,
             "sample": "one GN iteration (dimension-tree MTTKRP, CG to 1e-3) and one ALS sweep from the start"}
+
+
+def exact_cp_cpu_sample():
+    """One GN iteration (varying identity damping, from the start) of the FP64 oracle on each exact-CP
+    workload with R above the sides, timed on the host cores (bounded sample; unit: s per iteration)."""
+    import oracle
+    from paper_1910_12331_gb300 import datagen
+
+    out = {"kind": "oracle", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+           "unit": "s per GN iteration", "sample": "one GN iteration (CG to 1e-3) from the start of each workload"}
+    for name, sd, R, dist in (("gauss80_r120", 80, 120, "normal"), ("uniform11_150_r200", 150, 200, "uniform11")):
+        p = datagen.make_problem((sd, sd, sd), R, dist=dist, dtype=np.float64, seed=0)
+        hi, lo = lam_thresholds(p["init"])
+        t0 = time.perf_counter()
+        _, _, _, st, _ = oracle.gn_step(p["X"], [a.copy() for a in p["init"]], hi, 0, lo, hi, MU, EPS_CG, CG_MAX, 0,
+                                        True)
+        out[name] = {"gn_iteration_s": time.perf_counter() - t0, "cg_iters": st["cg_iters"]}
+    return out
 
 
 def likelihood_study(dev, n_problems=100, starts=15):
@@ -921,6 +957,7 @@ def main():
     if not args.no_cpu_baseline:
         cpu = cpu_baseline_record(p, lam_hi, lam_lo)
         c3_info["cpu_baseline"] = c3_cpu_sample()
+        exact_info["cpu_baseline"] = exact_cp_cpu_sample()
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
