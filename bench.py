@@ -58,13 +58,13 @@ MU = 2.0
 # profiles/resid_gradient_collinear400.md).  It is reported only while every source of the record
 # still has the SHA-1 it had when the counters were taken.
 PROFILED = {
-    "pcg": {"src": {"paper_1910_12331_gb300/csrc/k_pcg.cu": "24d022423a189dc3b24ea1a80b73ec1ed1e3e913",
-                    "paper_1910_12331_gb300/csrc/common.cuh": "38895925148d4aefd7ace4863abd08e9daeb8fa3"},
-            "dram_bytes": 934912 + 16384, "cg_iters": 25},
-    # recon_tc_kernel (272335104 B read + 244399104 B written) + mttkrp_tc_kernel (391951104 + 6906880)
-    "gradient": {"src": {"paper_1910_12331_gb300/csrc/k_resid_tc.cu": "b1313156a691a5fc88c474cb9faaf3b6d039073e",
-                         "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu": "7fa17f39d64c1220a4737a72f92bcbbc7bbb0ae7"},
-                 "dram_bytes": 272335104 + 244399104 + 391951104 + 6906880},
+    "pcg": {"src": {"paper_1910_12331_gb300/csrc/k_pcg.cu": "8d1f61e031a45b4987413092a51efb5b5ab5c16b",
+                    "paper_1910_12331_gb300/csrc/common.cuh": "40734fb1244aa169472e951051e1c496044bcc11"},
+            "dram_bytes": 966656 + 136960, "cg_iters": 27},
+    # recon_tc_kernel (272687360 B read + 244927232 B written) + mttkrp_tc_kernel (391966464 + 7487488)
+    "gradient": {"src": {"paper_1910_12331_gb300/csrc/k_resid_tc.cu": "e1d375b16ea4885322925fd0296c72138322ddbb",
+                         "paper_1910_12331_gb300/csrc/k_mttkrp_tc.cu": "07a08367384d5c9fe3585da614836548472bec1a"},
+                 "dram_bytes": 272687360 + 244927232 + 391966464 + 7487488},
 }
 # The mixed path of the timed solve: residual-form gradient every iteration, FP32 CG vectors.
 MIXED = {"prec": "residual", "cg_fp32": True}

@@ -105,3 +105,45 @@ def test_exact_decomposition_rank_above_sides(env, orc):
             assert r <= 1.01e-10
             ok += 1
     assert ok >= 1
+
+
+def test_gn_step_large_rank_diag_damping(env, orc):
+    """The diagonal damping (Section 3.2) with the CG kernel's matrices in global
+    memory: R = 120 > s, one FP64 step at a fixed CG count against the oracle."""
+    torch, api, h = env
+    rng = np.random.default_rng(43)
+    dims, R, k = (30, 25, 20), 120, 3
+    A = [rng.standard_normal((s, R)) for s in dims]
+    X = rng.standard_normal(dims)
+    lam, lo, hi = 0.05, 1e-7, 0.1
+    Ad = _dev(torch, A)
+    params = api.gn_params(lam, lo, hi, eps_cg=0.0, cg_max_iter=k, reg="diag")
+    s, st = api.cp_gn_step(h, torch.from_numpy(X).cuda(), Ad, params)
+    Ao, lam_o, dir_o, so, sto = orc.gn_step(X, A, lam, 0, lo, hi, 2.0, 0.0, k, reg=orc.REG_DIAG)
+    assert s == sto == api.CP_WARN_CG_MAXIT and st["cg_iters"] == so["cg_iters"] == k
+    V = [a.cpu().numpy() - a0 for a, a0 in zip(Ad, A)]
+    Vo = [a - a0 for a, a0 in zip(Ao, A)]
+    assert _relerr(V, Vo) <= 1e-12
+    assert params.lam == lam_o and params.lam_dir == dir_o
+
+
+@pytest.mark.parametrize("cg_fp32", [False, True])
+def test_workspace_size_bounds_large_rank_step(env, cg_fp32):
+    """cp_workspace_size bounds what a fresh handle allocates for a GN step
+    whose CG keeps its matrices and rows in global memory (R = 150)."""
+    torch, api, h = env
+    rng = np.random.default_rng(44)
+    dims, R = (40, 35, 30), 150
+    X = torch.from_numpy(rng.standard_normal(dims)).cuda()
+    A = _dev(torch, [rng.standard_normal((s, R)) for s in dims])
+    bound = api.cp_workspace_size(h, X, R, "fp64")[0]
+    params = api.gn_params(1.0, 1e-6, 1.0, eps_cg=0.0, cg_max_iter=2, cg_fp32=cg_fp32)
+    api.cp_gn_step(h, X, [a.clone() for a in A], params)  # modules loaded
+    torch.cuda.synchronize()
+    h2 = api.Handle(0)
+    free0 = torch.cuda.mem_get_info()[0]
+    api.cp_gn_step(h2, X, A, params)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    h2.close()
+    assert used <= bound + 32 * (2 << 20), (used, bound)
