@@ -552,7 +552,10 @@ __global__ void __launch_bounds__(kThreads, 1) pcg_kernel(PcgArgs<T> a, int stag
         const T be = first ? (T)0 : (T)ratio;
         if (have0) {
             a.Yfull[e0] = fmadd(be, y0, acc0);
-            for (size_t e = e0 + estep; e < ny; e += estep) a.Yfull[e] = fmadd(be, a.Yfull[e], sum_partials(e));
+            // (at the first gather Y^(p)(W_old) does not exist yet: the buffer holds whatever an
+            // earlier call left there, so it is not read)
+            for (size_t e = e0 + estep; e < ny; e += estep)
+                a.Yfull[e] = first ? sum_partials(e) : fmadd(be, a.Yfull[e], sum_partials(e));
         }
     };
     if (ok) gather(0.0, true, rz, rsum);
