@@ -147,3 +147,27 @@ def test_workspace_size_bounds_large_rank_step(env, cg_fp32):
     used = free0 - torch.cuda.mem_get_info()[0]
     h2.close()
     assert used <= bound + 32 * (2 << 20), (used, bound)
+
+
+@pytest.mark.parametrize("cg_fp32,tol", [(False, 1e-12), (True, 1e-4)])
+def test_gn_step_one_row_per_block_fresh_handle(env, orc, cg_fp32, tol):
+    """R = 150 over 105 factor rows: one row per CG block, more Y entries than
+    gathering threads (several per thread), on a fresh handle whose buffers hold
+    whatever earlier allocations left: the step against the oracle's."""
+    torch, api, _ = env
+    rng = np.random.default_rng(45)
+    dims, R, k = (40, 35, 30), 150, 3
+    A = [rng.standard_normal((s, R)) for s in dims]
+    X = rng.standard_normal(dims)
+    hi, lo = orc.default_lambda(A)
+    h2 = api.Handle(0)
+    try:
+        Ad = _dev(torch, A)
+        params = api.gn_params(hi, lo, hi, eps_cg=0.0, cg_max_iter=k, cg_fp32=cg_fp32)
+        s, st = api.cp_gn_step(h2, torch.from_numpy(X).cuda(), Ad, params)
+    finally:
+        h2.close()
+    Ao, _, _, so, sto = orc.gn_step(X, A, hi, 0, lo, hi, 2.0, 0.0, k)
+    assert s == sto == api.CP_WARN_CG_MAXIT and st["cg_iters"] == k and st["cg_blocks"] == 105
+    V = [a.cpu().numpy() - a0 for a, a0 in zip(Ad, A)]
+    assert _relerr(V, [a - a0 for a, a0 in zip(Ao, A)]) <= tol
