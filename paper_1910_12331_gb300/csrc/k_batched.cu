@@ -61,41 +61,72 @@ struct BArgs {
     double target;
 };
 
-// Sum over the CTA of one double per thread (all threads call; result in every thread).
-template <int BT>
-__device__ __forceinline__ double bsum(double v, double* red) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double t = l < (BT / 32) ? red[l] : 0.0;
-    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    return t;
+// Sums over the CTA of up to four FP32 values per thread: error-free FP32 pairs within each warp
+// (Knuth's two-sum; the FP32 units, not GB300's slow FP64 pipe, do the thread-level work), then
+// FP64 across the warps in warp 0 alone (the shuffle levels that would only add zeros skipped),
+// which also forms the scalars the step needs from the sums: fin(r, lane) runs on every lane of
+// warp 0, lanes 0..3 holding the full sums, and lane 0's r comes back to every thread through
+// red[64..].  All threads call.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+// sqrt(r[0]) + sqrt(r[1]) + sqrt(r[2]), the three roots taken at once by lanes 0, 1 and 2 (a warp
+// instruction costs the FP64 pipe the same for one lane as for all); called by a whole warp.
+__device__ __forceinline__ double sqrt3_sum(const double (&r)[8], int l) {
+    const double sq = sqrt(l == 0 ? r[0] : (l == 1 ? r[1] : r[2]));
+    return (__shfl_sync(0xffffffffu, sq, 0) + __shfl_sync(0xffffffffu, sq, 1)) + __shfl_sync(0xffffffffu, sq, 2);
 }
 
-// Three sums at once (all threads call).
-template <int BT>
-__device__ __forceinline__ void bsum3(double& a, double& b, double& c, double* red) {
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
+template <int BT, int K, typename Fin>
+__device__ __forceinline__ void bsum_k(const float (&v)[K], double* red, double (&out)[8], Fin fin) {
+    constexpr int NW = BT / 32;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
+    float h[K], lo[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        h[q] = v[q];
+        lo[q] = 0.f;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h[q], o), ol = __shfl_xor_sync(0xffffffffu, lo[q], o);
+            float t, e;
+            two_sum_f(h[q], oh, t, e);
+            h[q] = t;
+            lo[q] += ol + e;
+        }
+    }
+    __syncthreads();  // red may still be read from the previous reduction
     if (l == 0) {
-        red[w] = a;
-        red[(BT / 32) + w] = b;
-        red[2 * (BT / 32) + w] = c;
+#pragma unroll
+        for (int q = 0; q < K; ++q) red[q * NW + w] = (double)h[q] + (double)lo[q];
     }
     __syncthreads();
-    a = b = c = 0.0;
-    for (int k = 0; k < (BT / 32); ++k) {
-        a += red[k];
-        b += red[(BT / 32) + k];
-        c += red[2 * (BT / 32) + k];
+    if (w == 0) {
+        constexpr int P = NW <= 4 ? 4 : (NW <= 8 ? 8 : (NW <= 16 ? 16 : 32));  // lanes >= NW hold zeros
+        double t[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            t[q] = l < NW ? red[q * NW + l] : 0.0;
+#pragma unroll
+            for (int o = P / 2; o; o >>= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+        }
+        double r[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) r[q] = q < K ? t[q] : 0.0;
+        fin(r, l);
+        if (l == 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[64 + q] = r[q];
+        }
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q] = red[64 + q];
 }
 
 struct Smem {
@@ -105,9 +136,13 @@ struct Smem {
     double *gj, *red;               // R^2 + R, 96
 };
 
+// v[n] for a run-time n by selects, so that the arrays of Smem stay in registers
+__device__ __forceinline__ int pick3(const int (&v)[3], int n) { return n == 0 ? v[0] : (n == 1 ? v[1] : v[2]); }
+
 __device__ __forceinline__ void carve(Smem& m, unsigned char* base, const BProb& pb) {
     m.R = pb.R;
     m.roff[0] = 0;
+#pragma unroll
     for (int n = 0; n < 3; ++n) {
         m.s[n] = pb.s[n];
         if (n) m.roff[n] = m.roff[n - 1] + pb.s[n - 1];
@@ -137,9 +172,10 @@ __device__ __forceinline__ void gram_gamma(const Smem& m) {
     const int R = m.R, RR = R * R;
     for (int e = threadIdx.x; e < 3 * RR; e += BT) {
         const int n = e / RR, r = (e % RR) / R, z = e % R;
-        const float* a = m.A + m.roff[n] * R;
+        const float* a = m.A + pick3(m.roff, n) * R;
         float acc = 0.f;
-        for (int i = 0; i < m.s[n]; ++i) acc = fmaf(a[i * R + r], a[i * R + z], acc);
+#pragma unroll 4
+        for (int i = 0; i < pick3(m.s, n); ++i) acc = fmaf(a[i * R + r], a[i * R + z], acc);
         m.Sg[e] = acc;
     }
     __syncthreads();
@@ -155,111 +191,348 @@ __device__ __forceinline__ void gram_gamma(const Smem& m) {
     __syncthreads();
 }
 
-// sum_k x[k] a[k][r] with four independent partial sums
-__device__ __forceinline__ float dot_k(const float* __restrict__ x, const float* a, int R, int r, int n) {
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-    int k = 0;
-    for (; k + 3 < n; k += 4) {
-        t0 = fmaf(__ldg(x + k), a[k * R + r], t0);
-        t1 = fmaf(__ldg(x + k + 1), a[(k + 1) * R + r], t1);
-        t2 = fmaf(__ldg(x + k + 2), a[(k + 2) * R + r], t2);
-        t3 = fmaf(__ldg(x + k + 3), a[(k + 3) * R + r], t3);
+// ---- The three MTTKRPs and the residual with the lanes of a warp over k, the contiguous index
+// of X: rows x[i, j, :] are read coalesced, and the loads of successive rows do not depend on each
+// other, so several are in flight per warp (X is read from global memory, where a warp that waits
+// for one load at a time is bound by the memory latency).  Accumulators over the ranks live in
+// registers, MR >= R of them (a template bucket: 8, 16, 24 or 32).
+
+// Mode 1 (mode = 0) or mode 2 (mode = 1), one warp per pair of output rows q, q + 1:
+//   M1[q][r] = sum_k a3[k][r] sum_j x[q, j, k] a2[j][r],  M2[q][r] = sum_k a3[k][r] sum_i x[i, q, k] a1[i][r];
+// the inner sums per lane (its k; each factor value loaded serves both rows), then a3[k][r] times
+// them summed over the lanes by shuffles; lane r keeps the sum for rank r.
+template <int BT, int MR>
+__device__ __forceinline__ void mttkrp_m12(const Smem& m, const float* __restrict__ X, float* out, int mode) {
+    const int R = m.R, s1 = m.s[0], s2 = m.s[1], s3 = m.s[2];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const float *a1 = m.A, *a2 = m.A + m.roff[1] * R, *a3t = out + m.roff[2] * R;  // a3t[r][k] = a3[k][r]
+    const int nrow = mode == 0 ? s1 : s2, nin = mode == 0 ? s2 : s1;
+    const float* fac = mode == 0 ? a2 : a1;
+    const int64_t step = mode == 0 ? (int64_t)s3 : (int64_t)s2 * s3;  // X distance of successive summed rows
+    const int64_t qstep = mode == 0 ? (int64_t)s2 * s3 : (int64_t)s3;  // X distance of successive output rows
+    for (int q = 2 * w; q < nrow; q += 2 * (BT / 32)) {
+        const bool two = q + 1 < nrow;
+        const float* xq = X + q * qstep;
+        const float* xq1 = two ? xq + qstep : xq;
+        float mine0 = 0.f, mine1 = 0.f;
+        for (int k0 = 0; k0 < s3; k0 += 32) {
+            const int k = k0 + l;
+            const bool kon = k < s3;
+            float t0[MR], t1[MR];
+#pragma unroll
+            for (int r = 0; r < MR; ++r) t0[r] = t1[r] = 0.f;
+#pragma unroll (BT > 256 ? 4 : 8)
+            for (int pp = 0; pp < nin; ++pp) {
+                const float x0 = kon ? __ldg(xq + pp * step + k) : 0.f;
+                const float x1 = kon ? __ldg(xq1 + pp * step + k) : 0.f;
+                const float* fr = fac + pp * R;
+#pragma unroll
+                for (int r = 0; r < MR; ++r)
+                    if (r < R) {
+                        const float f = fr[r];
+                        t0[r] = fmaf(x0, f, t0[r]);
+                        t1[r] = fmaf(x1, f, t1[r]);
+                    }
+            }
+            const int kc = kon ? k : 0;
+#pragma unroll
+            for (int r = 0; r < MR; ++r) {
+                if (r < R) {
+                    const float c = a3t[r * s3 + kc];
+                    float v0 = kon ? t0[r] * c : 0.f, v1 = kon ? t1[r] * c : 0.f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                    }
+                    if (l == r) {
+                        mine0 += v0;
+                        mine1 += v1;
+                    }
+                }
+            }
+        }
+        if (l < R) {
+            out[(pick3(m.roff, mode) + q) * R + l] = mine0;
+            if (two) out[(pick3(m.roff, mode) + q + 1) * R + l] = mine1;
+        }
     }
-    for (; k < n; ++k) t0 = fmaf(__ldg(x + k), a[k * R + r], t0);
-    return (t0 + t1) + (t2 + t3);
 }
 
-// M^(n) for all modes into out (S x R): warps own rows of mode n, lanes own rank columns.
-template <int BT>
-__device__ __forceinline__ void mttkrp3(const Smem& m, const float* __restrict__ X, float* out) {
+// Mode 3: M3[k][r] = sum_i a1[i][r] sum_j x[i, j, k] a2[j][r], lane = k, two rows i at a time (each
+// factor value loaded serves both); the rows i split over up to four groups of warps whose partials
+// (in W .. V, free at this point of the iteration) are added in a fixed order.
+template <int BT, int MR>
+__device__ __forceinline__ void mttkrp_m3(const Smem& m, const float* __restrict__ X, float* out) {
     const int R = m.R, s1 = m.s[0], s2 = m.s[1], s3 = m.s[2];
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
-    const bool on = r < R;
-    const int rr = on ? r : 0;
-    const float *a1 = m.A, *a2 = m.A + m.roff[1] * R, *a3 = m.A + m.roff[2] * R;
-    // mode 1: M[i][r] = sum_j a2[j][r] sum_k X[i,j,k] a3[k][r]
-    for (int i = w; i < s1; i += (BT / 32)) {
-        float acc = 0.f;
-        for (int j = 0; j < s2; ++j) {
-            const float* x = X + ((int64_t)i * s2 + j) * s3;
-            acc = fmaf(dot_k(x, a3, R, rr, s3), a2[j * R + rr], acc);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const float *a1 = m.A, *a2 = m.A + m.roff[1] * R;
+    const int nkb = (s3 + 31) / 32;
+    const int ig_n = max(1, min(4, (BT / 32) / nkb));
+    const int64_t istep = (int64_t)s2 * s3;
+    for (int task = w; task < nkb * ig_n; task += BT / 32) {
+        const int kb = task % nkb, ig = task / nkb;
+        const int k = kb * 32 + l;
+        const bool kon = k < s3;
+        const int i0 = (int)((int64_t)s1 * ig / ig_n), i1 = (int)((int64_t)s1 * (ig + 1) / ig_n);
+        float acc[MR];
+#pragma unroll
+        for (int r = 0; r < MR; ++r) acc[r] = 0.f;
+        for (int i = i0; i < i1; i += 2) {
+            const bool two = i + 1 < i1;
+            const float* xi = X + i * istep + (kon ? k : 0);
+            const float* xi1 = two ? xi + istep : xi;
+            float t0[MR], t1[MR];
+#pragma unroll
+            for (int r = 0; r < MR; ++r) t0[r] = t1[r] = 0.f;
+#pragma unroll (BT > 256 ? 4 : 8)
+            for (int j = 0; j < s2; ++j) {
+                const float x0 = kon ? __ldg(xi + (int64_t)j * s3) : 0.f;
+                const float x1 = kon ? __ldg(xi1 + (int64_t)j * s3) : 0.f;
+                const float* fr = a2 + j * R;
+#pragma unroll
+                for (int r = 0; r < MR; ++r)
+                    if (r < R) {
+                        const float f = fr[r];
+                        t0[r] = fmaf(x0, f, t0[r]);
+                        t1[r] = fmaf(x1, f, t1[r]);
+                    }
+            }
+            const float* fa = a1 + i * R;
+            const float* fb = a1 + (two ? i + 1 : i) * R;
+#pragma unroll
+            for (int r = 0; r < MR; ++r)
+                if (r < R) {
+                    acc[r] = fmaf(fa[r], t0[r], acc[r]);
+                    if (two) acc[r] = fmaf(fb[r], t1[r], acc[r]);
+                }
         }
-        if (on) out[i * R + r] = acc;
-    }
-    // mode 2: M[j][r] = sum_i a1[i][r] sum_k X[i,j,k] a3[k][r]
-    for (int j = w; j < s2; j += (BT / 32)) {
-        float acc = 0.f;
-        for (int i = 0; i < s1; ++i) {
-            const float* x = X + ((int64_t)i * s2 + j) * s3;
-            acc = fmaf(dot_k(x, a3, R, rr, s3), a1[i * R + rr], acc);
+        float* part = m.W + (size_t)ig * s3 * R;
+        if (kon) {
+#pragma unroll
+            for (int r = 0; r < MR; ++r)
+                if (r < R) part[k * R + r] = acc[r];
         }
-        if (on) out[(m.roff[1] + j) * R + r] = acc;
     }
-    // mode 3: M[k][r] = sum_i a1[i][r] sum_j X[i,j,k] a2[j][r]
-    for (int k = w; k < s3; k += (BT / 32)) {
-        float acc = 0.f;
-        for (int i = 0; i < s1; ++i) {
-            const float* x = X + (int64_t)i * s2 * s3 + k;
-            float t = 0.f;
-            for (int j = 0; j < s2; ++j) t = fmaf(__ldg(x + (int64_t)j * s3), a2[j * R + rr], t);
-            acc = fmaf(t, a1[i * R + rr], acc);
+    __syncthreads();
+    for (int e = threadIdx.x; e < s3 * R; e += BT) {
+        float v = 0.f;
+        for (int g = 0; g < ig_n; ++g) v += m.W[(size_t)g * s3 * R + e];
+        out[m.roff[2] * R + e] = v;
+    }
+}
+
+// M^(n) for all modes into out (S x R).
+template <int BT, int MR>
+__device__ __forceinline__ void mttkrp3_r(const Smem& m, const float* __restrict__ X, float* out) {
+    {  // a3 transposed (R x s3) for modes 1 and 2, in the rows of mode 3 of out, which mode 3 writes last
+        const int R = m.R, s3 = m.s[2];
+        float* a3t = out + m.roff[2] * R;
+        for (int e = threadIdx.x; e < s3 * R; e += BT) {
+            const int k = e / R, r = e - k * R;
+            a3t[r * s3 + k] = m.A[m.roff[2] * R + e];
         }
-        if (on) out[(m.roff[2] + k) * R + r] = acc;
+        __syncthreads();
     }
+    mttkrp_m12<BT, MR>(m, X, out, 0);
+    mttkrp_m12<BT, MR>(m, X, out, 1);
+    mttkrp_m3<BT, MR>(m, X, out);
     __syncthreads();
 }
 
-// ||X - [[A]]||_F^2: a warp per row (i, j), lanes over k; compensated FP32 partials, FP64 across threads.
 template <int BT>
-__device__ __forceinline__ double resid2(const Smem& m, const float* __restrict__ X) {
-    const int R = m.R, s1 = m.s[0], s2 = m.s[1], s3 = m.s[2];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const float *a1 = m.A, *a2 = m.A + m.roff[1] * R, *a3 = m.A + m.roff[2] * R;
-    float sum = 0.f, comp = 0.f;
-    for (int ij = w; ij < s1 * s2; ij += (BT / 32)) {
-        const int i = ij / s2, j = ij % s2;
-        const float* x = X + (int64_t)ij * s3;
-        for (int k = l; k < s3; k += 32) {
-            float rec = 0.f;
-            for (int r = 0; r < R; ++r) rec = fmaf(a1[i * R + r] * a2[j * R + r], a3[k * R + r], rec);
-            const float e = __ldg(x + k) - rec;
-            const float y = fmaf(e, e, -comp);  // Kahan
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
-        }
-    }
-    return bsum<BT>((double)sum - (double)comp, m.red);
+__device__ __forceinline__ void mttkrp3(const Smem& m, const float* __restrict__ X, float* out) {
+    if (m.R <= 8)
+        mttkrp3_r<BT, 8>(m, X, out);
+    else if (m.R <= 16)
+        mttkrp3_r<BT, 16>(m, X, out);
+    else if (m.R <= 24)
+        mttkrp3_r<BT, 24>(m, X, out);
+    else
+        mttkrp3_r<BT, 32>(m, X, out);
 }
 
-// out = in P_inv^(n) per mode (rows of mode n times the symmetric R x R block)
+// ||X - [[A]]||_F^2: a warp per row (i, j), lanes over k; compensated FP32 partials, FP64 across
+// threads.  A lane's values of x in a row (up to eight) are loaded before any is used, and the
+// products a1[i][r] a2[j][r] of the row are formed once, in registers.
+template <int BT, int MR>
+__device__ __forceinline__ double resid2_r(const Smem& m, const float* __restrict__ X) {
+    const int R = m.R, s1 = m.s[0], s2 = m.s[1], s3 = m.s[2];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const float *a1 = m.A, *a2 = m.A + m.roff[1] * R;
+    // a3 transposed (R x s3) into the mode-3 rows of Q, free where the residual is taken: the lanes
+    // (successive k) then read successive words, free of the bank conflicts of a3[k][r]
+    float* a3t = m.Q + m.roff[2] * R;
+    for (int e = threadIdx.x; e < s3 * R; e += BT) {
+        const int k = e / R, r = e - k * R;
+        a3t[r * s3 + k] = m.A[m.roff[2] * R + e];
+    }
+    __syncthreads();
+    float sum = 0.f, comp = 0.f;
+    // the next row's values of x are loaded while this row is reconstructed
+    float xn[8];
+    auto load = [&](int ij) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            xn[u] = ij < s1 * s2 && l + 32 * u < s3 ? __ldg(X + (int64_t)ij * s3 + l + 32 * u) : 0.f;
+    };
+    load(w);
+    for (int ij = w; ij < s1 * s2; ij += (BT / 32)) {
+        const int i = ij / s2, j = ij % s2;
+        float xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = xn[u];
+        load(ij + (BT / 32));
+        float wr[MR];
+#pragma unroll
+        for (int r = 0; r < MR; ++r) wr[r] = r < R ? a1[i * R + r] * a2[j * R + r] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = l + 32 * u;
+            if (k < s3) {
+                float rec = 0.f;
+#pragma unroll
+                for (int r = 0; r < MR; ++r)
+                    if (r < R) rec = fmaf(wr[r], a3t[r * s3 + k], rec);
+                const float e = xv[u] - rec;
+                const float y = fmaf(e, e, -comp);  // Kahan
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            }
+        }
+    }
+    const float v[2] = {sum, -comp};
+    double o[8];
+    bsum_k<BT, 2>(v, m.red, o, [](double (&r)[8], int) { r[0] += r[1]; });
+    return o[0];
+}
+
+template <int BT>
+__device__ __forceinline__ double resid2(const Smem& m, const float* __restrict__ X) {
+    if (m.R <= 8) return resid2_r<BT, 8>(m, X);
+    if (m.R <= 16) return resid2_r<BT, 16>(m, X);
+    if (m.R <= 24) return resid2_r<BT, 24>(m, X);
+    return resid2_r<BT, 32>(m, X);
+}
+
+// Row products of the CG in register tiles: a thread forms 4 rows (of one mode) x 2 columns
+// (z and z + ch, ch = ceil(R/2)) of the S x R result, so that each value it loads from shared
+// memory serves 2 or 4 multiply-adds.  Every output element keeps its own accumulation chain.
+struct RowTile {
+    int n, row0, nr, z0, z1;  // mode, first row, rows in the tile (1..4), columns (z1 = z0 if none)
+    bool z1on;
+};
+__device__ __forceinline__ int tiles_of(const Smem& m) {
+    const int ch = (m.R + 1) >> 1;
+    return (((m.s[0] + 3) >> 2) + ((m.s[1] + 3) >> 2) + ((m.s[2] + 3) >> 2)) * ch;
+}
+__device__ __forceinline__ RowTile tile_at(const Smem& m, int t) {
+    const int ch = (m.R + 1) >> 1;
+    const int t0 = ((m.s[0] + 3) >> 2) * ch, t1 = t0 + ((m.s[1] + 3) >> 2) * ch;
+    RowTile o;
+    o.n = t >= t1 ? 2 : (t >= t0 ? 1 : 0);
+    const int tl = t - (o.n == 2 ? t1 : (o.n == 1 ? t0 : 0));
+    const int rt = tl / ch, ct = tl - rt * ch;
+    o.row0 = pick3(m.roff, o.n) + 4 * rt;
+    o.nr = min(4, pick3(m.s, o.n) - 4 * rt);
+    o.z0 = ct;
+    o.z1on = ct + ch < m.R;
+    o.z1 = o.z1on ? ct + ch : ct;
+    return o;
+}
+
+// out = in P_inv^(n) per mode (rows of mode n times the symmetric R x R block); per element two
+// chains, even and odd r.
 template <int BT>
 __device__ __forceinline__ void apply_pinv(const Smem& m, const float* in, float* out) {
-    const int R = m.R, SR = m.S * R;
-    for (int e = threadIdx.x; e < SR; e += BT) {
-        const int row = e / R, z = e % R;
-        const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
-        const float* P = m.Pi + n * R * R;
-        const float* x = in + row * R;
-        float acc = 0.f;
-        for (int r = 0; r < R; ++r) acc = fmaf(x[r], P[r * R + z], acc);
-        out[e] = acc;
+    const int R = m.R, nt = tiles_of(m);
+    for (int t = threadIdx.x; t < nt; t += BT) {
+        const RowTile tl = tile_at(m, t);
+        const float* P = m.Pi + tl.n * R * R;
+        const float* x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = in + (tl.row0 + min(k, tl.nr - 1)) * R;
+        float e0[4][2], e1[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e0[k][0] = e0[k][1] = e1[k][0] = e1[k][1] = 0.f;
+        int r = 0;
+        for (; r + 1 < R; r += 2) {
+            const float pa0 = P[r * R + tl.z0], pa1 = P[r * R + tl.z1];
+            const float pb0 = P[(r + 1) * R + tl.z0], pb1 = P[(r + 1) * R + tl.z1];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float xa = x[k][r], xb = x[k][r + 1];
+                e0[k][0] = fmaf(xa, pa0, e0[k][0]);
+                e0[k][1] = fmaf(xa, pa1, e0[k][1]);
+                e1[k][0] = fmaf(xb, pb0, e1[k][0]);
+                e1[k][1] = fmaf(xb, pb1, e1[k][1]);
+            }
+        }
+        if (r < R) {
+            const float pa0 = P[r * R + tl.z0], pa1 = P[r * R + tl.z1];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                e0[k][0] = fmaf(x[k][r], pa0, e0[k][0]);
+                e0[k][1] = fmaf(x[k][r], pa1, e0[k][1]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < tl.nr) {
+                out[(tl.row0 + k) * R + tl.z0] = e0[k][0] + e1[k][0];
+                if (tl.z1on) out[(tl.row0 + k) * R + tl.z1] = e0[k][1] + e1[k][1];
+            }
     }
     __syncthreads();
 }
 
 // Q = (J^T J + lam D) W via Y^(p) = A^(p)^T W^(p), T^(n) = sum_{p != n} Gamma^(n,p) * Y^(p),
 // Q^(n) = lam W^(n) D^(n) + W^(n) Gamma^(n,n) + A^(n) T^(n)^T, D^(n) = I or diag(Gamma^(n,n)).
+// Y and T are kept transposed (Yb[p][r][z] = Y^(p)[z][r], Tb[n][r][z] = T^(n)[z][r]; the blocks
+// Gamma^(n,p) are symmetric), so that the tiled Q reads A^(n) T^(n)^T's right factor by rows.
 template <int BT>
 __device__ __forceinline__ void matvec(const Smem& m, float lam, bool diag) {
-    const int R = m.R, RR = R * R, SR = m.S * R;
-    for (int e = threadIdx.x; e < 3 * RR; e += BT) {
-        const int p = e / RR, r = (e % RR) / R, z = e % R;
-        const float* a = m.A + m.roff[p] * R;
-        const float* w = m.W + m.roff[p] * R;
-        float acc = 0.f;
-        for (int i = 0; i < m.s[p]; ++i) acc = fmaf(a[i * R + r], w[i * R + z], acc);
-        m.Yb[e] = acc;
+    const int R = m.R, RR = R * R;
+    {  // a thread forms Yb[p][r][z] for r in {r0, r0 + ch}, z in {z0, z0 + ch}, ch = ceil(R/2)
+        const int ch = (R + 1) >> 1, cc = ch * ch;
+        for (int t = threadIdx.x; t < 3 * cc; t += BT) {
+            const int p = t / cc, tr = t - p * cc, rr = tr / ch, zz = tr - rr * ch;
+            const bool r1on = rr + ch < R, z1on = zz + ch < R;
+            const int r0 = rr, r1 = r1on ? rr + ch : rr, z0 = zz, z1 = z1on ? zz + ch : zz;
+            const float* a = m.A + pick3(m.roff, p) * R;
+            const float* w = m.W + pick3(m.roff, p) * R;
+            float c0[4], c1[4];  // (r0,z0) (r0,z1) (r1,z0) (r1,z1); two chains each (even and odd i)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c0[u] = c1[u] = 0.f;
+            const int sp = pick3(m.s, p);
+            int i = 0;
+            for (; i + 1 < sp; i += 2) {
+                const float az0 = a[i * R + z0], az1 = a[i * R + z1], w0 = w[i * R + r0], w1 = w[i * R + r1];
+                const float bz0 = a[(i + 1) * R + z0], bz1 = a[(i + 1) * R + z1];
+                const float v0 = w[(i + 1) * R + r0], v1 = w[(i + 1) * R + r1];
+                c0[0] = fmaf(az0, w0, c0[0]);
+                c0[1] = fmaf(az1, w0, c0[1]);
+                c0[2] = fmaf(az0, w1, c0[2]);
+                c0[3] = fmaf(az1, w1, c0[3]);
+                c1[0] = fmaf(bz0, v0, c1[0]);
+                c1[1] = fmaf(bz1, v0, c1[1]);
+                c1[2] = fmaf(bz0, v1, c1[2]);
+                c1[3] = fmaf(bz1, v1, c1[3]);
+            }
+            if (i < sp) {
+                const float az0 = a[i * R + z0], az1 = a[i * R + z1], w0 = w[i * R + r0], w1 = w[i * R + r1];
+                c0[0] = fmaf(az0, w0, c0[0]);
+                c0[1] = fmaf(az1, w0, c0[1]);
+                c0[2] = fmaf(az0, w1, c0[2]);
+                c0[3] = fmaf(az1, w1, c0[3]);
+            }
+            float* y = m.Yb + p * RR;
+            y[r0 * R + z0] = c0[0] + c1[0];
+            if (z1on) y[r0 * R + z1] = c0[1] + c1[1];
+            if (r1on) y[r1 * R + z0] = c0[2] + c1[2];
+            if (r1on && z1on) y[r1 * R + z1] = c0[3] + c1[3];
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 3 * RR; e += BT) {
@@ -270,19 +543,46 @@ __device__ __forceinline__ void matvec(const Smem& m, float lam, bool diag) {
         m.Tb[e] = t;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < SR; e += BT) {
-        const int row = e / R, z = e % R;
-        const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
-        const float* G = m.Gm + (n * 3 + n) * RR;
-        const float* T = m.Tb + n * RR;
-        const float* w = m.W + row * R;
-        const float* a = m.A + row * R;
-        float acc = (diag ? lam * G[z * R + z] : lam) * w[z];
-        for (int r = 0; r < R; ++r) {
-            acc = fmaf(w[r], G[r * R + z], acc);
-            acc = fmaf(a[r], T[z * R + r], acc);
+    const int nt = tiles_of(m);
+    for (int t = threadIdx.x; t < nt; t += BT) {
+        const RowTile tl = tile_at(m, t);
+        const float* G = m.Gm + (tl.n * 3 + tl.n) * RR;
+        const float* T = m.Tb + tl.n * RR;
+        const float* w[4];
+        const float* a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int row = tl.row0 + min(k, tl.nr - 1);
+            w[k] = m.W + row * R;
+            a[k] = m.A + row * R;
         }
-        m.Q[e] = acc;
+        const float d0 = diag ? lam * G[tl.z0 * R + tl.z0] : lam, d1 = diag ? lam * G[tl.z1 * R + tl.z1] : lam;
+        float c1[4][2], c2[4][2];  // W Gamma + lam D W and A T^T: two chains per element
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c1[k][0] = d0 * w[k][tl.z0];
+            c1[k][1] = d1 * w[k][tl.z1];
+            c2[k][0] = c2[k][1] = 0.f;
+        }
+#pragma unroll 2
+        for (int r = 0; r < R; ++r) {
+            const float g0 = G[r * R + tl.z0], g1 = G[r * R + tl.z1];
+            const float t0 = T[r * R + tl.z0], t1 = T[r * R + tl.z1];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float wv = w[k][r], av = a[k][r];
+                c1[k][0] = fmaf(wv, g0, c1[k][0]);
+                c1[k][1] = fmaf(wv, g1, c1[k][1]);
+                c2[k][0] = fmaf(av, t0, c2[k][0]);
+                c2[k][1] = fmaf(av, t1, c2[k][1]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < tl.nr) {
+                m.Q[(tl.row0 + k) * R + tl.z0] = c1[k][0] + c2[k][0];
+                if (tl.z1on) m.Q[(tl.row0 + k) * R + tl.z1] = c1[k][1] + c2[k][1];
+            }
     }
     __syncthreads();
 }
@@ -347,7 +647,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
         for (int e = threadIdx.x; e < SR; e += BT) {
             const int row = e / R, r = e % R;
             const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
-            m.A[e] = (float)pb.A[n][(row - m.roff[n]) * R + r];
+            m.A[e] = (float)pb.A[n][(row - pick3(m.roff, n)) * R + r];
         }
         // ||X||^2
         float xs = 0.f;
@@ -356,7 +656,13 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
             const float x = __ldg(X + e);
             xs = fmaf(x, x, xs);
         }
-        const double nx2 = bsum<BT>((double)xs, m.red);
+        double nx2;
+        {
+            const float v[1] = {xs};
+            double o[8];
+            bsum_k<BT, 1>(v, m.red, o, [](double (&)[8], int) {});
+            nx2 = o[0];
+        }
         double lam = pb.lam;
         const bool diag = pb.reg == CP_REG_DIAG;
         int dir = 0, status = CP_OK, it = 0, cg_total = 0, converged = 0, breakdowns = 0, backtracks = 0;
@@ -397,6 +703,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                 const float* G = m.Gm + (n * 3 + n) * R * R;
                 const float* a = m.A + row * R;
                 float acc = m.Q[e];
+#pragma unroll 4
                 for (int r = 0; r < R; ++r) acc = fmaf(-a[r], G[r * R + z], acc);
                 m.Rv[e] = acc;
                 m.V[e] = 0.f;
@@ -405,9 +712,13 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                 else if (n == 1) g1 += sq;
                 else g2 += sq;
             }
-            double ga = g0, gb = g1, gc = g2;
-            bsum3<BT>(ga, gb, gc, m.red);
-            const double gsum = sqrt(ga) + sqrt(gb) + sqrt(gc);
+            double gsum;
+            {
+                const float v[3] = {g0, g1, g2};
+                double o[8];
+                bsum_k<BT, 3>(v, m.red, o, [](double (&r)[8], int l) { r[3] = sqrt3_sum(r, l); });
+                gsum = o[3];
+            }
             if (!(gsum == gsum) || isinf(gsum)) {
                 status = CP_ERR_NONFINITE;
                 break;
@@ -422,7 +733,13 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                 m.W[e] = m.Z[e];
                 rzp = fmaf(m.Rv[e], m.Z[e], rzp);
             }
-            double rz = bsum<BT>((double)rzp, m.red);
+            double rz;
+            {
+                const float v[1] = {rzp};
+                double o[8];
+                bsum_k<BT, 1>(v, m.red, o, [](double (&)[8], int) {});
+                rz = o[0];
+            }
             double rnorm = gsum;
             double arz = 0.0;  // sum_k alpha_k <R_k, Z_k> = <-G, V> (PCG from V = 0)
             int k = 0;
@@ -430,12 +747,17 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                 matvec<BT>(m, (float)lam, diag);
                 float wqp = 0.f;
                 for (int e = threadIdx.x; e < SR; e += BT) wqp = fmaf(m.W[e], m.Q[e], wqp);
-                const double wq = bsum<BT>((double)wqp, m.red);
+                double o[8];
+                {
+                    const float v[1] = {wqp};
+                    bsum_k<BT, 1>(v, m.red, o, [rz](double (&r)[8], int) { r[1] = r[0] > 0.0 ? rz / r[0] : 0.0; });
+                }
+                const double wq = o[0];
                 if (!(wq > 0.0)) {  // FP32 curvature lost: end CG with the update found so far
                     ++breakdowns;
                     break;
                 }
-                const float alpha = (float)(rz / wq);
+                const float alpha = (float)o[1];
                 arz += (double)alpha * rz;
                 for (int e = threadIdx.x; e < SR; e += BT) {
                     m.V[e] = fmaf(alpha, m.W[e], m.V[e]);
@@ -452,11 +774,16 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                     else if (row >= m.roff[1]) q1 = fmaf(rv, rv, q1);
                     else q0 = fmaf(rv, rv, q0);
                 }
-                double ra = q0, rb = q1, rzd = rzn;
-                bsum3<BT>(ra, rb, rzd, m.red);
-                const double rc = bsum<BT>((double)q2, m.red);
-                rnorm = sqrt(ra) + sqrt(rb) + sqrt(rc);
-                const float beta = (float)(rzd / rz);
+                {
+                    const float v[4] = {q0, q1, q2, rzn};
+                    bsum_k<BT, 4>(v, m.red, o, [rz](double (&r)[8], int l) {
+                        r[4] = sqrt3_sum(r, l);
+                        r[5] = r[3] / rz;
+                    });
+                }
+                const double rzd = o[3];
+                rnorm = o[4];
+                const float beta = (float)o[5];
                 rz = rzd;
                 for (int e = threadIdx.x; e < SR; e += BT) m.W[e] = fmaf(beta, m.W[e], m.Z[e]);
                 __syncthreads();
@@ -477,7 +804,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
                     for (int e = threadIdx.x; e < SR; e += BT) {
                         const int row = e / R, r = e % R;
                         const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
-                        m.A[e] = (float)(pb.A[n][(row - m.roff[n]) * R + r] + t * (double)m.V[e]);
+                        m.A[e] = (float)(pb.A[n][(row - pick3(m.roff, n)) * R + r] + t * (double)m.V[e]);
                     }
                     __syncthreads();
                     if (0.5 * fmax(resid2<BT>(m, X), 0.0) <= f0 + pb.armijo_c * t * slope + tol_f) {
@@ -491,7 +818,7 @@ __global__ void __launch_bounds__(BT, 1) batched_gn_kernel(BArgs args) {
             for (int e = threadIdx.x; e < SR; e += BT) {
                 const int row = e / R, r = e % R;
                 const int n = row >= m.roff[2] ? 2 : (row >= m.roff[1] ? 1 : 0);
-                double* a = pb.A[n] + (row - m.roff[n]) * R + r;
+                double* a = pb.A[n] + (row - pick3(m.roff, n)) * R + r;
                 const double v = *a + step * (double)m.V[e];
                 *a = v;
                 m.A[e] = (float)v;
