@@ -379,6 +379,10 @@ def batched_timing(dev, count=512):
             "cg_iters_mean": float(np.mean([r["cg_iters_total"] for r in res])),
             "cg_breakdowns": sum(r["cg_breakdowns"] for r in res),
             "status_counts": {str(k): sum(1 for r in res if r["status"] == k) for k in sorted({r["status"] for r in res})},
+            # without step-size control a GN step can overshoot; a problem whose factors then grow until a
+            # pivot of the preconditioner's factorisation is no longer positive ends with CP_ERR_NOT_SPD (5)
+            "not_converged": [{"problem": i, "status": r["status"], "iters": r["iters"],
+                               "rel_residual": r["rel_residual"]} for i, r in enumerate(res) if not r["converged"]],
             "launches": 1, "graph": "one captured plan launch, replayed", "threads_per_cta": threads,
             "problem_order": ["given", "largest work first"][order], "autotune_s": tune_s,
             "with_armijo": armijo}
