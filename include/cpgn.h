@@ -429,7 +429,11 @@ cp_status cp_gn_solve_batched(cp_handle h, int nprob, const cp_batch_problem* pr
  * and the results).  cp_batch_plan_results copies the results of the last
  * completed launch to `results` (host, nprob entries); synchronises.
  * cp_batch_plan_threads returns the block size in use, cp_batch_plan_order the
- * problem order (0: as given, 1: largest work first).  cp_batch_plan_destroy
+ * problem order (0: as given, 1: largest work first).  cp_batch_plan_configure
+ * sets both instead of the autotuner's or the default choice (threads 128, 256
+ * or 384, order 0 or 1; CP_ERR_ARG otherwise, CP_ERR_UNSUPPORTED if the block
+ * size cannot run with the plan's shared memory); it enqueues nothing and
+ * applies to later launches.  cp_batch_plan_destroy
  * frees the plan's device memory (after its launches have finished; the
  * caller's current device is kept) and the plan.  Errors: CP_ERR_ARG,
  * CP_ERR_UNSUPPORTED, CP_ERR_NOMEM, CP_ERR_CUDA. */
@@ -441,6 +445,7 @@ cp_status cp_batch_plan_launch(cp_handle h, cp_batch_plan plan);
 cp_status cp_batch_plan_results(cp_handle h, cp_batch_plan plan, cp_batch_result* results);
 cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads);
 cp_status cp_batch_plan_order(cp_batch_plan plan, int* order);
+cp_status cp_batch_plan_configure(cp_batch_plan plan, int threads, int order);
 cp_status cp_batch_plan_destroy(cp_batch_plan plan);
 
 /* ---------------------------------------------------------------------------

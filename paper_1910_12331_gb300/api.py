@@ -31,7 +31,7 @@ SYMBOLS = ("cp_status_string", "cp_create", "cp_destroy", "cp_set_stream", "cp_w
            "cp_mttkrp_all", "cp_gradient", "cp_gn_matvec", "cp_gn_step", "cp_gn_solve", "cp_als_sweep",
            "cp_residual", "cp_residual_sums", "cp_residual_tensor", "cp_hosvd", "cp_tucker_expand", "cp_gn_solve_batched", "cp_gn_matvec_noalloc",
            "cp_batch_plan_create", "cp_batch_plan_launch", "cp_batch_plan_results", "cp_batch_plan_threads", "cp_batch_plan_order",
-           "cp_batch_plan_destroy", "cp_probe_grid_barrier", "cp_probe_fp64_fma")
+           "cp_batch_plan_configure", "cp_batch_plan_destroy", "cp_probe_grid_barrier", "cp_probe_fp64_fma")
 
 
 class cp_desc(ctypes.Structure):
@@ -147,6 +147,7 @@ def load(build_if_missing: bool = False):
         L.cp_batch_plan_results.argtypes = [vp, vp, ctypes.POINTER(cp_batch_result)]
         L.cp_batch_plan_threads.argtypes = [vp, ctypes.POINTER(i)]
         L.cp_batch_plan_order.argtypes = [vp, ctypes.POINTER(i)]
+        L.cp_batch_plan_configure.argtypes = [vp, i, i]
         L.cp_batch_plan_destroy.argtypes = [vp]
         L.cp_probe_grid_barrier.argtypes = [i, i, i, i, ctypes.POINTER(d)]
         L.cp_probe_fp64_fma.argtypes = [i, ctypes.POINTER(d)]
@@ -578,6 +579,10 @@ class BatchPlan:
         o = ctypes.c_int()
         _check(load().cp_batch_plan_order(self.p, ctypes.byref(o)), "cp_batch_plan_order")
         return o.value
+
+    def configure(self, threads, order):
+        """Fix the block size (128, 256 or 384) and the problem order (0 or 1) of later launches."""
+        _check(load().cp_batch_plan_configure(self.p, int(threads), int(order)), "cp_batch_plan_configure")
 
     def launch(self):
         """Enqueue one solve of every problem on torch's current stream (no synchronisation)."""

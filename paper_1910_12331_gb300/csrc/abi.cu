@@ -829,6 +829,12 @@ cp_status cp_batch_plan_threads(cp_batch_plan plan, int* threads) {
     return CP_OK;
 }
 
+cp_status cp_batch_plan_configure(cp_batch_plan plan, int threads, int order) {
+    if (!plan) return CP_ERR_ARG;
+    DeviceGuard g(plan->device);
+    return batch_plan_configure(plan->p, threads, order);
+}
+
 cp_status cp_batch_plan_order(cp_batch_plan plan, int* order) {
     if (!plan || !order) return CP_ERR_ARG;
     *order = batch_plan_order(plan->p);

@@ -1086,6 +1086,20 @@ cp_status batch_plan_results(BatchPlan* pl, cudaStream_t stream, cp_batch_result
 }
 
 int batch_plan_threads(const BatchPlan* pl) { return pl->threads; }
+
+cp_status batch_plan_configure(BatchPlan* pl, int threads, int order) {
+    if ((threads != 128 && threads != 256 && threads != 384) || (order != 0 && order != 1)) return CP_ERR_ARG;
+    if (cudaSetDevice(pl->device) != cudaSuccess) {
+        cudaGetLastError();
+        return CP_ERR_CUDA;
+    }
+    const int g = grid_of(pl->device, threads, pl->smem, pl->nprob);
+    if (g < 1) return CP_ERR_UNSUPPORTED;
+    pl->threads = threads;
+    pl->order = order;
+    pl->grid = g;
+    return CP_OK;
+}
 int batch_plan_order(const BatchPlan* pl) { return pl->order; }
 
 void batch_plan_destroy(BatchPlan* pl) {

@@ -147,6 +147,7 @@ cp_status batch_plan_create(int device, cudaStream_t stream, int nprob, const cp
 cp_status batch_plan_launch(BatchPlan* pl, cudaStream_t stream);
 cp_status batch_plan_results(BatchPlan* pl, cudaStream_t stream, cp_batch_result* results);
 int batch_plan_threads(const BatchPlan* pl);
+cp_status batch_plan_configure(BatchPlan* pl, int threads, int order);
 int batch_plan_order(const BatchPlan* pl);
 void batch_plan_destroy(BatchPlan* pl);
 

@@ -78,6 +78,9 @@ def test_batch_plan_arguments_rejected_without_gpu(lib):
     lib.cp_batch_plan_threads.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     t = ctypes.c_int(-1)
     assert lib.cp_batch_plan_threads(None, ctypes.byref(t)) == 1 and t.value == -1
+    lib.cp_batch_plan_configure.restype = ctypes.c_int
+    lib.cp_batch_plan_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    assert lib.cp_batch_plan_configure(None, 256, 0) == 1
     lib.cp_batch_plan_destroy.restype = ctypes.c_int
     assert lib.cp_batch_plan_destroy(None) == 1
 

@@ -161,6 +161,53 @@ def test_plan_graph_replay(env, orc):
             assert torch.equal(a, b)
 
 
+# Shapes that reach every branch of the kernel: each register bucket of the rank sums (R <= 8, 16, 24, 32),
+# third sides from under one warp to eight warps' worth (256), odd row counts (the two-row MTTKRP's tail),
+# odd R (the register tiles' second column absent) and a rank above a side.
+_VARIANT_CASES = [((17, 23, 19), 4, 11), ((9, 5, 3), 2, 12), ((16, 17, 256), 16, 13), ((45, 33, 70), 21, 14),
+                  ((30, 31, 100), 28, 15), ((61, 20, 47), 13, 16), ((6, 40, 33), 9, 17)]
+
+
+@pytest.mark.parametrize("threads", [128, 256, 384])
+@pytest.mark.parametrize("order", [0, 1])
+def test_every_variant_matches_oracle(env, orc, threads, order):
+    """Each block size and problem order, fixed by cp_batch_plan_configure: one GN
+    iteration with exactly three CG iterations from the oracle's state, per problem
+    against the oracle's FP64 step (FP32 vectors, so an FP32-level bound)."""
+    torch, api, h = env
+    k = 3
+    data, probs = [], []
+    for dims, R, seed in _VARIANT_CASES:
+        p, q = _prob(torch, orc, dims, R, seed)
+        data.append(p)
+        probs.append(q)
+    plan = api.BatchPlan(h, probs, eps_cg=0.0, cg_max_iter=k, max_iters=1, target_residual=0.0, autotune=False)
+    plan.configure(threads, order)
+    assert plan.threads == threads and plan.order == order
+    plan.launch()
+    res = plan.results()
+    plan.close()
+    for p, q, r in zip(data, probs, res):
+        assert r["status"] == 0 and r["iters"] == 1 and r["cg_iters_total"] == k
+        A_ref, _, _, st, _ = orc.gn_step(p["X"], [a.copy() for a in p["init"]], q["lam"], 0, q["lam_lo"],
+                                         q["lam_hi"], 2.0, 0.0, k, 0, False)
+        for a, a0, b in zip(q["A"], p["init"], A_ref):
+            d_gpu = a.cpu().numpy() - a0
+            d_ref = b - a0
+            assert np.linalg.norm(d_gpu - d_ref) <= 2e-4 * np.linalg.norm(d_ref) + 1e-12
+
+
+def test_plan_configure_rejects_bad_arguments(env, orc):
+    torch, api, h = env
+    _, q = _prob(torch, orc, (8, 9, 10), 3, 5)
+    plan = api.BatchPlan(h, [q], eps_cg=1e-3, cg_max_iter=10, max_iters=2, target_residual=1e-6, autotune=False)
+    for threads, order in ((64, 0), (512, 0), (256, 2), (256, -1)):
+        with pytest.raises(api.CPError):
+            plan.configure(threads, order)
+    assert plan.threads == 256 and plan.order == 0
+    plan.close()
+
+
 def test_plan_autotune(env, orc):
     """The autotuner times the block sizes on a scratch copy of the factors:
     the caller's factors are untouched by plan creation, the pick is one of
