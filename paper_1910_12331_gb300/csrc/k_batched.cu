@@ -10,7 +10,8 @@
 // through Y^(p) = A^(p)^T W^(p)); CTA-local barriers only, no grid barrier.
 // Vectors, factors and Gram products are FP32 in shared memory; dot products,
 // norms, alpha, beta and the factor master copy are FP64 (per-thread FP32
-// partials of a few products, then an FP64 tree).  The stop test is the direct
+// partials, summed as error-free FP32 pairs within each warp, then in FP64
+// across the warps by one warp).  The stop test is the direct
 // relative residual ||X - [[A]]||_F / ||X||_F with FP32 reconstruction and
 // compensated FP32 partial sums, which resolves the target r <= 1e-6 of these
 // problems.
@@ -29,8 +30,8 @@
 namespace cpgn {
 namespace {
 
-// Threads per CTA: a template parameter (128, 256 or 384), chosen per plan by
-// the autotuner (or 256).  BW = warps per CTA.
+// Threads per CTA: a template parameter BT (128, 256 or 384), chosen per plan by
+// the autotuner, or set by cp_batch_plan_configure (default 256).
 constexpr size_t kBatchSmemMax = 220 * 1024;
 
 struct BProb {
@@ -352,9 +353,9 @@ __device__ __forceinline__ void mttkrp3(const Smem& m, const float* __restrict__
         mttkrp3_r<BT, 32>(m, X, out);
 }
 
-// ||X - [[A]]||_F^2: a warp per row (i, j), lanes over k; compensated FP32 partials, FP64 across
-// threads.  A lane's values of x in a row (up to eight) are loaded before any is used, and the
-// products a1[i][r] a2[j][r] of the row are formed once, in registers.
+// ||X - [[A]]||_F^2: a warp per row (i, j), lanes over k; compensated FP32 partials, then the block
+// sum.  A lane's values of x in a row (up to eight) are loaded while the previous row is
+// reconstructed, and the products a1[i][r] a2[j][r] of the row are formed once, in registers.
 template <int BT, int MR>
 __device__ __forceinline__ double resid2_r(const Smem& m, const float* __restrict__ X) {
     const int R = m.R, s1 = m.s[0], s2 = m.s[1], s3 = m.s[2];
