@@ -361,8 +361,10 @@ cp_status cp_tucker_expand(cp_handle h, int order, const int64_t* dims, const in
  * Many small independent order-3 problems (Algorithm 1 with Algorithm 2 per
  * problem) solved by one persistent kernel launch: each CTA takes problems
  * from a work counter and runs the whole Gauss-Newton iteration of one problem
- * in its shared memory (FP32 vectors, factors and Gram products; FP64 dot
- * products, CG scalars, preconditioner elimination and factor master copy).
+ * in its shared memory (FP32 vectors, factors and Gram products; dot products
+ * from per-thread FP32 partials summed error-free within each warp, then in
+ * FP64 across the warps; FP64 CG scalars, preconditioner elimination and
+ * factor master copy).
  * A problem stops when its direct relative residual ||X - [[A]]|| / ||X|| <=
  * target_residual (converged = 1), after max_iters GN iterations, or on an
  * error (its status).  lambda follows the varying rule of Section 3.2 from
@@ -392,7 +394,8 @@ typedef struct {
     int converged;         /* 1 if the residual target was met */
     int cg_breakdowns;     /* CG solves ended early because the FP32 curvature <W, Q W> was not
                               positive (the update found so far is applied) */
-    double rel_residual;   /* last residual evaluated (FP32 reconstruction, FP64 sums) */
+    double rel_residual;   /* last residual evaluated (FP32 reconstruction, compensated FP32
+                              partials, FP64 block sum) */
     double lam;            /* lambda of the last iteration */
     int ls_backtracks;     /* step reductions the line search took in all */
 } cp_batch_result;
